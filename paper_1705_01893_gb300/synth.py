@@ -1,0 +1,171 @@
+"""Seeded synthetic inputs for the messenger mapmaker: sky, scan pointing, 1/f noise.
+
+This module only *generates data* (the forward model d = P m_true + n of Sec. 2, Eq. 1).
+It holds none of the solver's arithmetic and is shared by the CUDA path, the tests and
+the CPU oracle as a pure input source.
+
+Workload shapes (the paper's own simulation, Sec. 2.3, uses a 2-degree patch with
+compact sources that is not reproduced; these synthetic stand-ins keep its structure:
+cross-linked rasters, polarised detectors at several angles, N(f) = s^2 (1 + (fk/f)^a)):
+
+* ``config_temperature_64``   64x64 T-only map, one detector, 64 horizontal then 64
+  vertical sweeps of 256 samples at 4 samples/pixel (32768 samples, 100 Hz).
+* ``config_iqu(...)``         W x W IQU map, D detectors of n samples each at 200 Hz,
+  alternating horizontal / vertical sweeps (4 samples per pixel), detector angles
+  0, 180/D, ... degrees plus a 0.5 Hz half-wave-plate rotation.
+
+Noise draws use a circulant covariance per chunk: n = irfft(sqrt(N_k) * rfft(w)),
+w ~ N(0, 1), whose covariance is exactly F^-1 diag(N_k) F.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 1705_0000
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.default_rng([int(seed), int(stream)])
+
+
+def grf_map(nx: int, ny: int, seed: int, stream: int, rms: float = 1.0) -> np.ndarray:
+    """Gaussian random field with power ~ l^-2 (amplitude ~ 1/|l|), zero mean, given rms."""
+    w = _rng(seed, stream).standard_normal((ny, nx))
+    W = np.fft.rfft2(w)
+    ly = np.fft.fftfreq(ny)[:, None] * ny
+    lx = np.fft.rfftfreq(nx)[None, :] * nx
+    ell = np.sqrt(lx * lx + ly * ly)
+    amp = np.zeros_like(ell)
+    amp[ell > 0] = 1.0 / ell[ell > 0]
+    m = np.fft.irfft2(W * amp, s=(ny, nx))
+    m -= m.mean()
+    m *= rms / m.std()
+    return m
+
+
+def sky(width: int, ncomp: int, seed: int) -> np.ndarray:
+    """[width*width, ncomp] float64 sky: T unit rms; Q, U independent GRFs at 0.1 T rms."""
+    t = grf_map(width, width, seed, 1, 1.0).ravel()
+    if ncomp == 1:
+        return t[:, None].copy()
+    q = grf_map(width, width, seed, 2, 0.1).ravel()
+    u = grf_map(width, width, seed, 3, 0.1).ravel()
+    return np.stack([t, q, u], axis=1)
+
+
+def noise_psd(n: int, fs: float, sigma: float, fknee: float, alpha: float) -> np.ndarray:
+    """PSD on the rfft bins k = 0..n//2 used to *draw* noise; DC floored at bin 1."""
+    f = np.arange(n // 2 + 1) * (fs / n)
+    N = np.empty(n // 2 + 1)
+    N[1:] = sigma * sigma * (1.0 + (fknee / f[1:]) ** alpha)
+    N[0] = N[1]
+    return N
+
+
+def draw_noise(n: int, psd: np.ndarray, seed: int, stream: int) -> np.ndarray:
+    w = _rng(seed, stream).standard_normal(n)
+    return np.fft.irfft(np.sqrt(psd) * np.fft.rfft(w), n)
+
+
+def raster_temperature(width: int, spp: int) -> np.ndarray:
+    """width horizontal sweeps (row s, sample j -> column j//spp) then width vertical ones."""
+    j = np.arange(width * spp) // spp
+    rows = [s * width + j for s in range(width)]
+    cols = [j * width + s for s in range(width)]
+    return np.concatenate(rows + cols).astype(np.int32)
+
+
+def raster_alternating(width: int, spp: int, n: int, phase: int) -> np.ndarray:
+    """Sweeps of width*spp samples alternating horizontal / vertical, advancing one
+    row / column every two sweeps, starting ``phase`` rows/columns in."""
+    per = width * spp
+    nsweep = n // per
+    j = np.arange(per) // spp
+    out = np.empty(nsweep * per, dtype=np.int64)
+    for s in range(nsweep):
+        line = (s // 2 + phase) % width
+        out[s * per:(s + 1) * per] = line * width + j if s % 2 == 0 else j * width + line
+    return out[:n].astype(np.int32)
+
+
+def _project(m: np.ndarray, pix: np.ndarray, c: np.ndarray | None, s: np.ndarray | None) -> np.ndarray:
+    """Signal timestream of Eq. 1 (T, or T + Q cos2psi + U sin2psi) for the data model."""
+    good = pix >= 0
+    out = np.zeros(pix.shape[0])
+    p = pix[good]
+    out[good] = m[p, 0]
+    if m.shape[1] == 3:
+        out[good] += m[p, 1] * c[good] + m[p, 2] * s[good]
+    return out
+
+
+def make_problem(width: int, ncomp: int, pix_chunks, fs: float, sigmas, fknees, alphas,
+                 angles_deg, hwp_hz: float, seed: int, weight_dtype=np.float32,
+                 noiseless: bool = False):
+    """Assemble concatenated chunk arrays.  Returns a dict of numpy arrays:
+    pix int32 [n], cos/sin weight_dtype [n] (None for T-only), tod float32 [n],
+    offsets int64 [n_chunks+1], params float64 [n_chunks, 4] = (sigma, fknee, alpha, fs),
+    m_true float64 [npix, ncomp]."""
+    m_true = sky(width, ncomp, seed)
+    nchunk = len(pix_chunks)
+    lens = [len(p) for p in pix_chunks]
+    offsets = np.zeros(nchunk + 1, dtype=np.int64)
+    offsets[1:] = np.cumsum(lens)
+    pix = np.concatenate(pix_chunks).astype(np.int32)
+    cos = sin = None
+    if ncomp == 3:
+        cos = np.empty(offsets[-1], dtype=weight_dtype)
+        sin = np.empty(offsets[-1], dtype=weight_dtype)
+    tod = np.empty(offsets[-1], dtype=np.float32)
+    params = np.zeros((nchunk, 4))
+    for c in range(nchunk):
+        a, b = offsets[c], offsets[c + 1]
+        n = b - a
+        cc = ss = None
+        if ncomp == 3:
+            t = np.arange(n) / fs
+            psi = np.deg2rad(angles_deg[c]) + 2.0 * np.pi * hwp_hz * t
+            cos[a:b] = np.cos(2.0 * psi)
+            sin[a:b] = np.sin(2.0 * psi)
+            cc = cos[a:b].astype(np.float64)
+            ss = sin[a:b].astype(np.float64)
+        sig = _project(m_true, pix[a:b], cc, ss)
+        if not noiseless:
+            sig = sig + draw_noise(n, noise_psd(n, fs, sigmas[c], fknees[c], alphas[c]), seed, 100 + c)
+        tod[a:b] = sig
+        params[c] = (sigmas[c], fknees[c], alphas[c], fs)
+    return dict(width=width, npix=width * width, ncomp=ncomp, pix=pix, cos=cos, sin=sin,
+                tod=tod, offsets=offsets, params=params, m_true=m_true)
+
+
+def config_temperature_64(seed: int = SEED_BASE + 0, noiseless: bool = False):
+    """64x64 T-only map, 1 detector, 32768 samples at 100 Hz, sigma 1, fknee 1 Hz, alpha 2."""
+    pix = raster_temperature(64, 4)
+    return make_problem(64, 1, [pix], 100.0, [1.0], [1.0], [2.0], [0.0], 0.0, seed,
+                        noiseless=noiseless)
+
+
+def config_iqu(width: int, n_det: int, n_per_det: int, seed: int, fs: float = 200.0,
+               spp: int = 4, fknee_range=(0.1, 2.0), alpha_range=(1.0, 3.0),
+               weight_dtype=np.float32, noiseless: bool = False, phase_step: int | None = None):
+    """IQU raster of n_det detectors at angles k*180/n_det degrees with a 0.5 Hz HWP.
+    Per-detector 1/f noise: sigma 1, fknee ~ U(fknee_range), alpha ~ U(alpha_range)."""
+    rng = _rng(seed, 7)
+    fknees = rng.uniform(*fknee_range, size=n_det)
+    alphas = rng.uniform(*alpha_range, size=n_det)
+    if phase_step is None:
+        phase_step = max(1, width // n_det)
+    chunks = [raster_alternating(width, spp, n_per_det, d * phase_step) for d in range(n_det)]
+    angles = [180.0 * d / n_det for d in range(n_det)]
+    return make_problem(width, 3, chunks, fs, [1.0] * n_det, fknees, alphas, angles, 0.5,
+                        seed, weight_dtype=weight_dtype, noiseless=noiseless)
+
+
+def config_iqu_512(seed: int = SEED_BASE + 1):
+    """512x512 IQU map, 8 detectors x 2^22 samples at 200 Hz, FP32 cos2psi/sin2psi."""
+    return config_iqu(512, 8, 1 << 22, seed)
+
+
+def config_iqu_256(seed: int = SEED_BASE + 3):
+    """256x256 IQU map, 4 detectors x 2^20 samples at 200 Hz."""
+    return config_iqu(256, 4, 1 << 20, seed)

@@ -1,0 +1,271 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix (CPU only).
+
+None of these expected values comes from the CUDA path.  Each pin is chosen so that a
+plausible slip in the oracle (a dropped term, a wrong sign, a swapped weight, a missing
+normalisation) breaks at least one of them; ``test_planted_mistakes`` proves that for a
+list of such slips.
+"""
+import numpy as np
+import pytest
+
+import oracle.messenger as O
+from paper_1705_01893_gb300 import synth
+
+
+def tiny(seed=11, noiseless=False, width=8, ndet=2, n=512):
+    return synth.config_iqu(width, ndet, n, seed, noiseless=noiseless)
+
+
+def exact_signal(s, m=None):
+    """d = P m written out in float64 straight from Eq. 1 (independent of the oracle)."""
+    m = s["m_true"] if m is None else m
+    pix = s["pix"].astype(np.int64)
+    d = m[pix, 0].copy()
+    if s["ncomp"] == 3:
+        d += m[pix, 1] * s["cos"].astype(np.float64) + m[pix, 2] * s["sin"].astype(np.float64)
+    return d
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+# --------------------------------------------------------------------------- pins
+def pin_fourier_chi2(prob, rng):
+    """chi^2 summed over Fourier modes (Sec. 3.1) equals the explicit quadratic form
+    (d - Pm)^T N'^-1 (d - Pm) with a dense circulant N' (Eq. 3), at lambda = 1 and 7."""
+    m = rng.standard_normal((prob.npix, prob.ncomp))
+    for lam in (1.0, 7.0):
+        a = O.chi2(prob, m, lam)
+        b = O.dense_chi2(prob, m, lam)
+        assert abs(a - b) <= 1e-10 * abs(b), (lam, a, b)
+
+
+def pin_white_noise(s):
+    """White noise (Nbar = 0): t = d, so one iteration from any start is the binned map,
+    which is then the exact GLS solution (Sec. 2.1 with T = N)."""
+    off = s["offsets"]
+    psd = [np.full(int(off[c + 1] - off[c]) // 2 + 1, 2.0) for c in range(len(off) - 1)]
+    prob = O.problem_from_synth(s, psd=psd, tau=np.full(len(off) - 1, 2.0))
+    m_any = np.random.default_rng(3).standard_normal((prob.npix, prob.ncomp))
+    m1, _ = O.messenger_step(prob, m_any, 1.0)
+    ref = O.dense_solve(prob)
+    assert rel(m1, ref) < 1e-12
+
+
+def pin_noiseless(s):
+    """Noiseless d = P m_true: the binned map recovers m_true on valid pixels and m_true is
+    a fixed point of the iteration at any lambda (unbiasedness, Sec. 2.1)."""
+    prob = O.problem_from_synth(s)
+    v = prob.valid
+    mt = s["m_true"] * v[:, None]          # cut pixels carry no signal in this pin
+    prob.tod = exact_signal(s, mt)
+    prob.dtilde = [np.fft.rfft(prob.tod[a:b]) for a, b in prob.chunks()]
+    mb, _ = O.messenger_step(prob, np.zeros_like(mt), np.inf)
+    assert np.max(np.abs(mb - mt)) < 1e-12
+    for lam in (1.0, 30.0):
+        m1, x2 = O.messenger_step(prob, mt, lam)
+        assert np.max(np.abs(m1 - mt)) < 1e-12
+        assert x2 < 1e-20
+
+
+def pin_gls_convergence(prob):
+    """lambda = 1 iterations converge to the brute-force dense GLS solution (Eq. 2)."""
+    ref = O.dense_solve(prob)
+    m, ch = O.run_messenger(prob, np.r_[np.inf, np.ones(300)])
+    assert rel(m, ref) < 1e-8
+    assert abs(ch[-1] - O.chi2(prob, ref)) < 1e-9 * ch[-1]
+
+
+def pin_fixed_lambda(prob, lam=5.0):
+    """Fixed-lambda iterations converge to m(lambda) with N' = N + (lambda - 1) T
+    (Sec. 2.1), and chi^2(m_i, lambda) never increases (App. A: each half-step minimises
+    the augmented chi^2_1, whose minimum over t is chi^2(m, lambda))."""
+    ref = O.dense_solve(prob, lam)
+    m = np.zeros((prob.npix, prob.ncomp))
+    m, _ = O.messenger_step(prob, m, np.inf)
+    vals = []
+    for _ in range(200):
+        vals.append(O.chi2(prob, m, lam))
+        m, _ = O.messenger_step(prob, m, lam)
+    assert rel(m, ref) < 1e-8
+    d = np.diff(vals)
+    assert np.all(d <= 1e-10 * abs(vals[0])), d.max()
+
+
+def pin_pcg(prob):
+    """PCG converges to the same dense solution; messenger and PCG end points agree."""
+    ref = O.dense_solve(prob)
+    x, ch = O.pcg(prob, 80)
+    assert rel(x, ref) < 1e-10
+    assert np.all(np.diff(ch[:20]) <= 1e-9 * ch[0])
+
+
+ALL_PINS = ["fourier_chi2", "white_noise", "noiseless", "gls", "fixed_lambda", "pcg"]
+
+
+def run_pin(name):
+    s = tiny()
+    if name == "fourier_chi2":
+        pin_fourier_chi2(O.problem_from_synth(s), np.random.default_rng(5))
+    elif name == "white_noise":
+        pin_white_noise(s)
+    elif name == "noiseless":
+        pin_noiseless(tiny(noiseless=True))
+    elif name == "gls":
+        pin_gls_convergence(O.problem_from_synth(s))
+    elif name == "fixed_lambda":
+        pin_fixed_lambda(O.problem_from_synth(s))
+    elif name == "pcg":
+        pin_pcg(O.problem_from_synth(s))
+
+
+@pytest.mark.parametrize("name", ALL_PINS)
+def test_pin(name):
+    run_pin(name)
+
+
+# ----------------------------------------------------------------- further pins
+def test_hits_closed_form_temperature_raster():
+    """64 horizontal + 64 vertical sweeps at 4 samples/pixel: exactly 8 hits per pixel."""
+    s = synth.config_temperature_64()
+    prob = O.problem_from_synth(s)
+    assert prob.hits.dtype.kind == "i"
+    assert np.all(prob.hits == 8)
+    assert np.all(prob.valid)
+
+
+def test_temperature_binned_map_noiseless():
+    """T-only, noiseless: the binned map is the per-pixel mean of the samples = m_true."""
+    s = synth.config_temperature_64(noiseless=True)
+    prob = O.problem_from_synth(s)
+    prob.tod = exact_signal(s)
+    prob.dtilde = [np.fft.rfft(prob.tod[a:b]) for a, b in prob.chunks()]
+    mb, _ = O.messenger_step(prob, np.zeros((prob.npix, 1)), np.inf)
+    assert np.max(np.abs(mb - s["m_true"])) < 1e-12
+
+
+def test_large_lambda_forgets_start():
+    """For very large lambda, F = 0: the next map does not depend on m_i (Sec. 2.1)."""
+    prob = O.problem_from_synth(tiny())
+    rng = np.random.default_rng(1)
+    a, _ = O.messenger_step(prob, rng.standard_normal((prob.npix, 3)), 1e14)
+    b, _ = O.messenger_step(prob, rng.standard_normal((prob.npix, 3)), 1e14)
+    c, _ = O.messenger_step(prob, np.zeros((prob.npix, 3)), np.inf)
+    assert rel(a, c) < 1e-9 and rel(b, c) < 1e-9
+
+
+def test_spectral_radius_below_one():
+    """The error propagator F(lambda) has spectral radius < 1 on the observed pixels
+    (Sec. 2.1), and one messenger step equals m_d + F m_i."""
+    prob = O.problem_from_synth(tiny())
+    for lam in (1.0, 10.0):
+        F = O.dense_F(prob, lam)
+        rho = np.max(np.abs(np.linalg.eigvals(F)))
+        assert rho < 1.0
+        idx = np.flatnonzero(prob.valid)
+        m = np.zeros((prob.npix, 3))
+        m[idx] = np.random.default_rng(2).standard_normal((idx.size, 3))
+        md, _ = O.messenger_step(prob, np.zeros_like(m), lam)
+        m1, _ = O.messenger_step(prob, m, lam)
+        assert rel(m1[idx].ravel(), md[idx].ravel() + F @ m[idx].ravel()) < 1e-10
+
+
+def test_heterogeneous_tau_same_solution():
+    """Any admissible T (here tau_c = 0.5 sigma_c^2 per chunk, Sec. 4.2) leaves the fixed
+    point unchanged: lambda = 1 iterations still reach the GLS solution."""
+    s = tiny()
+    prob = O.problem_from_synth(s, tau=np.array([0.5, 0.8]))
+    ref = O.dense_solve(prob)
+    m, _ = O.run_messenger(prob, np.r_[np.inf, np.ones(400)])
+    assert rel(m, ref) < 1e-7
+
+
+def test_unbiased_over_noise_seeds():
+    """<m_i> = m_true for every iterate (Sec. 2.1): mean over seeds within 5 sigma."""
+    base = tiny(seed=100)
+    v = O.problem_from_synth(base).valid
+    mt = base["m_true"] * v[:, None]        # no signal on cut pixels (their rows are zero)
+    maps = []
+    for k in range(48):
+        s = tiny(seed=100 + k)
+        s["tod"] = (exact_signal(base, mt) + (s["tod"] - exact_signal(s))).astype(np.float32)
+        prob = O.problem_from_synth(s)
+        m, _ = O.run_messenger(prob, O.cooling_schedule(O.lambda_max(prob), 3, 3))
+        maps.append(m)
+    maps = np.array(maps)
+    mean = maps.mean(0)[v]
+    err = maps.std(0)[v] / np.sqrt(len(maps))
+    z = np.abs(mean - base["m_true"][v]) / err
+    assert np.max(z) < 5.0
+
+
+def test_rfft_convention_round_trip():
+    """The oracle's spectrum convention: Parseval with multiplicity weights, and round trip."""
+    x = np.random.default_rng(0).standard_normal(1000)
+    X = np.fft.rfft(x)
+    assert abs(np.sum(O.rfft_weights(1000) * np.abs(X) ** 2) / 1000 - x @ x) < 1e-9 * (x @ x)
+    assert np.allclose(np.fft.irfft(X, 1000), x)
+
+
+def test_schedule_shape():
+    lam = O.cooling_schedule(1e4, 10, 10)
+    assert lam.size == 101 and np.isinf(lam[0])
+    assert lam[1] == pytest.approx(1e4) and lam[-1] == 1.0
+    assert np.all(np.diff(lam[1:]) <= 0)
+
+
+# ------------------------------------------------------------- planted mistakes
+def _plant(monkeypatch, which):
+    if which == "drop_lambda":
+        orig = O.messenger_step
+
+        def bad(prob, m, lam):
+            return orig(prob, m, 1.0 if np.isfinite(lam) else lam)
+        monkeypatch.setattr(O, "messenger_step", bad)
+    elif which == "swap_qu":
+        orig = O.Problem.weights
+
+        def bad(self, a, b):
+            w = orig(self, a, b)
+            return w[:, [0, 2, 1]] if w.shape[1] == 3 else w
+        monkeypatch.setattr(O.Problem, "weights", bad)
+    elif which == "filter_sign":
+        def bad(prob, m, lam):
+            acc = np.zeros((prob.npix, prob.ncomp))
+            for c, (a, b) in enumerate(prob.chunks()):
+                n = b - a
+                r = np.fft.rfft(prob.P(m, a, b))
+                lt = lam * prob.tau[c] if np.isfinite(lam) else np.inf
+                tt = prob.dtilde[c] if np.isinf(lt) else (lt * prob.dtilde[c] - prob.nbar(c) * r) / (lt + prob.nbar(c))
+                acc += prob.PT(np.fft.irfft(tt, n), a, b) / prob.tau[c]
+            return prob.bin(acc), 0.0
+        monkeypatch.setattr(O, "messenger_step", bad)
+    elif which == "chi2_no_mult":
+        monkeypatch.setattr(O, "rfft_weights", lambda n: np.ones(n // 2 + 1))
+    elif which == "nbar_is_n":
+        monkeypatch.setattr(O.Problem, "nbar", lambda self, c: self.psd[c])
+    elif which == "pcg_no_precond_update":
+        orig = O.jacobi_blocks
+        monkeypatch.setattr(O, "jacobi_blocks", lambda prob: 2.0 * orig(prob) + 1e-3)
+    elif which == "transposed_block":
+        orig = O.Problem.bin
+
+        def bad(self, acc):
+            return np.einsum("pji,pj->pi", self.W + np.triu(np.ones(3), 1)[None] * 1e-2, acc) \
+                if self.ncomp == 3 else orig(self, acc)
+        monkeypatch.setattr(O.Problem, "bin", bad)
+
+
+@pytest.mark.parametrize("which", ["drop_lambda", "swap_qu", "filter_sign", "chi2_no_mult",
+                                   "nbar_is_n", "transposed_block"])
+def test_planted_mistakes(monkeypatch, which):
+    """Each planted slip in the oracle must break at least one pin."""
+    _plant(monkeypatch, which)
+    failures = 0
+    for name in ALL_PINS:
+        try:
+            run_pin(name)
+        except (AssertionError, np.linalg.LinAlgError, FloatingPointError):
+            failures += 1
+    assert failures >= 1, which
