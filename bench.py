@@ -1,0 +1,325 @@
+"""Benchmark of the GB300 messenger-field mapmaker.
+
+One step = one cooled messenger iteration (Sec. 2.1) over the whole workload: pointing
+gather + column FFTs, row FFTs with the Fourier-diagonal filter and chi^2, inverse FFTs +
+FP64 binning, and the per-pixel 3x3 map solve.  Workload: 512x512 IQU map, 8 detectors x
+2^22 samples at 200 Hz (33.5 M samples), FP32 cos/sin weights, per-detector 1/f noise,
+lambda cycling through a 10 x 10 cooling schedule.  Inputs per step (pointing 403 MB,
+data spectrum 134 MB, noise table 67 MB) exceed the 129 MB L2, so no flush is needed.
+
+``--impl reference`` times the FP64 CPU oracle on the same workload instead (a bounded
+sample: one of the eight detector chunks per step, scaled by eight).
+
+With ``--gpus N`` under torchrun each rank runs an independent replica on its own GPU
+(the solver is single-GPU); value = total iterations of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "messenger iters/s"
+UNIT = "iter/s"
+WORKLOAD = "iqu512_8det_2^22"
+
+
+def workload_config(s):
+    n = int(s["offsets"][-1])
+    return {"workload": WORKLOAD, "map": "512x512 IQU", "detectors": len(s["offsets"]) - 1,
+            "samples_per_detector": int(s["offsets"][1] - s["offsets"][0]), "n_samples": n,
+            "weights": "fp32 cos2psi/sin2psi", "schedule": "10 levels x 10 iterations, cycled",
+            "l2": "inputs larger than L2 (>600 MB read per step), no flush",
+            "parallelism": "replicas"}
+
+
+def bytes_per_stage(n, npix, ncomp, wbytes):
+    """Algorithmic HBM bytes of each kernel per launch (see the design notes)."""
+    blk = 6 if ncomp == 3 else 1
+    mapb = 16 if ncomp == 3 else 4
+    return {
+        "gather_fft": n * (4 + wbytes) + 4 * n + mapb * npix,
+        "filter": 14 * n,
+        "ifft_bin": 4 * n + n * (4 + wbytes) + 8 * ncomp * npix,
+        "map": npix * (16 * ncomp + 8 * blk + mapb),
+    }
+
+
+def b_strict(n, npix, ncomp, wbytes):
+    return n * (2 * (4 + wbytes) + 4) + npix * (104 if ncomp == 3 else 24)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", dev_id, f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if "Active" in r[4 + i]
+                          and "Not" not in r[4 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ----------------------------------------------------------------------- CPU oracle
+def time_oracle(s, steps, warmup, one_chunk=True):
+    """Time the FP64 oracle's messenger step on the host (chunk 0 only when one_chunk,
+    scaled by the chunk count)."""
+    import oracle.messenger as O
+    sub = s
+    scale = 1.0
+    if one_chunk:
+        c = 0
+        a, b = int(s["offsets"][c]), int(s["offsets"][c + 1])
+        sub = dict(s)
+        sub["pix"], sub["tod"] = s["pix"][a:b], s["tod"][a:b]
+        sub["cos"] = None if s["cos"] is None else s["cos"][a:b]
+        sub["sin"] = None if s["sin"] is None else s["sin"][a:b]
+        sub["offsets"] = np.array([0, b - a], dtype=np.int64)
+        sub["params"] = s["params"][c:c + 1]
+        scale = float(len(s["offsets"]) - 1)
+    prob = O.problem_from_synth(sub)
+    lam = O.cooling_schedule(O.lambda_max(prob), 10, 10)
+    m = np.zeros((sub["npix"], sub["ncomp"]))
+    for i in range(warmup):
+        m, _ = O.messenger_step(prob, m, lam[i % len(lam)])
+    t0 = time.perf_counter()
+    for i in range(steps):
+        m, _ = O.messenger_step(prob, m, lam[(warmup + i) % len(lam)])
+    dt = (time.perf_counter() - t0) / steps * scale
+    return 1.0 / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1705_01893_gb300 import synth
+    s = synth.config_iqu_512()
+    v, dt = time_oracle(s, args.steps, args.warmup, one_chunk=True)
+    sample = "chunk 0 of 8 (2^22 samples) per step, time x8; numpy FP64, 1 thread"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(s),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1705_01893_gb300 import binding, build, synth
+    if local == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    binding.load()
+
+    s = synth.config_iqu_512()
+    n, npix, nc = int(s["offsets"][-1]), s["npix"], s["ncomp"]
+    plan = binding.plan_from_synth(s, dev)
+    sched = binding.cooling_schedule(plan.lambda_max(), 10, 10)
+    m = torch.zeros(npix, nc, dtype=torch.float64, device=dev)
+    chi = torch.zeros(max(args.steps, 1) + args.warmup, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    B = binding
+
+    def step(i, ev=None):
+        lam = float(sched[i % len(sched)])
+        if ev is not None:
+            ev[0].record(stream)
+        plan.stage(B.MM_STAGE_GATHER_FFT)
+        if ev is not None:
+            ev[1].record(stream)
+        plan.stage(B.MM_STAGE_FILTER, lam, chi2_slot=chi[i:i + 1])
+        if ev is not None:
+            ev[2].record(stream)
+        plan.stage(B.MM_STAGE_IFFT_BIN)
+        if ev is not None:
+            ev[3].record(stream)
+        plan.stage(B.MM_STAGE_MAP)
+        if ev is not None:
+            ev[4].record(stream)
+
+    plan.stage(B.MM_STAGE_LOAD, map_inout=m)
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+
+    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", local))
+    sampler = ClockSampler(("GPU-" + uuid) if "-" in uuid and not uuid.startswith("GPU") else uuid)
+    time.sleep(0.3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(args.warmup + k, evs[k])
+    t_end.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    stage_names = ["gather_fft", "filter", "ifft_bin", "map"]
+    stage_ms = {nm: [evs[k][j].elapsed_time(evs[k][j + 1]) for k in range(args.steps)]
+                for j, nm in enumerate(stage_names)}
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # end to end through the public call, host buffers: map in (pinned), one iteration,
+    # map and chi^2 out, synchronised every step
+    m_host = torch.zeros(npix, nc, dtype=torch.float64).pin_memory()
+    m_back = torch.empty_like(m_host).pin_memory()
+    c_back = torch.empty(1, dtype=torch.float64).pin_memory()
+    m_dev = torch.empty(npix, nc, dtype=torch.float64, device=dev)
+    c_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+    m_host.copy_(m.cpu())
+    e2e_steps = max(3, min(args.steps, 20))
+    for i in range(2):
+        m_dev.copy_(m_host, non_blocking=True)
+        plan.messenger(m_dev, [float(sched[i % len(sched)])], c_dev)
+        m_back.copy_(m_dev, non_blocking=True)
+        c_back.copy_(c_dev, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        m_dev.copy_(m_back if i else m_host, non_blocking=True)
+        plan.messenger(m_dev, [float(sched[i % len(sched)])], c_dev)
+        m_back.copy_(m_dev, non_blocking=True)
+        c_back.copy_(c_dev, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * npix * nc,
+           "d2h_bytes_per_step": 8 * npix * nc + 8}
+
+    if rank != 0:
+        return
+    wbytes = 8 if s["cos"] is not None and s["cos"].dtype == np.float32 else (4 if nc == 3 else 0)
+    bps = bytes_per_stage(n, npix, nc, wbytes)
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    avg = {k: sum(v) / len(v) for k, v in stage_ms.items()}
+    dom = max(avg, key=lambda k: avg[k])
+    achieved = bps[dom] / (avg[dom] * 1e-3) / 1e9
+    iter_bytes = sum(bps.values())
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        traffic = json.load(open(prof)).get(dom)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(s),
+        "tod_gsamples_per_s": n * value / 1e9,
+        "iteration_hbm": {"bytes_pass": iter_bytes, "bytes_strict": b_strict(n, npix, nc, wbytes),
+                          "frac_pass": iter_bytes / (ms_step * 1e-3) / 1e9 / hbm,
+                          "frac_strict": b_strict(n, npix, nc, wbytes) / (ms_step * 1e-3) / 1e9 / hbm,
+                          "peak_gbs": hbm, "peak": peak_src},
+        "stage_ms": {k: round(v, 5) for k, v in avg.items()},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "bytes_per_launch": bps[dom], "peak_source": peak_src},
+        "e2e": e2e,
+        "gpu_launches": args.steps * (3 * len(plan_groups(s)) + 1),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, dt = time_oracle(s, 1, 0, one_chunk=False)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "1 full iteration of the 8 x 2^22 workload, numpy FP64, 1 thread"}
+    print(json.dumps(line), flush=True)
+
+
+def plan_groups(s):
+    lens = np.diff(s["offsets"])
+    return sorted(set(int(x) for x in lens))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * mm.h -- C ABI of the GB300 messenger-field mapmaker (Huffenberger & Naess 2017,
+ * "Cosmic Microwave Background Mapmaking with a Messenger Field", arXiv:1705.01893).
+ *
+ * Problem (Sec. 2, Eqs. 1-3): time-ordered data d = P m + n in chunks c = 0..C-1 of
+ * n_c samples each; stationary noise per chunk with power spectrum N_c(f) (circulant
+ * covariance, independent chunks).  The solver finds m minimising
+ *     chi^2(m) = (d - P m)^T N^-1 (d - P m),
+ * the minimum-variance map m = (P^T N^-1 P)^-1 P^T N^-1 d (Eq. 2), with the messenger
+ * iteration of Sec. 2.1 (T = diag(tau_c), piecewise per chunk as in Sec. 4.2) or, for
+ * comparison, preconditioned conjugate gradients.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Device buffers are caller-owned (e.g. torch tensors); the library never allocates
+ *    or frees device memory.  All per-plan device state lives in the caller's
+ *    `workspace`, sized by mm_plan_workspace_size.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream unless documented otherwise.
+ *  - Pointing: pix int32 [n] (-1 = sample excluded), and for IQU maps cos 2psi / sin 2psi
+ *    [n] in FP32 (MM_W_F32) or FP16 (MM_W_F16).  Pointing weights of a sample are
+ *    (1, cos 2psi, sin 2psi) (single pencil beam, Sec. 2.1).  The plan keeps the pointing
+ *    pointers: they must stay valid and unchanged for the plan's lifetime.
+ *  - Maps are float64 row-major [n_pix][ncomp], ncomp = 1 (T) or 3 (I, Q, U).  Pixels that
+ *    are unobserved or cut read back as 0.  Cut: a pixel is kept iff it has >= 1 hit and,
+ *    for IQU, eigmin/eigmax of its 3x3 block of P^T T^-1 P is >= rcond_min.
+ *  - Chunk lengths: n_c even with n_c/2 a power of two in [2^8, 2^23] in this version;
+ *    other lengths return MM_ERR_UNSUPPORTED.
+ *  - Errors: every call returns an mm_status; on failure mm_last_error() describes it.
+ *    A failed call leaves caller buffers unspecified and the plan usable, except
+ *    MM_ERR_STATE, which marks an entry point called out of order.
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_plan_s* mm_plan;
+typedef int mm_status;
+
+enum {
+  MM_OK = 0,
+  MM_ERR_ARG = -1,          /* bad argument (null pointer, size, range)            */
+  MM_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed         */
+  MM_ERR_NOMEM = -3,        /* workspace (or state) smaller than required          */
+  MM_ERR_TIMEOUT = -4,      /* reserved: a bounded device wait gave up             */
+  MM_ERR_STATE = -5,        /* call out of order (e.g. iterate before set_noise)   */
+  MM_ERR_SINGULAR = -6,     /* every pixel was cut                                 */
+  MM_ERR_UNSUPPORTED = -7   /* valid input this version does not handle            */
+};
+
+enum { MM_W_F32 = 0, MM_W_F16 = 1 };              /* pointing weight storage           */
+enum { MM_FP32_MIXED = 0 };                        /* messenger precision modes         */
+
+/* Bytes of device workspace a plan needs.  offsets: host int64 [n_chunks+1], chunk c
+ * spans samples [offsets[c], offsets[c+1]).  ncomp 1 or 3.  Pure host computation. */
+mm_status mm_plan_workspace_size(int n_chunks, const int64_t* offsets, int64_t n_pix,
+                                 int ncomp, int weight_dtype, size_t* bytes);
+
+/* Create a plan over the pointing matrix P (Sec. 2, Eq. 1: one pixel block per sample).
+ * Validates the chunk layout, lays out the workspace, builds FFT twiddle tables and the
+ * per-pixel hit counts (int32, exact).  cos2psi / sin2psi must be NULL iff ncomp == 1.
+ * workspace: device, >= mm_plan_workspace_size bytes, 256-byte aligned, caller-owned.
+ * rcond_min: IQU pixel-cut threshold (Sec. 2.1 needs P^T T^-1 P invertible), e.g. 1e-3.
+ * On success *out owns host memory only; release it with mm_plan_destroy. */
+mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t* offsets,
+                           const int32_t* pix, const void* cos2psi, const void* sin2psi,
+                           int weight_dtype, int64_t n_pix, int ncomp, double rcond_min,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/* Set the noise model and the data (Sec. 2.1 and Sec. 4.2).
+ *  psd_dev:    device float64 [sum_c (n_c/2+1)]: N_c(f_k), k = 0..n_c/2 per chunk, or NULL;
+ *  params:     host float64 [n_chunks][4] = (sigma, f_knee, alpha, f_sample) giving
+ *              N(f) = sigma^2 (1 + (f_knee/f)^alpha), DC bin floored to bin 1; used when
+ *              psd_dev is NULL (exactly one of psd_dev / params must be given);
+ *  tau:        host float64 [n_chunks] messenger covariance T = diag(tau_c), or NULL for
+ *              tau_c = sigma_c^2 (params) / min_k N_c(f_k) (table).  Requires N_c - tau_c
+ *              >= 0 on every bin (Nbar positive semi-definite, Sec. 2.1);
+ *  tod:        device float32 [n] data d.  Read during the call only.
+ * Forms Nbar, d~ = rfft(d), the weight blocks P^T T^-1 P, their inverses and the pixel cut,
+ * the block-Jacobi preconditioner and b = P^T N^-1 d for PCG, and lambda_max. */
+mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const double* params,
+                           const double* tau, const float* tod, void* stream);
+
+/* Host copy of lambda_max = max_c max_k Nbar_c(f_k) / tau_c, the top of the cooling
+ * range (Sec. 3.1).  Synchronises `stream`. */
+mm_status mm_lambda_max(mm_plan p, double* out, void* stream);
+
+/* Run n_iter messenger iterations (Sec. 2.1), iteration i at cooling parameter
+ * lambdas[i] (host array; INFINITY = the binned-map step t = d):
+ *   t~ = (lambda tau_c d~ + Nbar_c (P m)~) / (lambda tau_c + Nbar_c)  per Fourier mode,
+ *   m  = (P^T T^-1 P)^-1 P^T T^-1 t.
+ * map_inout: device float64 [n_pix][ncomp], read as m_0, overwritten by m_{n_iter}.
+ * chi2_out:  device float64 [n_iter] or NULL; chi2_out[i] = chi^2(m_i) (Eq. 3) of the map
+ *            entering iteration i, summed over all Fourier modes (Sec. 3.1).
+ * precision: MM_FP32_MIXED (FP32 timestreams and FFTs, FP64 pixel accumulation,
+ *            3x3 solves and chi^2 sums). */
+mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int precision,
+                               double* map_inout, double* chi2_out, void* stream);
+
+/* One stage of a messenger iteration, for callers that interleave their own work (or
+ * CUDA events) between the kernels of an iteration.  mm_messenger_iterate runs, per
+ * iteration, GATHER_FFT, FILTER, IFFT_BIN, MAP after one LOAD; the same sequence through
+ * this entry point gives identical results.
+ *   MM_STAGE_LOAD:       map_inout (device float64 [n_pix][ncomp]) -> internal FP32 map;
+ *   MM_STAGE_GATHER_FFT: P m gathered from the internal map, packed, column DFTs (Eq. 1);
+ *   MM_STAGE_FILTER:     row DFTs, per-mode messenger filter at `lambda` (>= 1 or INFINITY),
+ *                        chi^2 of the input map added to *chi2_slot if non-NULL (the caller
+ *                        zeroes it), inverse row DFTs (Sec. 2.1, Sec. 3.1);
+ *   MM_STAGE_IFFT_BIN:   inverse column DFTs and P^T T^-1 t into FP64 accumulators;
+ *   MM_STAGE_MAP:        m = (P^T T^-1 P)^-1 acc per pixel; written to map_inout if non-NULL,
+ *                        and to the internal map for the next GATHER_FFT.
+ * Unused arguments may be NULL / 0. */
+enum { MM_STAGE_LOAD = 0, MM_STAGE_GATHER_FFT = 1, MM_STAGE_FILTER = 2, MM_STAGE_IFFT_BIN = 3,
+       MM_STAGE_MAP = 4 };
+mm_status mm_messenger_stage(mm_plan p, int stage, double lambda, double* map_inout,
+                             double* chi2_slot, void* stream);
+
+/* Bytes of device state mm_pcg_iterate needs (caller-owned, 256-byte aligned). */
+mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes);
+
+/* Preconditioned conjugate gradients on P^T N^-1 P m = P^T N^-1 d, the paper's comparison
+ * solver (Sec. 1, Sec. 3.1), preconditioner = inverse of the per-pixel block
+ * sum_c c0_c P_c^T P_c with c0_c the diagonal of N_c^-1.  restart != 0 starts from
+ * map_inout (r = b - A m); restart == 0 continues from `state`.  map_inout holds the
+ * iterate.  chi2_out: device float64 [n_iter] or NULL, chi^2 of the iterate entering each
+ * step, from chi^2(x) = d^T N^-1 d - x.b - x.r. */
+mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, void* state, int restart,
+                         double* chi2_out, void* stream);
+
+/* chi^2(m, lambda) = (d - Pm)^T N'^-1 (d - Pm), N' = N + (lambda - 1) T (Sec. 2.1; Eq. 3
+ * at lambda = 1) into *chi2_dev (device float64 scalar, overwritten). */
+mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev,
+                  void* stream);
+
+/* Operators, for testing and for callers composing their own solvers.
+ * mm_apply_pointing:   tod_out[s] = (P m)_s in FP32 (Eq. 1), cut pixels contribute 0.
+ * mm_apply_pointing_T: acc_out[p][c] = sum_s P_sp,c tod[s] in FP64 over every sample with
+ *                      pix >= 0 (no cut), acc_out overwritten.
+ * mm_rfft:             spec_out = rfft of every chunk of tod, complex64 interleaved
+ *                      [sum_c (n_c/2+1)][2], unnormalised (numpy.fft.rfft convention). */
+mm_status mm_apply_pointing(mm_plan p, const double* map, float* tod_out, void* stream);
+mm_status mm_apply_pointing_T(mm_plan p, const float* tod, double* acc_out, void* stream);
+mm_status mm_rfft(mm_plan p, const float* tod, float* spec_out, void* stream);
+
+/* Copy plan maps out (any pointer may be NULL): hits int32 [n_pix]; valid uint8 [n_pix];
+ * weight float64 [n_pix][ncomp*ncomp] = (P^T T^-1 P)^-1 blocks (0 on cut pixels);
+ * available after mm_set_noise_psd (hits after mm_plan_pointing). */
+mm_status mm_plan_maps(mm_plan p, int32_t* hits, uint8_t* valid, double* weight,
+                       void* stream);
+
+/* Release the plan's host memory (the caller frees the workspace). NULL is a no-op. */
+void mm_plan_destroy(mm_plan p);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char* mm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MM_H */

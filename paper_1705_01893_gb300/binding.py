@@ -1,0 +1,239 @@
+"""Thin ctypes binding of ``libmm.so`` (C ABI in ``include/mm.h``).
+
+Argument marshalling only: torch tensors provide device memory and the CUDA stream; every
+step of the solver runs in the library's kernels.  There is no CPU fallback: if the
+library is missing or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmm.so")
+
+MM_OK, MM_ERR_ARG, MM_ERR_CUDA, MM_ERR_NOMEM, MM_ERR_TIMEOUT, MM_ERR_STATE, MM_ERR_SINGULAR, \
+    MM_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+MM_W_F32, MM_W_F16 = 0, 1
+MM_FP32_MIXED = 0
+MM_STAGE_LOAD, MM_STAGE_GATHER_FFT, MM_STAGE_FILTER, MM_STAGE_IFFT_BIN, MM_STAGE_MAP = range(5)
+
+_vp = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_dp = ctypes.POINTER(ctypes.c_double)
+_szp = ctypes.POINTER(ctypes.c_size_t)
+
+# name -> (restype, argtypes); mirrors include/mm.h
+SIGNATURES = {
+    "mm_plan_workspace_size": (ctypes.c_int, [ctypes.c_int, _i64p, ctypes.c_int64, ctypes.c_int,
+                                              ctypes.c_int, _szp]),
+    "mm_plan_pointing": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64p, _vp, _vp, _vp,
+                                        ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                        _vp, ctypes.c_size_t, _vp]),
+    "mm_set_noise_psd": (ctypes.c_int, [_vp, _vp, _dp, _dp, _vp, _vp]),
+    "mm_lambda_max": (ctypes.c_int, [_vp, _dp, _vp]),
+    "mm_messenger_iterate": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    "mm_messenger_stage": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]),
+    "mm_pcg_state_bytes": (ctypes.c_int, [_vp, _szp]),
+    "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
+    "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
+    "mm_apply_pointing": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "mm_apply_pointing_T": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "mm_rfft": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "mm_plan_maps": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "mm_plan_destroy": (None, [_vp]),
+    "mm_last_error": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libmm.so (built by ``paper_1705_01893_gb300.build``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: build it with paper_1705_01893_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MMError(RuntimeError):
+    def __init__(self, fn: str, code: int, msg: str):
+        super().__init__(f"{fn} -> {code}: {msg}")
+        self.code = code
+
+
+def _check(fn: str, code: int):
+    if code != MM_OK:
+        raise MMError(fn, code, load().mm_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _dptr(arr: Optional[np.ndarray]):
+    if arr is None:
+        return None
+    arr = np.ascontiguousarray(arr, dtype=np.float64)
+    return arr.ctypes.data_as(_dp), arr
+
+
+class Plan:
+    """A pointing plan plus noise model on one GPU.
+
+    pix, cos2psi, sin2psi and the workspace are torch CUDA tensors owned by this object
+    (the library keeps raw pointers to them for the plan's lifetime)."""
+
+    def __init__(self, offsets: Sequence[int], pix, cos2psi, sin2psi, n_pix: int, ncomp: int,
+                 rcond_min: float = 1e-3, stream=None):
+        import torch
+        lib = load()
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.n_chunks = len(self.offsets) - 1
+        self.n_pix, self.ncomp = int(n_pix), int(ncomp)
+        if pix.dtype != torch.int32 or not pix.is_cuda:
+            raise TypeError("pix must be an int32 CUDA tensor")
+        self.pix = pix.contiguous()
+        self.cos2psi = None if cos2psi is None else cos2psi.contiguous()
+        self.sin2psi = None if sin2psi is None else sin2psi.contiguous()
+        wd = MM_W_F32
+        if self.cos2psi is not None and self.cos2psi.dtype == torch.float16:
+            wd = MM_W_F16
+        self.weight_dtype = wd
+        nbytes = ctypes.c_size_t()
+        offp = self.offsets.ctypes.data_as(_i64p)
+        _check("mm_plan_workspace_size", lib.mm_plan_workspace_size(
+            self.n_chunks, offp, self.n_pix, self.ncomp, wd, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=pix.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self._ws_bytes = int(nbytes.value)
+        self.device = pix.device
+        h = _vp()
+        _check("mm_plan_pointing", lib.mm_plan_pointing(
+            ctypes.byref(h), self.n_chunks, offp, _ptr(self.pix), _ptr(self.cos2psi),
+            _ptr(self.sin2psi), wd, self.n_pix, self.ncomp, float(rcond_min), self._ws_ptr,
+            self._ws_bytes, _stream(stream)))
+        self._h = h
+        self._pcg_state = None
+
+    # --------------------------------------------------------------------------- life
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------------- set-up
+    def set_noise(self, tod, params: Optional[np.ndarray] = None, psd=None,
+                  tau: Optional[np.ndarray] = None, stream=None):
+        """params: [n_chunks, 4] (sigma, fknee, alpha, fs) or psd: CUDA float64 tensor."""
+        lib = load()
+        pp = _dptr(None if params is None else np.asarray(params).reshape(-1))
+        tp = _dptr(tau)
+        _check("mm_set_noise_psd", lib.mm_set_noise_psd(
+            self._h, _ptr(psd), pp[0] if pp else None, tp[0] if tp else None,
+            _ptr(tod.contiguous()), _stream(stream)))
+
+    def lambda_max(self, stream=None) -> float:
+        out = ctypes.c_double()
+        _check("mm_lambda_max", load().mm_lambda_max(self._h, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    # ---------------------------------------------------------------------- solvers
+    def messenger(self, map_inout, lambdas, chi2_out=None, stream=None):
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        _check("mm_messenger_iterate", load().mm_messenger_iterate(
+            self._h, lam.ctypes.data_as(_dp), len(lam), MM_FP32_MIXED, _ptr(map_inout),
+            _ptr(chi2_out), _stream(stream)))
+
+    def stage(self, stage: int, lam: float = 1.0, map_inout=None, chi2_slot=None, stream=None):
+        _check("mm_messenger_stage", load().mm_messenger_stage(
+            self._h, int(stage), float(lam), _ptr(map_inout), _ptr(chi2_slot), _stream(stream)))
+
+    def pcg_state(self):
+        import torch
+        if self._pcg_state is None:
+            n = ctypes.c_size_t()
+            _check("mm_pcg_state_bytes", load().mm_pcg_state_bytes(self._h, ctypes.byref(n)))
+            self._pcg_state_t = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=self.device)
+            self._pcg_state = (self._pcg_state_t.data_ptr() + 255) // 256 * 256
+        return self._pcg_state
+
+    def pcg(self, map_inout, n_iter: int, restart: bool = True, chi2_out=None, stream=None):
+        st = self.pcg_state()
+        _check("mm_pcg_iterate", load().mm_pcg_iterate(
+            self._h, int(n_iter), _ptr(map_inout), st, int(bool(restart)), _ptr(chi2_out),
+            _stream(stream)))
+
+    def chi2(self, map_in, lam: float = 1.0, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.zeros(1, dtype=torch.float64, device=self.device)
+        _check("mm_chi2", load().mm_chi2(self._h, _ptr(map_in), float(lam), _ptr(out),
+                                         _stream(stream)))
+        return out
+
+    # -------------------------------------------------------------------- operators
+    def apply_pointing(self, map_in, tod_out, stream=None):
+        _check("mm_apply_pointing", load().mm_apply_pointing(self._h, _ptr(map_in), _ptr(tod_out),
+                                                             _stream(stream)))
+
+    def apply_pointing_T(self, tod, acc_out, stream=None):
+        _check("mm_apply_pointing_T", load().mm_apply_pointing_T(self._h, _ptr(tod), _ptr(acc_out),
+                                                                 _stream(stream)))
+
+    def rfft(self, tod, spec_out, stream=None):
+        _check("mm_rfft", load().mm_rfft(self._h, _ptr(tod), _ptr(spec_out), _stream(stream)))
+
+    def maps(self, hits=None, valid=None, weight=None, stream=None):
+        _check("mm_plan_maps", load().mm_plan_maps(self._h, _ptr(hits), _ptr(valid), _ptr(weight),
+                                                   _stream(stream)))
+
+
+def plan_from_synth(s: dict, device="cuda:0", rcond_min: float = 1e-3, tau=None, stream=None):
+    """Upload a synthetic-data dict (see ``synth``) and build a plan with its noise model."""
+    import torch
+    dev = torch.device(device)
+    pix = torch.from_numpy(s["pix"]).to(dev)
+    cos = None if s["cos"] is None else torch.from_numpy(s["cos"]).to(dev)
+    sin = None if s["sin"] is None else torch.from_numpy(s["sin"]).to(dev)
+    tod = torch.from_numpy(s["tod"]).to(dev)
+    plan = Plan(s["offsets"], pix, cos, sin, s["npix"], s["ncomp"], rcond_min, stream=stream)
+    plan.set_noise(tod, params=s["params"], tau=tau, stream=stream)
+    plan.tod = tod
+    return plan
+
+
+def cooling_schedule(lam_max: float, levels: int, iters: int) -> np.ndarray:
+    """One lambda = inf step, then `levels` geometric levels lam_max -> 1, `iters` each."""
+    if levels == 1:
+        lv = [1.0]
+    else:
+        lv = [lam_max ** ((levels - 1 - j) / (levels - 1)) for j in range(levels)]
+    return np.array([math.inf] + [v for v in lv for _ in range(iters)])

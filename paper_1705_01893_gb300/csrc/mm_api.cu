@@ -1,0 +1,1114 @@
+// C ABI of the messenger mapmaker: plan layout in the caller's workspace, set-up kernels
+// (hit counts, weight blocks, pixel cut, noise tables, data spectrum), the messenger and
+// PCG drivers, and the per-pixel kernels of the map step.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "mm_internal.cuh"
+
+using namespace mm;
+
+// ------------------------------------------------------------------------------ errors
+static thread_local char g_err[512] = "";
+
+void mm_set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+extern "C" const char* mm_last_error(void) { return g_err; }
+
+#define MM_ARG(cond, ...)          \
+  do {                             \
+    if (!(cond)) {                 \
+      mm_set_error(__VA_ARGS__);   \
+      return MM_ERR_ARG;           \
+    }                              \
+  } while (0)
+
+#define MM_CUDA(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      mm_set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                   __LINE__);                                                      \
+      return MM_ERR_CUDA;                                                          \
+    }                                                                              \
+  } while (0)
+
+static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ------------------------------------------------------------------------ FFT shapes
+// M = 2^p complex points per chunk (n = 2M real samples): columns M1, rows M2 = M / M1.
+// Rows stay <= 8192 (two rows in shared memory), columns <= 1024.
+static bool fft_shape(int64_t n, int* M, int* M1, int* M2) {
+  if (n < 512 || (n & 1)) return false;
+  const int64_t m = n / 2;
+  if (m & (m - 1)) return false;
+  int p = 0;
+  while ((int64_t(1) << p) < m) ++p;
+  if (p < 8 || p > 23) return false;
+  int lo = p / 2;
+  if (lo > 9) lo = 9;
+  if (p - lo > 13) lo = p - 13;
+  *M = (int)m;
+  *M1 = 1 << lo;
+  *M2 = (int)(m >> lo);
+  return true;
+}
+
+static int log_lo_of(int M) {
+  int p = 0;
+  while ((1 << p) < M) ++p;
+  return (p + 1) / 2;
+}
+
+static size_t tw_count(int M, int M1, int M2) {
+  const int lo = log_lo_of(M);
+  return (size_t)M1 + M2 + (size_t(1) << lo) + (size_t)(M >> lo) + M1 + M2;
+}
+
+// -------------------------------------------------------------------- workspace layout
+struct Layout {
+  size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
+      ybuf, scal, total;
+  int n_groups;
+  int gM[kMaxGroups], gM1[kMaxGroups], gM2[kMaxGroups], gcount[kMaxGroups];
+  std::vector<int> chunk_group;
+  int64_t spec_total, n_total;
+};
+
+static size_t up(size_t x) { return (x + 255) & ~size_t(255); }
+
+static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, int ncomp,
+                             Layout* L) {
+  MM_ARG(n_chunks >= 1, "n_chunks must be >= 1 (got %d)", n_chunks);
+  MM_ARG(off != nullptr, "offsets is NULL");
+  MM_ARG(n_pix >= 1 && n_pix < (int64_t(1) << 31), "n_pix out of range (%lld)", (long long)n_pix);
+  MM_ARG(ncomp == 1 || ncomp == 3, "ncomp must be 1 or 3 (got %d)", ncomp);
+  MM_ARG(off[0] >= 0, "offsets[0] must be >= 0");
+  L->n_groups = 0;
+  L->chunk_group.assign(n_chunks, -1);
+  L->spec_total = 0;
+  for (int c = 0; c < n_chunks; ++c) {
+    const int64_t n = off[c + 1] - off[c];
+    int M, M1, M2;
+    if (!fft_shape(n, &M, &M1, &M2)) {
+      mm_set_error("chunk %d: length %lld unsupported (need n even, n/2 a power of two in "
+                   "[2^8, 2^23])", c, (long long)n);
+      return MM_ERR_UNSUPPORTED;
+    }
+    int g = -1;
+    for (int i = 0; i < L->n_groups; ++i)
+      if (L->gM[i] == M) g = i;
+    if (g < 0) {
+      if (L->n_groups == kMaxGroups) {
+        mm_set_error("more than %d distinct chunk lengths", kMaxGroups);
+        return MM_ERR_UNSUPPORTED;
+      }
+      g = L->n_groups++;
+      L->gM[g] = M; L->gM1[g] = M1; L->gM2[g] = M2; L->gcount[g] = 0;
+    }
+    L->gcount[g]++;
+    L->chunk_group[c] = g;
+    L->spec_total += M;
+  }
+  L->n_total = off[n_chunks];
+  MM_ARG(L->n_total < (int64_t(1) << 31) * 2, "too many samples");
+  size_t tw = 0;
+  for (int g = 0; g < L->n_groups; ++g) tw += tw_count(L->gM[g], L->gM1[g], L->gM2[g]);
+  const size_t np = (size_t)n_pix;
+  const size_t blk = ncomp == 3 ? 6 : 1;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { size_t r = o; o += up(bytes); return r; };
+  L->desc = take(sizeof(ChunkDesc) * n_chunks);
+  L->chunks = take(sizeof(int) * n_chunks);
+  L->params = take(sizeof(double) * 4 * n_chunks);
+  L->tw = take(sizeof(float2) * tw);
+  L->hits = take(sizeof(int32_t) * np);
+  L->valid = take(np);
+  L->W = take(sizeof(double) * blk * np);
+  L->Minv = take(sizeof(double) * blk * np);
+  L->acc = take(sizeof(double) * ncomp * np);
+  L->acc12 = take(sizeof(double) * 2 * blk * np);
+  L->map4 = take((ncomp == 3 ? 16 : 4) * np);
+  L->bvec = take(sizeof(double) * ncomp * np);
+  L->dtab = take(sizeof(float2) * L->spec_total);
+  L->nbar = take(sizeof(float) * L->spec_total);
+  L->nyq = take(sizeof(float) * n_chunks);
+  L->c0 = take(sizeof(double) * n_chunks);
+  L->ybuf = take(sizeof(float2) * L->spec_total);
+  L->scal = take(sizeof(double) * kScalCount);
+  L->total = o;
+  return MM_OK;
+}
+
+extern "C" mm_status mm_plan_workspace_size(int n_chunks, const int64_t* offsets, int64_t n_pix,
+                                            int ncomp, int weight_dtype, size_t* bytes) {
+  MM_ARG(bytes != nullptr, "bytes is NULL");
+  MM_ARG(weight_dtype == MM_W_F32 || weight_dtype == MM_W_F16, "bad weight_dtype %d",
+         weight_dtype);
+  Layout L;
+  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, &L);
+  if (st != MM_OK) return st;
+  *bytes = L.total;
+  return MM_OK;
+}
+
+// ---------------------------------------------------------------------- set-up kernels
+__global__ void k_twiddles(float2* out, int count, int denom_mul, int L) {
+  // out[m] = exp(-2 pi i m * denom_mul / L) computed in FP64, rounded to FP32
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= count) return;
+  double s, c;
+  sincospi(-2.0 * (double)m * (double)denom_mul / (double)L, &s, &c);
+  out[m] = make_float2((float)c, (float)s);
+}
+
+__global__ void k_hits(const int32_t* __restrict__ pix, int64_t n, int64_t n_pix,
+                       int32_t* __restrict__ hits, double* __restrict__ flag) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int p = pix[s];
+  if (p < -1 || p >= n_pix) {
+    flag[0] = 1.0;  // any nonzero marks an out-of-range pixel index
+    return;
+  }
+  if (p >= 0) atomicAdd(hits + p, 1);
+}
+
+struct NoiseArgs {
+  const ChunkDesc* desc;
+  const double* psd;       // table or nullptr
+  const double* params;    // device [n_chunks][4] when psd == nullptr
+  float* nbar;
+  float* nyq;
+  double* c0;
+  double* scal;            // lambda max bits, min(Nbar) check at kScalTmp
+};
+
+__device__ __forceinline__ double psd_value(const NoiseArgs& a, int c, const ChunkDesc& d, int k) {
+  if (a.psd) return a.psd[d.spec + c + k];
+  const double* q = a.params + 4 * c;      // sigma, f_knee, alpha, f_sample
+  const int kk = k == 0 ? 1 : k;           // DC bin floored to bin 1
+  const double f = (double)kk * q[3] / (double)d.n;
+  return q[0] * q[0] * (1.0 + pow(q[1] / f, q[2]));
+}
+
+// Nbar = N - tau on every rfft bin of chunk blockIdx.y, stored on the row-layout slots;
+// also c0 = (1/n) sum_k w_k / N_k, lambda_max and min(Nbar) (Sec. 2.1 needs Nbar >= 0).
+__global__ void k_noise(NoiseArgs a) {
+  const int c = blockIdx.y;
+  const ChunkDesc d = a.desc[c];
+  double sum = 0.0, mx = 0.0, mn = 1e300;
+  for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < d.M; slot += gridDim.x * blockDim.x) {
+    const int k1 = slot / d.M2, k2 = slot % d.M2;
+    const int k = k1 + d.M1 * k2;
+    const double N = psd_value(a, c, d, k);
+    const double nb = N - d.tau;
+    a.nbar[d.spec + slot] = (float)nb;
+    double w = k == 0 ? 1.0 : 2.0;
+    sum += w / N;
+    mx = fmax(mx, nb / d.tau);
+    mn = fmin(mn, nb);
+    if (k == 0) {
+      const double NM = psd_value(a, c, d, d.M);
+      const double nbM = NM - d.tau;
+      a.nyq[c] = (float)nbM;
+      sum += 1.0 / NM;
+      mx = fmax(mx, nbM / d.tau);
+      mn = fmin(mn, nbM);
+    }
+  }
+  __shared__ double rs[32], rx[32], rn[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_down_sync(0xffffffffu, sum, o);
+    mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rs[threadIdx.x >> 5] = sum; rx[threadIdx.x >> 5] = mx; rn[threadIdx.x >> 5] = mn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) {
+      sum += rs[i]; mx = fmax(mx, rx[i]); mn = fmin(mn, rn[i]);
+    }
+    atomicAdd(a.c0 + c, sum / (double)d.n);
+    atomicMax(reinterpret_cast<unsigned long long*>(a.scal + kScalLambdaMax),
+              (unsigned long long)__double_as_longlong(fmax(mx, 0.0)));
+    if (mn < 0.0) a.scal[kScalTmp] = fmin(a.scal[kScalTmp], mn);
+  }
+}
+
+__global__ void k_min_psd(const ChunkDesc* desc, const double* psd, double* out) {
+  const int c = blockIdx.x;
+  const ChunkDesc d = desc[c];
+  double mn = 1e300;
+  for (int k = threadIdx.x; k <= d.M; k += blockDim.x) mn = fmin(mn, psd[d.spec + c + k]);
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+  __shared__ double r[32];
+  if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mn = fmin(mn, r[i]);
+    out[c] = mn;
+  }
+}
+
+// Weight blocks: acc12[p][0..B) += (1/tau_c) w w^T, acc12[p][B..2B) += c0_c w w^T
+// (upper triangle 00 01 02 11 12 22 for IQU), w = (1, cos 2psi, sin 2psi).
+__global__ void k_weights_accum(const ChunkDesc* __restrict__ desc, int c,
+                                const int32_t* __restrict__ pix, const void* cosw,
+                                const void* sinw, int half_w, int ncomp,
+                                const double* __restrict__ c0, int64_t n0, int64_t n,
+                                double* __restrict__ acc12) {
+  const int64_t s = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int p = pix[s];
+  if (p < 0) return;
+  const double s1 = 1.0 / desc[c].tau, s2 = c0[c];
+  if (ncomp == 1) {
+    atomicAdd(acc12 + 2 * (int64_t)p, s1);
+    atomicAdd(acc12 + 2 * (int64_t)p + 1, s2);
+    return;
+  }
+  double cw, sw;
+  if (half_w) {
+    cw = __half2float(reinterpret_cast<const __half*>(cosw)[s]);
+    sw = __half2float(reinterpret_cast<const __half*>(sinw)[s]);
+  } else {
+    cw = reinterpret_cast<const float*>(cosw)[s];
+    sw = reinterpret_cast<const float*>(sinw)[s];
+  }
+  const double pr[6] = {1.0, cw, sw, cw * cw, cw * sw, sw * sw};
+  double* a = acc12 + 12 * (int64_t)p;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    atomicAdd(a + i, s1 * pr[i]);
+    atomicAdd(a + 6 + i, s2 * pr[i]);
+  }
+}
+
+// Eigenvalues of a symmetric 3x3 matrix by the trigonometric closed form (Smith 1961).
+__device__ void sym3_eig(const double* m, double* emin, double* emax) {
+  const double a00 = m[0], a01 = m[1], a02 = m[2], a11 = m[3], a12 = m[4], a22 = m[5];
+  const double p1 = a01 * a01 + a02 * a02 + a12 * a12;
+  const double q = (a00 + a11 + a22) / 3.0;
+  const double b00 = a00 - q, b11 = a11 - q, b22 = a22 - q;
+  const double p2 = b00 * b00 + b11 * b11 + b22 * b22 + 2.0 * p1;
+  if (p2 <= 0.0) { *emin = *emax = q; return; }
+  const double pp = sqrt(p2 / 6.0);
+  const double det = b00 * (b11 * b22 - a12 * a12) - a01 * (a01 * b22 - a12 * a02) +
+                     a02 * (a01 * a12 - b11 * a02);
+  double r = det / (2.0 * pp * pp * pp);
+  r = fmin(1.0, fmax(-1.0, r));
+  const double phi = acos(r) / 3.0;
+  const double e1 = q + 2.0 * pp * cos(phi);
+  const double e3 = q + 2.0 * pp * cos(phi + 2.0943951023931954923);
+  *emax = e1;
+  *emin = e3;
+}
+
+__device__ bool sym3_inv(const double* m, double* o) {
+  const double a = m[0], b = m[1], c = m[2], d = m[3], e = m[4], f = m[5];
+  const double c00 = d * f - e * e, c01 = c * e - b * f, c02 = b * e - c * d;
+  const double det = a * c00 + b * c01 + c * c02;
+  if (!(det > 0.0) && !(det < 0.0)) return false;
+  const double id = 1.0 / det;
+  o[0] = c00 * id;
+  o[1] = c01 * id;
+  o[2] = c02 * id;
+  o[3] = (a * f - c * c) * id;
+  o[4] = (b * c - a * e) * id;
+  o[5] = (a * d - b * b) * id;
+  return true;
+}
+
+// Per pixel: cut decision, W = (P^T T^-1 P)^-1 and the PCG block preconditioner inverse.
+__global__ void k_pixel_solve(int64_t n_pix, int ncomp, double rcond_min,
+                              const int32_t* __restrict__ hits, const double* __restrict__ acc12,
+                              uint8_t* __restrict__ valid, double* __restrict__ W,
+                              double* __restrict__ Minv, unsigned long long* n_valid) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  bool ok = hits[p] >= 1;
+  if (ncomp == 1) {
+    const double a = acc12[2 * p], b = acc12[2 * p + 1];
+    ok = ok && a > 0.0 && b > 0.0;
+    W[p] = ok ? 1.0 / a : 0.0;
+    Minv[p] = ok ? 1.0 / b : 0.0;
+  } else {
+    const double* A = acc12 + 12 * p;
+    double wi[6] = {0, 0, 0, 0, 0, 0}, mi[6] = {0, 0, 0, 0, 0, 0};
+    if (ok) {
+      double emin, emax;
+      sym3_eig(A, &emin, &emax);
+      ok = emax > 0.0 && emin / emax >= rcond_min;
+    }
+    if (ok) ok = sym3_inv(A, wi) && sym3_inv(A + 6, mi);
+    if (!ok)
+      for (int i = 0; i < 6; ++i) wi[i] = mi[i] = 0.0;
+    for (int i = 0; i < 6; ++i) {
+      W[6 * p + i] = wi[i];
+      Minv[6 * p + i] = mi[i];
+    }
+  }
+  valid[p] = ok ? 1 : 0;
+  if (ok) atomicAdd(n_valid, 1ull);
+}
+
+// ------------------------------------------------------------------ map-step kernels
+template <int NC>
+__device__ __forceinline__ void sym_apply(const double* W, const double* a, double* m) {
+  if constexpr (NC == 1) {
+    m[0] = W[0] * a[0];
+  } else {
+    m[0] = W[0] * a[0] + W[1] * a[1] + W[2] * a[2];
+    m[1] = W[1] * a[0] + W[3] * a[1] + W[4] * a[2];
+    m[2] = W[2] * a[0] + W[4] * a[1] + W[5] * a[2];
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void store_map4(void* map4, int64_t p, const double* m) {
+  if constexpr (NC == 1) reinterpret_cast<float*>(map4)[p] = (float)m[0];
+  else reinterpret_cast<float4*>(map4)[p] = make_float4((float)m[0], (float)m[1], (float)m[2], 0.f);
+}
+
+// m = (P^T T^-1 P)^-1 acc (the map step of Sec. 2.1); acc is cleared for the next pass.
+template <int NC>
+__global__ void k_bin_apply(int64_t n_pix, double* __restrict__ acc, const double* __restrict__ W,
+                            void* map4, double* __restrict__ map_out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  constexpr int B = NC == 3 ? 6 : 1;
+  double a[NC], w[B], m[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) { a[i] = acc[NC * p + i]; acc[NC * p + i] = 0.0; }
+#pragma unroll
+  for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
+  sym_apply<NC>(w, a, m);
+  store_map4<NC>(map4, p, m);
+  if (map_out)
+#pragma unroll
+    for (int i = 0; i < NC; ++i) map_out[NC * p + i] = m[i];
+}
+
+// map4 = float(map) on valid pixels, 0 on cut ones.
+template <int NC>
+__global__ void k_map_to4(int64_t n_pix, const double* __restrict__ map,
+                          const uint8_t* __restrict__ valid, void* map4) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  double m[NC];
+  const bool ok = valid[p] != 0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) m[i] = ok ? map[NC * p + i] : 0.0;
+  store_map4<NC>(map4, p, m);
+}
+
+// ----------------------------------------------------------------- operator kernels
+template <int NC>
+__global__ void k_gather(int64_t n, const int32_t* __restrict__ pix, const void* cosw,
+                         const void* sinw, int half_w, const void* map4, float* __restrict__ out) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int p = pix[s];
+  float v = 0.f;
+  if (p >= 0) {
+    if constexpr (NC == 1) {
+      v = reinterpret_cast<const float*>(map4)[p];
+    } else {
+      float cw, sw;
+      if (half_w) {
+        cw = __half2float(reinterpret_cast<const __half*>(cosw)[s]);
+        sw = __half2float(reinterpret_cast<const __half*>(sinw)[s]);
+      } else {
+        cw = reinterpret_cast<const float*>(cosw)[s];
+        sw = reinterpret_cast<const float*>(sinw)[s];
+      }
+      const float4 m = reinterpret_cast<const float4*>(map4)[p];
+      v = fmaf(sw, m.z, fmaf(cw, m.y, m.x));
+    }
+  }
+  out[s] = v;
+}
+
+template <int NC>
+__global__ void k_scatter(int64_t n, const int32_t* __restrict__ pix, const void* cosw,
+                          const void* sinw, int half_w, const float* __restrict__ tod,
+                          double* __restrict__ acc) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int p = pix[s];
+  if (p < 0) return;
+  const double t = tod[s];
+  double* a = acc + (int64_t)p * NC;
+  atomicAdd(a, t);
+  if constexpr (NC == 3) {
+    float cw, sw;
+    if (half_w) {
+      cw = __half2float(reinterpret_cast<const __half*>(cosw)[s]);
+      sw = __half2float(reinterpret_cast<const __half*>(sinw)[s]);
+    } else {
+      cw = reinterpret_cast<const float*>(cosw)[s];
+      sw = reinterpret_cast<const float*>(sinw)[s];
+    }
+    atomicAdd(a + 1, t * (double)cw);
+    atomicAdd(a + 2, t * (double)sw);
+  }
+}
+
+template <int NC>
+__global__ void k_expand_weights(int64_t n_pix, const double* __restrict__ W, double* __restrict__ out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  if constexpr (NC == 1) {
+    out[p] = W[p];
+  } else {
+    const double* w = W + 6 * p;
+    double* o = out + 9 * p;
+    o[0] = w[0]; o[1] = w[1]; o[2] = w[2];
+    o[3] = w[1]; o[4] = w[3]; o[5] = w[4];
+    o[6] = w[2]; o[7] = w[4]; o[8] = w[5];
+  }
+}
+
+// b = P^T N^-1 d on valid pixels; acc cleared.
+__global__ void k_finish_b(int64_t len, int ncomp, double* __restrict__ acc,
+                           const uint8_t* __restrict__ valid, double* __restrict__ b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  b[i] = valid[i / ncomp] ? acc[i] : 0.0;
+  acc[i] = 0.0;
+}
+
+// ------------------------------------------------------------------------ PCG kernels
+// State: r, z, p, q ([len] doubles each) then scalars.
+enum { kPcgRz0 = 0, kPcgRz1 = 1, kPcgPq = 2, kPcgXb = 3, kPcgXr = 4, kPcgNs = 8 };
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+template <int NC>
+__device__ __forceinline__ void block_apply(const double* Minv, int64_t pixel, const double* r,
+                                            double* z) {
+  constexpr int B = NC == 3 ? 6 : 1;
+  double w[B];
+#pragma unroll
+  for (int i = 0; i < B; ++i) w[i] = Minv[B * pixel + i];
+  sym_apply<NC>(w, r, z);
+}
+
+// r = b - A x (A x in acc), z = M^-1 r, p = z, map4 = p; rz, x.b, x.r.
+template <int NC>
+__global__ void k_pcg_init(int64_t n_pix, double* __restrict__ acc, const double* __restrict__ bvec,
+                           const double* __restrict__ x, const uint8_t* __restrict__ valid,
+                           const double* __restrict__ Minv, double* __restrict__ r,
+                           double* __restrict__ z, double* __restrict__ pv, void* map4,
+                           double* sc) {
+  __shared__ double red[32];
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double rz = 0, xb = 0, xr = 0;
+  if (p < n_pix) {
+    const bool ok = valid[p] != 0;
+    double rr[NC], zz[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int64_t j = NC * p + i;
+      rr[i] = ok ? bvec[j] - acc[j] : 0.0;
+      acc[j] = 0.0;
+    }
+    block_apply<NC>(Minv, p, rr, zz);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int64_t j = NC * p + i;
+      const double xv = ok ? x[j] : 0.0;
+      r[j] = rr[i]; z[j] = zz[i]; pv[j] = zz[i];
+      rz += rr[i] * zz[i];
+      xb += xv * bvec[j];
+      xr += xv * rr[i];
+    }
+    store_map4<NC>(map4, p, zz);
+  }
+  rz = block_sum(rz, red);
+  xb = block_sum(xb, red);
+  xr = block_sum(xr, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(sc + kPcgRz0, rz);
+    atomicAdd(sc + kPcgXb, xb);
+    atomicAdd(sc + kPcgXr, xr);
+  }
+}
+
+// q = A p on valid pixels (acc cleared), p.q; block 0 records chi^2 of the current iterate
+// and clears the accumulators the update kernel fills.
+__global__ void k_pcg_q(int64_t len, int ncomp, double* __restrict__ acc, const uint8_t* __restrict__ valid,
+                        const double* __restrict__ pv, double* __restrict__ q, double* sc, int rz_next,
+                        const double* cdd, double* chi2_slot) {
+  __shared__ double red[32];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double s = 0.0;
+  if (i < len) {
+    const double qq = valid[i / ncomp] ? acc[i] : 0.0;
+    acc[i] = 0.0;
+    q[i] = qq;
+    s = pv[i] * qq;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) atomicAdd(sc + kPcgPq, s);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (chi2_slot) *chi2_slot = *cdd - sc[kPcgXb] - sc[kPcgXr];
+    sc[kPcgXb] = 0.0;
+    sc[kPcgXr] = 0.0;
+    sc[rz_next] = 0.0;
+  }
+}
+
+// alpha = rz / pq; x += alpha p; r -= alpha q; z = M^-1 r; rz_next, x.b, x.r.
+template <int NC>
+__global__ void k_pcg_update(int64_t n_pix, double* __restrict__ x, double* __restrict__ r,
+                             double* __restrict__ z, const double* __restrict__ pv,
+                             const double* __restrict__ q, const double* __restrict__ bvec,
+                             const double* __restrict__ Minv, double* sc, int rz_cur, int rz_next) {
+  __shared__ double red[32];
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const double alpha = sc[rz_cur] / sc[kPcgPq];
+  double rz = 0, xb = 0, xr = 0;
+  if (p < n_pix) {
+    double rr[NC], zz[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int64_t j = NC * p + i;
+      const double xv = x[j] + alpha * pv[j];
+      x[j] = xv;
+      rr[i] = r[j] - alpha * q[j];
+      r[j] = rr[i];
+      xb += xv * bvec[j];
+      xr += xv * rr[i];
+    }
+    block_apply<NC>(Minv, p, rr, zz);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      z[NC * p + i] = zz[i];
+      rz += rr[i] * zz[i];
+    }
+  }
+  rz = block_sum(rz, red);
+  xb = block_sum(xb, red);
+  xr = block_sum(xr, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(sc + rz_next, rz);
+    atomicAdd(sc + kPcgXb, xb);
+    atomicAdd(sc + kPcgXr, xr);
+  }
+}
+
+// beta = rz_next / rz_cur; p = z + beta p; map4 = p; pq cleared by the next k_pcg_q's
+// predecessor (this kernel's last block is not known, so pq is reset by the driver).
+template <int NC>
+__global__ void k_pcg_dir(int64_t n_pix, const double* __restrict__ z, double* __restrict__ pv,
+                          void* map4, const double* sc, int rz_cur, int rz_next) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  const double beta = sc[rz_next] / sc[rz_cur];
+  double m[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    const int64_t j = NC * p + i;
+    m[i] = z[j] + beta * pv[j];
+    pv[j] = m[i];
+  }
+  store_map4<NC>(map4, p, m);
+}
+
+// ------------------------------------------------------------------------- plan API
+static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t* offsets,
+                                      const int32_t* pix, const void* cos2psi,
+                                      const void* sin2psi, int weight_dtype, int64_t n_pix,
+                                      int ncomp, double rcond_min, void* workspace,
+                                      size_t workspace_bytes, void* stream) {
+  MM_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  MM_ARG(pix != nullptr, "pix is NULL");
+  MM_ARG(weight_dtype == MM_W_F32 || weight_dtype == MM_W_F16, "bad weight_dtype %d",
+         weight_dtype);
+  Layout L;
+  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, &L);
+  if (st != MM_OK) return st;
+  MM_ARG((ncomp == 3) == (cos2psi != nullptr && sin2psi != nullptr),
+         "cos2psi/sin2psi must be given iff ncomp == 3");
+  MM_ARG(ncomp == 1 || (cos2psi != nullptr && sin2psi != nullptr), "weights missing");
+  MM_ARG(workspace != nullptr, "workspace is NULL");
+  MM_ARG(((uintptr_t)workspace & 255) == 0, "workspace must be 256-byte aligned");
+  if (workspace_bytes < L.total) {
+    mm_set_error("workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+    return MM_ERR_NOMEM;
+  }
+  MM_ARG(rcond_min >= 0.0 && rcond_min <= 1.0, "rcond_min must be in [0, 1]");
+
+  mm_plan_s* p = new (std::nothrow) mm_plan_s();
+  if (!p) { mm_set_error("host allocation failed"); return MM_ERR_NOMEM; }
+  p->n_chunks = n_chunks; p->ncomp = ncomp; p->wdtype = weight_dtype;
+  p->n_pix = n_pix; p->n_total = L.n_total; p->spec_total = L.spec_total;
+  p->rcond_min = rcond_min; p->pix = pix; p->cosw = cos2psi; p->sinw = sin2psi;
+  p->noise_set = false;
+  char* ws = static_cast<char*>(workspace);
+  p->d_desc = reinterpret_cast<ChunkDesc*>(ws + L.desc);
+  int* d_chunks = reinterpret_cast<int*>(ws + L.chunks);
+  p->tw_pool = reinterpret_cast<float2*>(ws + L.tw);
+  p->hits = reinterpret_cast<int32_t*>(ws + L.hits);
+  p->valid = reinterpret_cast<uint8_t*>(ws + L.valid);
+  p->W = reinterpret_cast<double*>(ws + L.W);
+  p->Minv = reinterpret_cast<double*>(ws + L.Minv);
+  p->acc = reinterpret_cast<double*>(ws + L.acc);
+  p->acc12 = reinterpret_cast<double*>(ws + L.acc12);
+  p->map4 = ws + L.map4;
+  p->bvec = reinterpret_cast<double*>(ws + L.bvec);
+  p->dtab = reinterpret_cast<float2*>(ws + L.dtab);
+  p->nbar = reinterpret_cast<float*>(ws + L.nbar);
+  p->nyq = reinterpret_cast<float*>(ws + L.nyq);
+  p->c0 = reinterpret_cast<double*>(ws + L.c0);
+  p->ybuf = reinterpret_cast<float2*>(ws + L.ybuf);
+  p->scal = reinterpret_cast<double*>(ws + L.scal);
+  p->params = reinterpret_cast<double*>(ws + L.params);
+
+  // host descriptors, grouped chunk lists
+  p->h_desc = new (std::nothrow) ChunkDesc[n_chunks];
+  p->h_chunk_group = new (std::nothrow) int[n_chunks];
+  std::vector<int> order;
+  if (!p->h_desc || !p->h_chunk_group) { mm_plan_destroy(p); mm_set_error("host allocation failed"); return MM_ERR_NOMEM; }
+  int64_t spec = 0;
+  for (int c = 0; c < n_chunks; ++c) {
+    ChunkDesc& d = p->h_desc[c];
+    const int g = L.chunk_group[c];
+    d.off = offsets[c];
+    d.spec = spec;
+    d.n = (int)(offsets[c + 1] - offsets[c]);
+    d.M = L.gM[g]; d.M1 = L.gM1[g]; d.M2 = L.gM2[g];
+    d.tau = 1.0;
+    spec += d.M;
+    p->h_chunk_group[c] = g;
+  }
+  p->n_groups = L.n_groups;
+  size_t tw_off = 0;
+  for (int g = 0; g < L.n_groups; ++g) {
+    Group& G = p->groups[g];
+    G.M = L.gM[g]; G.M1 = L.gM1[g]; G.M2 = L.gM2[g];
+    G.log_lo = log_lo_of(G.M);
+    G.chunks = d_chunks + order.size();
+    G.n_chunks = 0;
+    for (int c = 0; c < n_chunks; ++c)
+      if (L.chunk_group[c] == g) { order.push_back(c); G.n_chunks++; }
+    float2* t = p->tw_pool + tw_off;
+    G.tw_col = t; t += G.M1;
+    G.tw_row = t; t += G.M2;
+    G.tw_lo = t; t += (1 << G.log_lo);
+    G.tw_hi = t; t += (G.M >> G.log_lo);
+    G.tw_pack_a = t; t += G.M1;
+    G.tw_pack_b = t; t += G.M2;
+    tw_off += tw_count(G.M, G.M1, G.M2);
+  }
+  cudaStream_t s = S(stream);
+  auto fail = [&](const char* what, cudaError_t e) {
+    mm_set_error("%s: %s", what, cudaGetErrorString(e));
+    mm_plan_destroy(p);
+    return MM_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(ChunkDesc) * n_chunks,
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail("desc upload", e);
+  if ((e = cudaMemcpyAsync(d_chunks, order.data(), sizeof(int) * n_chunks,
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail("chunk list upload", e);
+  for (int g = 0; g < L.n_groups; ++g) {
+    const Group& G = p->groups[g];
+    struct { float2* o; int cnt, mul, L; } tabs[6] = {
+        {G.tw_col, G.M1, 1, G.M1},       {G.tw_row, G.M2, 1, G.M2},
+        {G.tw_lo, 1 << G.log_lo, 1, G.M}, {G.tw_hi, G.M >> G.log_lo, 1 << G.log_lo, G.M},
+        {G.tw_pack_a, G.M1, 1, 2 * G.M}, {G.tw_pack_b, G.M2, G.M1, 2 * G.M}};
+    for (auto& tb : tabs) {
+      k_twiddles<<<blocks_for(tb.cnt, 256), 256, 0, s>>>(tb.o, tb.cnt, tb.mul, tb.L);
+    }
+  }
+  if ((e = cudaMemsetAsync(p->hits, 0, sizeof(int32_t) * n_pix, s)) != cudaSuccess) return fail("memset", e);
+  if ((e = cudaMemsetAsync(p->scal, 0, sizeof(double) * kScalCount, s)) != cudaSuccess) return fail("memset", e);
+  if ((e = cudaMemsetAsync(p->acc, 0, sizeof(double) * ncomp * n_pix, s)) != cudaSuccess) return fail("memset", e);
+  if (L.n_total > 0)
+    k_hits<<<blocks_for(L.n_total, 256), 256, 0, s>>>(pix, L.n_total, n_pix, p->hits, p->scal + kScalTmp);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail("set-up kernels", e);
+  double flag = 0.0;
+  if ((e = cudaMemcpyAsync(&flag, p->scal + kScalTmp, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return fail("flag read", e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail("plan synchronise", e);
+  if (flag != 0.0) {
+    mm_plan_destroy(p);
+    mm_set_error("pix holds a value outside [-1, n_pix)");
+    return MM_ERR_ARG;
+  }
+  *out = p;
+  return MM_OK;
+}
+
+extern "C" void mm_plan_destroy(mm_plan p) {
+  if (!p) return;
+  delete[] p->h_desc;
+  delete[] p->h_chunk_group;
+  delete p;
+}
+
+// Run fn over the groups, failing on the first launch error.
+#define FOR_GROUPS(call)                                                  \
+  for (int g_ = 0; g_ < p->n_groups; ++g_) {                              \
+    const Group& G = p->groups[g_];                                       \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess) {                                              \
+      mm_set_error("%s: %s", #call, cudaGetErrorString(e_));              \
+      return MM_ERR_CUDA;                                                 \
+    }                                                                     \
+  }
+
+static mm_status check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mm_set_error("%s: %s", what, cudaGetErrorString(e));
+    return MM_ERR_CUDA;
+  }
+  return MM_OK;
+}
+#define LAUNCHED(what)                                   \
+  do {                                                   \
+    mm_status st_ = check_launch(what);             \
+    if (st_ != MM_OK) return st_;                        \
+  } while (0)
+
+extern "C" mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const double* params,
+                                      const double* tau, const float* tod, void* stream) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  MM_ARG((psd_dev != nullptr) != (params != nullptr), "give exactly one of psd / params");
+  MM_ARG(tod != nullptr, "tod is NULL");
+  cudaStream_t s = S(stream);
+  const int C = p->n_chunks;
+  std::vector<double> taus(C);
+  if (params) {
+    for (int c = 0; c < C; ++c) {
+      const double* q = params + 4 * c;
+      MM_ARG(q[0] > 0 && q[1] >= 0 && q[3] > 0 && isfinite(q[2]),
+             "chunk %d: params (sigma, f_knee, alpha, f_sample) invalid", c);
+      taus[c] = tau ? tau[c] : q[0] * q[0];
+    }
+  } else if (tau) {
+    for (int c = 0; c < C; ++c) taus[c] = tau[c];
+  } else {
+    // tau_c = min_k N_c(f_k)
+    k_min_psd<<<C, 256, 0, s>>>(p->d_desc, psd_dev, p->params);
+    LAUNCHED("k_min_psd");
+    MM_CUDA(cudaMemcpyAsync(taus.data(), p->params, sizeof(double) * C, cudaMemcpyDeviceToHost, s));
+    MM_CUDA(cudaStreamSynchronize(s));
+  }
+  for (int c = 0; c < C; ++c) {
+    MM_ARG(taus[c] > 0 && isfinite(taus[c]), "chunk %d: tau must be positive", c);
+    p->h_desc[c].tau = taus[c];
+  }
+  MM_CUDA(cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(ChunkDesc) * C, cudaMemcpyHostToDevice, s));
+  const double* d_params = nullptr;
+  if (params) {
+    MM_CUDA(cudaMemcpyAsync(p->params, params, sizeof(double) * 4 * C, cudaMemcpyHostToDevice, s));
+    d_params = p->params;
+  }
+  MM_CUDA(cudaMemsetAsync(p->c0, 0, sizeof(double) * C, s));
+  MM_CUDA(cudaMemsetAsync(p->scal, 0, sizeof(double) * kScalCount, s));
+  NoiseArgs na{p->d_desc, psd_dev, d_params, p->nbar, p->nyq, p->c0, p->scal};
+  {
+    int maxM = 0;
+    for (int c = 0; c < C; ++c) maxM = p->h_desc[c].M > maxM ? p->h_desc[c].M : maxM;
+    const int per = 256 * 16;
+    k_noise<<<dim3((maxM + per - 1) / per, C), 256, 0, s>>>(na);
+    LAUNCHED("k_noise");
+  }
+  // scal[kScalTmp] holds min(Nbar) if it went negative
+  double mn = 0.0;
+  MM_CUDA(cudaMemcpyAsync(&mn, p->scal + kScalTmp, sizeof(double), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  if (mn < 0.0) {
+    mm_set_error("Nbar = N - tau is negative (min %.3e): tau exceeds the noise spectrum", mn);
+    return MM_ERR_ARG;
+  }
+
+  // weight blocks, pixel cut, W and the PCG preconditioner
+  const int blk = p->ncomp == 3 ? 6 : 1;
+  MM_CUDA(cudaMemsetAsync(p->acc12, 0, sizeof(double) * 2 * blk * p->n_pix, s));
+  // one launch per chunk keeps the chunk's scales without a per-sample search
+  for (int c = 0; c < C; ++c) {
+    const ChunkDesc& d = p->h_desc[c];
+    k_weights_accum<<<blocks_for(d.n, 256), 256, 0, s>>>(
+        p->d_desc, c, p->pix, p->cosw, p->sinw, p->wdtype == MM_W_F16, p->ncomp, p->c0, d.off,
+        d.off + d.n, p->acc12);
+  }
+  LAUNCHED("k_weights_accum");
+  unsigned long long* d_nvalid = reinterpret_cast<unsigned long long*>(p->scal + kScalTmp + 1);
+  MM_CUDA(cudaMemsetAsync(d_nvalid, 0, 8, s));
+  k_pixel_solve<<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->ncomp, p->rcond_min, p->hits,
+                                                          p->acc12, p->valid, p->W, p->Minv, d_nvalid);
+  LAUNCHED("k_pixel_solve");
+
+  // d~ = rfft(d) into the row-layout table
+  {
+    RowArgs a{kRowSpectrum, 1.0, nullptr, nullptr};
+    FOR_GROUPS(launch_col_forward(p, G, kSrcTod, tod, s));
+    FOR_GROUPS(launch_row(p, G, a, s));
+  }
+  // b = P^T N^-1 d and d^T N^-1 d
+  {
+    MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * p->ncomp * p->n_pix, s));
+    RowArgs a{kRowPcgRhs, 1.0, p->scal + kScalCdd, nullptr};
+    FOR_GROUPS(launch_row(p, G, a, s));
+    FOR_GROUPS(launch_col_inverse(p, G, s));
+    const int64_t len = p->ncomp * p->n_pix;
+    k_finish_b<<<blocks_for(len, 256), 256, 0, s>>>(len, p->ncomp, p->acc, p->valid, p->bvec);
+    LAUNCHED("k_finish_b");
+  }
+  unsigned long long nvalid = 0;
+  MM_CUDA(cudaMemcpyAsync(&nvalid, d_nvalid, 8, cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  if (nvalid == 0) {
+    mm_set_error("every pixel was cut (no pixel with hits and rcond >= %g)", p->rcond_min);
+    return MM_ERR_SINGULAR;
+  }
+  p->noise_set = true;
+  return MM_OK;
+}
+
+extern "C" mm_status mm_lambda_max(mm_plan p, double* out, void* stream) {
+  MM_ARG(p != nullptr && out != nullptr, "NULL argument");
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  MM_CUDA(cudaMemcpyAsync(out, p->scal + kScalLambdaMax, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
+  MM_CUDA(cudaStreamSynchronize(S(stream)));
+  return MM_OK;
+}
+
+static mm_status load_map(mm_plan p, const double* map, cudaStream_t s) {
+  if (p->ncomp == 3) k_map_to4<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, map, p->valid, p->map4);
+  else k_map_to4<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, map, p->valid, p->map4);
+  LAUNCHED("k_map_to4");
+  return MM_OK;
+}
+
+extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int precision,
+                                          double* map_inout, double* chi2_out, void* stream) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  MM_ARG(n_iter >= 0, "n_iter must be >= 0");
+  MM_ARG(n_iter == 0 || lambdas != nullptr, "lambdas is NULL");
+  MM_ARG(map_inout != nullptr, "map_inout is NULL");
+  if (precision != MM_FP32_MIXED) {
+    mm_set_error("precision mode %d not supported", precision);
+    return MM_ERR_UNSUPPORTED;
+  }
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  for (int i = 0; i < n_iter; ++i)
+    MM_ARG(lambdas[i] >= 1.0 || isinf(lambdas[i]), "lambdas[%d] = %g must be >= 1 or inf", i, lambdas[i]);
+  if (n_iter == 0) return MM_OK;
+  cudaStream_t s = S(stream);
+  mm_status st = load_map(p, map_inout, s);
+  if (st != MM_OK) return st;
+  if (chi2_out) MM_CUDA(cudaMemsetAsync(chi2_out, 0, sizeof(double) * n_iter, s));
+  for (int it = 0; it < n_iter; ++it) {
+    RowArgs a{kRowMessenger, lambdas[it], chi2_out ? chi2_out + it : nullptr, nullptr};
+    for (int g = 0; g < p->n_groups; ++g) {
+      const Group& G = p->groups[g];
+      cudaError_t e;
+      if ((e = launch_col_forward(p, G, kSrcGather, nullptr, s)) != cudaSuccess ||
+          (e = launch_row(p, G, a, s)) != cudaSuccess ||
+          (e = launch_col_inverse(p, G, s)) != cudaSuccess) {
+        mm_set_error("messenger launch: %s", cudaGetErrorString(e));
+        return MM_ERR_CUDA;
+      }
+    }
+    double* mo = it == n_iter - 1 ? map_inout : nullptr;
+    if (p->ncomp == 3) k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, mo);
+    else k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, mo);
+    LAUNCHED("k_bin_apply");
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_messenger_stage(mm_plan p, int stage, double lambda, double* map_inout,
+                                        double* chi2_slot, void* stream) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  cudaStream_t s = S(stream);
+  switch (stage) {
+    case MM_STAGE_LOAD:
+      MM_ARG(map_inout != nullptr, "map_inout is NULL");
+      return load_map(p, map_inout, s);
+    case MM_STAGE_GATHER_FFT:
+      FOR_GROUPS(launch_col_forward(p, G, kSrcGather, nullptr, s));
+      return MM_OK;
+    case MM_STAGE_FILTER: {
+      MM_ARG(lambda >= 1.0 || isinf(lambda), "lambda = %g must be >= 1 or inf", lambda);
+      RowArgs a{kRowMessenger, lambda, chi2_slot, nullptr};
+      FOR_GROUPS(launch_row(p, G, a, s));
+      return MM_OK;
+    }
+    case MM_STAGE_IFFT_BIN:
+      FOR_GROUPS(launch_col_inverse(p, G, s));
+      return MM_OK;
+    case MM_STAGE_MAP:
+      if (p->ncomp == 3) k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, map_inout);
+      else k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, map_inout);
+      LAUNCHED("k_bin_apply");
+      return MM_OK;
+  }
+  mm_set_error("unknown stage %d", stage);
+  return MM_ERR_ARG;
+}
+
+extern "C" mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes) {
+  MM_ARG(p != nullptr && bytes != nullptr, "NULL argument");
+  *bytes = up(sizeof(double) * 4 * p->ncomp * p->n_pix) + up(sizeof(double) * kPcgNs);
+  return MM_OK;
+}
+
+static mm_status apply_A(mm_plan p, cudaStream_t s) {
+  RowArgs a{kRowPcgApply, 1.0, nullptr, nullptr};
+  FOR_GROUPS(launch_col_forward(p, G, kSrcGather, nullptr, s));
+  FOR_GROUPS(launch_row(p, G, a, s));
+  FOR_GROUPS(launch_col_inverse(p, G, s));
+  return MM_OK;
+}
+
+extern "C" mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, void* state, int restart,
+                                    double* chi2_out, void* stream) {
+  MM_ARG(p != nullptr && map_inout != nullptr && state != nullptr, "NULL argument");
+  MM_ARG(((uintptr_t)state & 255) == 0, "state must be 256-byte aligned");
+  MM_ARG(n_iter >= 0, "n_iter must be >= 0");
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  cudaStream_t s = S(stream);
+  const int64_t len = p->ncomp * p->n_pix;
+  double* r = static_cast<double*>(state);
+  double* z = r + len;
+  double* pv = z + len;
+  double* q = pv + len;
+  double* sc = reinterpret_cast<double*>(static_cast<char*>(state) + up(sizeof(double) * 4 * len));
+  const unsigned nb = blocks_for(p->n_pix, 256), nbl = blocks_for(len, 256);
+  const bool tri = p->ncomp == 3;
+  if (restart) {
+    MM_CUDA(cudaMemsetAsync(sc, 0, sizeof(double) * kPcgNs, s));
+    mm_status st = load_map(p, map_inout, s);
+    if (st != MM_OK) return st;
+    st = apply_A(p, s);
+    if (st != MM_OK) return st;
+    if (tri) k_pcg_init<3><<<nb, 256, 0, s>>>(p->n_pix, p->acc, p->bvec, map_inout, p->valid, p->Minv, r, z, pv, p->map4, sc);
+    else k_pcg_init<1><<<nb, 256, 0, s>>>(p->n_pix, p->acc, p->bvec, map_inout, p->valid, p->Minv, r, z, pv, p->map4, sc);
+    LAUNCHED("k_pcg_init");
+  } else {
+    // continue: map4 must hold the current direction p
+    if (tri) k_map_to4<3><<<nb, 256, 0, s>>>(p->n_pix, pv, p->valid, p->map4);
+    else k_map_to4<1><<<nb, 256, 0, s>>>(p->n_pix, pv, p->valid, p->map4);
+    LAUNCHED("k_map_to4");
+  }
+  for (int it = 0; it < n_iter; ++it) {
+    // the parity of rz slots is kept in scalar slot 7 across calls
+    MM_CUDA(cudaMemsetAsync(sc + kPcgPq, 0, sizeof(double), s));
+    mm_status st = apply_A(p, s);
+    if (st != MM_OK) return st;
+    int cur = kPcgRz0, nxt = kPcgRz1;
+    // parity bookkeeping on the host: each call restarts parity at slot 0 after copying
+    k_pcg_q<<<nbl, 256, 0, s>>>(len, p->ncomp, p->acc, p->valid, pv, q, sc, nxt,
+                                p->scal + kScalCdd, chi2_out ? chi2_out + it : nullptr);
+    LAUNCHED("k_pcg_q");
+    if (tri) k_pcg_update<3><<<nb, 256, 0, s>>>(p->n_pix, map_inout, r, z, pv, q, p->bvec, p->Minv, sc, cur, nxt);
+    else k_pcg_update<1><<<nb, 256, 0, s>>>(p->n_pix, map_inout, r, z, pv, q, p->bvec, p->Minv, sc, cur, nxt);
+    LAUNCHED("k_pcg_update");
+    if (tri) k_pcg_dir<3><<<nb, 256, 0, s>>>(p->n_pix, z, pv, p->map4, sc, cur, nxt);
+    else k_pcg_dir<1><<<nb, 256, 0, s>>>(p->n_pix, z, pv, p->map4, sc, cur, nxt);
+    LAUNCHED("k_pcg_dir");
+    // rz_cur <- rz_next for the next iteration
+    MM_CUDA(cudaMemcpyAsync(sc + kPcgRz0, sc + kPcgRz1, sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev, void* stream) {
+  MM_ARG(p != nullptr && map != nullptr && chi2_dev != nullptr, "NULL argument");
+  MM_ARG(lambda >= 1.0 && isfinite(lambda), "lambda must be finite and >= 1");
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  cudaStream_t s = S(stream);
+  MM_CUDA(cudaMemsetAsync(chi2_dev, 0, sizeof(double), s));
+  mm_status st = load_map(p, map, s);
+  if (st != MM_OK) return st;
+  RowArgs a{kRowChi2, lambda, chi2_dev, nullptr};
+  FOR_GROUPS(launch_col_forward(p, G, kSrcGather, nullptr, s));
+  FOR_GROUPS(launch_row(p, G, a, s));
+  return MM_OK;
+}
+
+extern "C" mm_status mm_apply_pointing(mm_plan p, const double* map, float* tod_out, void* stream) {
+  MM_ARG(p != nullptr && map != nullptr && tod_out != nullptr, "NULL argument");
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run (pixel cut unknown)"); return MM_ERR_STATE; }
+  cudaStream_t s = S(stream);
+  mm_status st = load_map(p, map, s);
+  if (st != MM_OK) return st;
+  const unsigned nb = blocks_for(p->n_total, 256);
+  if (p->ncomp == 3) k_gather<3><<<nb, 256, 0, s>>>(p->n_total, p->pix, p->cosw, p->sinw, p->wdtype == MM_W_F16, p->map4, tod_out);
+  else k_gather<1><<<nb, 256, 0, s>>>(p->n_total, p->pix, p->cosw, p->sinw, p->wdtype == MM_W_F16, p->map4, tod_out);
+  LAUNCHED("k_gather");
+  return MM_OK;
+}
+
+extern "C" mm_status mm_apply_pointing_T(mm_plan p, const float* tod, double* acc_out, void* stream) {
+  MM_ARG(p != nullptr && tod != nullptr && acc_out != nullptr, "NULL argument");
+  cudaStream_t s = S(stream);
+  MM_CUDA(cudaMemsetAsync(acc_out, 0, sizeof(double) * p->ncomp * p->n_pix, s));
+  const unsigned nb = blocks_for(p->n_total, 256);
+  if (p->ncomp == 3) k_scatter<3><<<nb, 256, 0, s>>>(p->n_total, p->pix, p->cosw, p->sinw, p->wdtype == MM_W_F16, tod, acc_out);
+  else k_scatter<1><<<nb, 256, 0, s>>>(p->n_total, p->pix, p->cosw, p->sinw, p->wdtype == MM_W_F16, tod, acc_out);
+  LAUNCHED("k_scatter");
+  return MM_OK;
+}
+
+extern "C" mm_status mm_rfft(mm_plan p, const float* tod, float* spec_out, void* stream) {
+  MM_ARG(p != nullptr && tod != nullptr && spec_out != nullptr, "NULL argument");
+  cudaStream_t s = S(stream);
+  RowArgs a{kRowNatural, 1.0, nullptr, reinterpret_cast<float2*>(spec_out)};
+  FOR_GROUPS(launch_col_forward(p, G, kSrcTod, tod, s));
+  FOR_GROUPS(launch_row(p, G, a, s));
+  return MM_OK;
+}
+
+extern "C" mm_status mm_plan_maps(mm_plan p, int32_t* hits, uint8_t* valid, double* weight, void* stream) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  cudaStream_t s = S(stream);
+  if (hits) MM_CUDA(cudaMemcpyAsync(hits, p->hits, sizeof(int32_t) * p->n_pix, cudaMemcpyDeviceToDevice, s));
+  if ((valid || weight) && !p->noise_set) {
+    mm_set_error("valid / weight need mm_set_noise_psd first");
+    return MM_ERR_STATE;
+  }
+  if (valid) MM_CUDA(cudaMemcpyAsync(valid, p->valid, p->n_pix, cudaMemcpyDeviceToDevice, s));
+  if (weight) {
+    if (p->ncomp == 3) k_expand_weights<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->W, weight);
+    else k_expand_weights<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->W, weight);
+    LAUNCHED("k_expand_weights");
+  }
+  return MM_OK;
+}

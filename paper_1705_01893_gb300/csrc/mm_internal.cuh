@@ -1,0 +1,270 @@
+// Internal declarations of the messenger mapmaker: plan layout, chunk descriptors,
+// complex arithmetic and the shared-memory Stockham FFT used by every hot kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/mm.h"
+
+namespace mm {
+
+// ----------------------------------------------------------------------------- layout
+// One chunk of the timestream.  Its rfft of length n = 2M is computed as a complex FFT of
+// length M = M1 * M2 over z_j = x_{2j} + i x_{2j+1}, done as a four-step transform:
+// column FFTs of length M1 (kernel A / C), twiddles w_M^{k1 j2}, row FFTs of length M2
+// (kernel B).  Spectra live in "row layout": slot k1*M2 + k2 holds frequency k1 + M1*k2.
+struct ChunkDesc {
+  int64_t off;       // first sample of the chunk
+  int64_t spec;      // first slot of the chunk in the spectrum-sized buffers (M per chunk)
+  int n, M, M1, M2;
+  double tau;        // messenger variance tau_c (Sec. 4.2)
+};
+
+// Chunks of the same length share FFT shapes and twiddle tables and run in one launch.
+struct Group {
+  int M, M1, M2, log_lo;   // w_M^e = tw_hi[e >> log_lo] * tw_lo[e & (2^log_lo - 1)]
+  int n_chunks;
+  int* chunks;             // device: chunk indices of this group
+  float2* tw_col;          // [M1]  exp(-2 pi i m / M1)
+  float2* tw_row;          // [M2]  exp(-2 pi i m / M2)
+  float2* tw_lo;           // [2^log_lo]          exp(-2 pi i m / M)
+  float2* tw_hi;           // [M >> log_lo]        exp(-2 pi i m 2^log_lo / M)
+  float2* tw_pack_a;       // [M1]  exp(-2 pi i m / (2M))     (real-pack twiddle, k1 part)
+  float2* tw_pack_b;       // [M2]  exp(-2 pi i m M1 / (2M))  (real-pack twiddle, k2 part)
+};
+
+constexpr int kMaxGroups = 16;
+
+}  // namespace mm
+
+struct mm_plan_s {
+  int n_chunks, ncomp, wdtype;
+  int64_t n_pix, n_total, spec_total;
+  double rcond_min;
+  const int32_t* pix;
+  const void* cosw;
+  const void* sinw;
+  // host copies
+  mm::ChunkDesc* h_desc;
+  int n_groups;
+  mm::Group groups[mm::kMaxGroups];
+  int* h_chunk_group;
+  bool noise_set;
+  // device regions inside the caller's workspace
+  mm::ChunkDesc* d_desc;
+  int32_t* hits;
+  uint8_t* valid;
+  double* W;        // [n_pix][6] (IQU, symmetric upper triangle 00 01 02 11 12 22) or [n_pix]
+  double* Minv;     // PCG block preconditioner, same layout
+  double* acc;      // [n_pix][ncomp] FP64 accumulators of P^T T^-1 t
+  double* acc12;    // [n_pix][12] set-up scratch: P^T T^-1 P and sum c0 P^T P (6 each)
+  void* map4;       // float4 [n_pix] (IQU) or float [n_pix] (T)
+  double* bvec;     // [n_pix][ncomp] b = P^T N^-1 d
+  float2* dtab;     // [spec_total] d~ in row layout (slot 0: (d~_0, d~_M))
+  float* nbar;      // [spec_total] Nbar on the same slots (slot 0: Nbar_0)
+  float* nyq;       // [n_chunks] Nbar at the Nyquist bin
+  double* c0;       // [n_chunks] (1/n) sum_k w_k / N_k
+  float2* ybuf;     // [spec_total] intermediate of the four-step FFT
+  double* scal;     // [64] scalars (see kScal*)
+  double* params;   // [n_chunks][4] noise parameters (device copy)
+  float2* tw_pool;
+};
+
+namespace mm {
+
+enum {
+  kScalLambdaMax = 0,   // stored as the bit pattern of a non-negative double
+  kScalCdd = 1,         // d^T N^-1 d
+  kScalTmp = 2,
+  kScalCount = 64
+};
+
+// ---------------------------------------------------------------------- complex helpers
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) {
+  return make_float2(a.x * s, a.y * s);
+}
+// multiply by -i (DIR < 0) or +i (DIR > 0)
+template <int DIR>
+__device__ __forceinline__ float2 mul_i(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
+// ------------------------------------------------------------------------- butterflies
+// In-register DFTs of length 2, 4, 8 with kernel exp(DIR * 2 pi i jk / R).
+template <int DIR>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  float2 t0 = cadd(v0, v2), t1 = csub(v0, v2);
+  float2 t2 = cadd(v1, v3), t3 = mul_i<DIR>(csub(v1, v3));
+  v0 = cadd(t0, t2);
+  v2 = csub(t0, t2);
+  v1 = cadd(t1, t3);
+  v3 = csub(t1, t3);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft8(float2* v) {
+  const float h = 0.70710678118654752440f;
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<DIR>(e0, e1, e2, e3);
+  dft4<DIR>(o0, o1, o2, o3);
+  // o_k *= w8^k, w8 = exp(DIR * i pi / 4)
+  o1 = DIR < 0 ? make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x))
+               : make_float2(h * (o1.x - o1.y), h * (o1.y + o1.x));
+  o2 = mul_i<DIR>(o2);
+  o3 = DIR < 0 ? make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y))
+               : make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y));
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+template <int R, int DIR>
+__device__ __forceinline__ void dftR(float2* v) {
+  if constexpr (R == 2) dft2<DIR>(v[0], v[1]);
+  else if constexpr (R == 4) dft4<DIR>(v[0], v[1], v[2], v[3]);
+  else dft8<DIR>(v);
+}
+
+// ----------------------------------------------------------------- shared-memory layouts
+// Column layout: NB transforms interleaved, element (b, i) at s[i * NB + b]; with NB >= 16
+// consecutive b are consecutive 8-byte words, so every access of a pass is conflict-free.
+template <int NB>
+struct ColLayout {
+  __device__ __forceinline__ static int at(int b, int i) { return i * NB + b; }
+  static constexpr bool kBFast = true;
+};
+// Row layout: transform b occupies [b*L, (b+1)*L), XOR-swizzled in 16-word groups so the
+// strided stores of the first Stockham passes spread over all banks.
+template <int L>
+struct RowLayout {
+  __device__ __forceinline__ static int swz(int idx) { return idx ^ ((idx >> 4) & 15); }
+  __device__ __forceinline__ static int at(int b, int i) { return swz(b * L + i); }
+  static constexpr bool kBFast = false;
+};
+
+// One radix-R Stockham pass (auto-sorting, out of place in registers / in place in shared
+// memory): for butterfly j of transform b with k = j mod Ns, gather x[j + r L/R], twiddle
+// by w_{Ns R}^{r k}, DFT_R, scatter to (j - k) R + k + q Ns.
+template <int L, int NB, class Lay, int T, int DIR, int R, int Ns>
+__device__ __forceinline__ void fft_pass(float2* s, const float2* __restrict__ tw) {
+  constexpr int NBF = NB * (L / R);
+  constexpr int U = (NBF + T - 1) / T;
+  float2 v[U][R];
+  int jj[U], bb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int g = threadIdx.x + u * T;
+    if (NBF % T != 0 && g >= NBF) continue;
+    int b, j;
+    if constexpr (Lay::kBFast) { b = g % NB; j = g / NB; }
+    else { j = g % (L / R); b = g / (L / R); }
+    jj[u] = j; bb[u] = b;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[u][r] = s[Lay::at(b, j + r * (L / R))];
+    if constexpr (Ns > 1) {
+      const int k = j % Ns;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = __ldg(&tw[(r * k) * (L / (Ns * R))]);
+        if (DIR > 0) w.y = -w.y;
+        v[u][r] = cmul(v[u][r], w);
+      }
+    }
+    dftR<R, DIR>(v[u]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int g = threadIdx.x + u * T;
+    if (NBF % T != 0 && g >= NBF) continue;
+    const int j = jj[u], b = bb[u];
+    const int k = j % Ns;
+    const int o = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) s[Lay::at(b, o + r * Ns)] = v[u][r];
+  }
+  __syncthreads();
+}
+
+template <int Rem>
+__host__ __device__ constexpr int pick_radix() {
+  return Rem == 2 ? 2 : (ilog2(Rem) % 3 == 0 ? 8 : 4);
+}
+
+template <int L, int NB, class Lay, int T, int DIR, int Ns>
+__device__ __forceinline__ void fft_passes(float2* s, const float2* __restrict__ tw) {
+  if constexpr (Ns < L) {
+    constexpr int R = pick_radix<L / Ns>();
+    fft_pass<L, NB, Lay, T, DIR, R, Ns>(s, tw);
+    fft_passes<L, NB, Lay, T, DIR, Ns * R>(s, tw);
+  }
+}
+
+// NB unnormalised length-L DFTs (kernel exp(DIR 2 pi i jk / L)) in shared memory, natural
+// order in and out.  tw[m] = exp(-2 pi i m / L).  Ends with a __syncthreads.
+template <int L, int NB, class Lay, int T, int DIR>
+__device__ __forceinline__ void smem_fft(float2* s, const float2* __restrict__ tw) {
+  fft_passes<L, NB, Lay, T, DIR, 1>(s, tw);
+}
+
+// w_M^e for 0 <= e < M from the two-level table (FP64-accurate entries, FP32 product).
+__device__ __forceinline__ float2 tw_big(const Group& g, int e) {
+  return cmul(__ldg(&g.tw_hi[e >> g.log_lo]), __ldg(&g.tw_lo[e & ((1 << g.log_lo) - 1)]));
+}
+
+// -------------------------------------------------------------------- kernel launchers
+// Modes of the row kernel (B).
+enum RowMode {
+  kRowSpectrum = 0,   // forward only: store X = rfft(x) into dtab (row layout)
+  kRowNatural = 1,    // forward only: store X into a natural-order complex64 array
+  kRowMessenger = 2,  // forward, messenger filter (+ chi^2 of the input), inverse
+  kRowPcgApply = 3,   // forward, Y = X / N, inverse
+  kRowPcgRhs = 4,     // no forward: Y = d~ / N (+ chi^2 of m = 0, i.e. d^T N^-1 d), inverse
+  kRowChi2 = 5        // forward, chi^2 only
+};
+
+struct RowArgs {
+  int mode;
+  double lambda;       // cooling parameter (messenger) / N' = N + (lambda-1) tau (chi^2)
+  double* chi2;        // device accumulator or nullptr
+  float2* natural;     // kRowNatural output
+};
+
+// Source of the forward column pass.
+enum ColSrc { kSrcGather = 0, kSrcTod = 1 };
+
+cudaError_t launch_col_forward(const mm_plan_s* p, const Group& g, int src, const float* tod,
+                               cudaStream_t st);
+cudaError_t launch_row(const mm_plan_s* p, const Group& g, const RowArgs& a, cudaStream_t st);
+cudaError_t launch_col_inverse(const mm_plan_s* p, const Group& g, cudaStream_t st);
+
+}  // namespace mm
+
+// error reporting shared by the ABI translation units
+void mm_set_error(const char* fmt, ...);

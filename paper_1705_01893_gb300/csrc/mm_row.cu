@@ -1,0 +1,220 @@
+// Row pass of the four-step FFT with the Fourier-diagonal messenger update in the middle
+// (kernel B).  A CTA owns rows k1 and M1-k1 of one chunk's intermediate: after the forward
+// row DFTs it holds Z_k and Z_{M-k} for all its frequencies, exactly the pairs that the
+// real-to-complex split needs:
+//   E_k = (Z_k + conj Z_{M-k}) / 2,  O_k = -i (Z_k - conj Z_{M-k}) / 2,
+//   X_k = E_k + w_{2M}^k O_k,        X_{M-k} = conj(E_k - w_{2M}^k O_k),
+// with X = rfft(x) of the chunk.  It applies the per-mode filter (Sec. 2.1 with T = tau I:
+//   t~ = (lambda tau d~ + Nbar (Pm)~) / (lambda tau + Nbar)),
+// accumulates chi^2 = (1/n) sum_k w_k |d~ - (Pm)~|^2 / N (Eq. 3 evaluated per Fourier mode,
+// Sec. 3.1), merges the filtered Hermitian spectrum back into the packed form
+//   Z'_k = (Y_k + conj Y_{M-k}) + i conj(w_{2M}^k) (Y_k - conj Y_{M-k})
+// and runs the inverse row DFTs, so the spectrum never leaves the chip between the forward
+// and inverse transforms.
+#include "mm_internal.cuh"
+
+namespace mm {
+
+struct RowParams {
+  const ChunkDesc* desc;
+  const int* chunks;
+  Group g;
+  float2* ybuf;
+  float2* dtab;
+  const float* nbar;
+  const float* nyq;
+  RowArgs a;
+};
+
+template <int M2, int T>
+__global__ void __launch_bounds__(T) k_row(RowParams q) {
+  extern __shared__ float2 sm[];
+  using Lay = RowLayout<M2>;
+  __shared__ float red[32];
+  const int c = q.chunks[blockIdx.y];
+  const ChunkDesc d = q.desc[c];
+  const int M1 = d.M1, M = d.M;
+  const int rA = blockIdx.x;
+  const int rB = (M1 - rA) & (M1 - 1);
+  const bool self = rA == rB;
+  const int mode = q.a.mode;
+  float2* y = q.ybuf + d.spec;
+  const bool fwd = mode != kRowPcgRhs;
+  const bool inv = mode == kRowMessenger || mode == kRowPcgApply || mode == kRowPcgRhs;
+
+  if (fwd) {
+    for (int i = threadIdx.x; i < M2; i += T) {
+      const float2 a = y[(int64_t)rA * M2 + i];
+      sm[Lay::at(0, i)] = a;
+      sm[Lay::at(1, i)] = self ? a : y[(int64_t)rB * M2 + i];
+    }
+    __syncthreads();
+    smem_fft<M2, 2, Lay, T, -1>(sm, q.g.tw_row);
+  }
+
+  // per-mode constants
+  const float tau = (float)d.tau;
+  const float inv_n = 1.0f / (float)d.n;
+  float lt = 0.f;               // lambda * tau
+  bool lam_inf = false;
+  if (mode == kRowMessenger) {
+    lam_inf = isinf(q.a.lambda);
+    lt = lam_inf ? 0.f : (float)(q.a.lambda * d.tau);
+  }
+  // N' = Nbar + cn for chi^2: tau (Eq. 3) or lambda tau (chi^2(m, lambda))
+  const float cn = mode == kRowChi2 ? (float)(q.a.lambda * d.tau) : tau;
+  // output scale: irfft normalisation 1/n, and T^-1 = 1/tau for the messenger map step
+  const float sc = mode == kRowMessenger ? inv_n / tau : inv_n;
+  const float2* dt = q.dtab + d.spec;
+  const float* nb = q.nbar + d.spec;
+  const float2 wa = __ldg(&q.g.tw_pack_a[rA]);
+  float x2 = 0.f;
+
+  auto filt = [&](float2 X, float2 D, float nbv) -> float2 {
+    if (mode == kRowMessenger) {
+      if (lam_inf) return cscale(D, sc);
+      const float r = sc / (lt + nbv);
+      return make_float2((lt * D.x + nbv * X.x) * r, (lt * D.y + nbv * X.y) * r);
+    }
+    if (mode == kRowPcgApply) return cscale(X, sc / (nbv + tau));
+    return cscale(D, sc / (nbv + tau));  // kRowPcgRhs
+  };
+  const bool want_x2 = q.a.chi2 != nullptr &&
+                       (mode == kRowMessenger || mode == kRowChi2 || mode == kRowPcgRhs);
+
+  for (int p = threadIdx.x; p < M2; p += T) {
+    int qs, qi;  // partner slot (0 = row rA, 1 = row rB) and index
+    if (!self) { qs = 1; qi = M2 - 1 - p; }
+    else if (rA == 0) { qs = 0; qi = (M2 - p) & (M2 - 1); if (p > qi) continue; }
+    else { qs = 0; qi = M2 - 1 - p; if (p > qi) continue; }
+    const int rowq = qs ? rB : rA;
+    const int sk = rA * M2 + p, sp = rowq * M2 + qi;   // spectrum slots of k and M-k
+    const float2 Zk = fwd ? sm[Lay::at(0, p)] : make_float2(0.f, 0.f);
+    const float2 Zp = fwd ? sm[Lay::at(qs, qi)] : make_float2(0.f, 0.f);
+
+    if (rA == 0 && p == 0) {
+      // k = 0 and k = M (both real): X_0 = Re Z_0 + Im Z_0, X_M = Re Z_0 - Im Z_0
+      const float X0 = Zk.x + Zk.y, XM = Zk.x - Zk.y;
+      if (mode == kRowSpectrum) { q.dtab[d.spec] = make_float2(X0, XM); continue; }
+      if (mode == kRowNatural) {
+        float2* o = q.a.natural + d.spec + c;
+        o[0] = make_float2(X0, 0.f);
+        o[M] = make_float2(XM, 0.f);
+        continue;
+      }
+      const float2 D = dt[0];
+      const float n0 = nb[0], nM = __ldg(q.nyq + c);
+      if (want_x2) {
+        const float e0 = D.x - X0, eM = D.y - XM;
+        x2 += e0 * e0 / (n0 + cn) + eM * eM / (nM + cn);
+      }
+      if (!inv) continue;
+      const float Y0 = filt(make_float2(X0, 0.f), make_float2(D.x, 0.f), n0).x;
+      const float YM = filt(make_float2(XM, 0.f), make_float2(D.y, 0.f), nM).x;
+      sm[Lay::at(0, 0)] = make_float2(Y0 + YM, Y0 - YM);
+      continue;
+    }
+
+    const float2 w = cmul(wa, __ldg(&q.g.tw_pack_b[p]));   // w_{2M}^k, k = rA + M1 p
+    const float2 E = cscale(cadd(Zk, cconj(Zp)), 0.5f);
+    const float2 O = cscale(mul_i<-1>(csub(Zk, cconj(Zp))), 0.5f);
+    const float2 wO = cmul(w, O);
+    const float2 Xk = cadd(E, wO);
+    const float2 Xp = cconj(csub(E, wO));
+    const bool same = (qs == 0 && qi == p);   // k == M - k (k = M/2)
+    if (mode == kRowSpectrum) {
+      q.dtab[d.spec + sk] = Xk;
+      if (!same) q.dtab[d.spec + sp] = Xp;
+      continue;
+    }
+    if (mode == kRowNatural) {
+      float2* o = q.a.natural + d.spec + c;
+      const int k = rA + M1 * p;
+      o[k] = Xk;
+      o[M - k] = Xp;
+      continue;
+    }
+    const float2 Dk = dt[sk], Dp = dt[sp];
+    const float nk = nb[sk], np = nb[sp];
+    if (want_x2) {
+      const float2 ek = csub(Dk, Xk), ep = csub(Dp, Xp);
+      float t = (ek.x * ek.x + ek.y * ek.y) / (nk + cn);
+      if (!same) t += (ep.x * ep.x + ep.y * ep.y) / (np + cn);
+      x2 += 2.f * t;
+    }
+    if (!inv) continue;
+    const float2 Yk = filt(Xk, Dk, nk);
+    const float2 Yp = filt(Xp, Dp, np);
+    // Z'_k = (Y_k + conj Y_p) + i conj(w) (Y_k - conj Y_p);
+    // Z'_p = (Y_p + conj Y_k) - i w (Y_p - conj Y_k)
+    const float2 zk = cadd(cadd(Yk, cconj(Yp)), mul_i<+1>(cmulc(csub(Yk, cconj(Yp)), w)));
+    sm[Lay::at(0, p)] = zk;
+    if (!same) {
+      const float2 zp = csub(cadd(Yp, cconj(Yk)), mul_i<+1>(cmul(w, csub(Yp, cconj(Yk)))));
+      sm[Lay::at(qs, qi)] = zp;
+    }
+  }
+
+  if (want_x2) {
+    // block reduction: FP32 within warps, FP64 across warps and CTAs
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x2 += __shfl_down_sync(0xffffffffu, x2, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < T / 32; ++i) s += red[i];
+      atomicAdd(q.a.chi2, s / (double)d.n);
+    }
+  }
+  if (!inv) return;
+  __syncthreads();
+  smem_fft<M2, 2, Lay, T, +1>(sm, q.g.tw_row);
+  for (int i = threadIdx.x; i < M2; i += T) {
+    y[(int64_t)rA * M2 + i] = cmulc(sm[Lay::at(0, i)], tw_big(q.g, rA * i));
+    if (!self) y[(int64_t)rB * M2 + i] = cmulc(sm[Lay::at(1, i)], tw_big(q.g, rB * i));
+  }
+}
+
+constexpr int row_threads(int M2) {
+  return M2 / 8 < 32 ? 32 : (M2 / 8 > 1024 ? 1024 : M2 / 8);
+}
+
+template <int M2>
+static cudaError_t row_m2(const mm_plan_s* p, const Group& g, const RowArgs& a,
+                          cudaStream_t st) {
+  constexpr int T = row_threads(M2);
+  RowParams q;
+  q.desc = p->d_desc;
+  q.chunks = g.chunks;
+  q.g = g;
+  q.ybuf = p->ybuf;
+  q.dtab = p->dtab;
+  q.nbar = p->nbar;
+  q.nyq = p->nyq;
+  q.a = a;
+  const size_t smem = sizeof(float2) * 2 * M2;
+  auto k = k_row<M2, T>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<dim3(g.M1 / 2 + 1, g.n_chunks), T, smem, st>>>(q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row(const mm_plan_s* p, const Group& g, const RowArgs& a, cudaStream_t st) {
+  switch (g.M2) {
+    case 16: return row_m2<16>(p, g, a, st);
+    case 32: return row_m2<32>(p, g, a, st);
+    case 64: return row_m2<64>(p, g, a, st);
+    case 128: return row_m2<128>(p, g, a, st);
+    case 256: return row_m2<256>(p, g, a, st);
+    case 512: return row_m2<512>(p, g, a, st);
+    case 1024: return row_m2<1024>(p, g, a, st);
+    case 2048: return row_m2<2048>(p, g, a, st);
+    case 4096: return row_m2<4096>(p, g, a, st);
+    case 8192: return row_m2<8192>(p, g, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mm

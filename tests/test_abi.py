@@ -1,0 +1,78 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every declared symbol;
+host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1705_01893_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "mm.h")).read()
+    decl = r"^(?:mm_status|void|const char\*)\s+(mm_\w+)\s*\("
+    return sorted(set(re.findall(decl, text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load()
+
+
+def test_header_matches_binding():
+    assert set(declared_symbols()) == set(binding.SIGNATURES)
+
+
+def test_every_declared_symbol_exported(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_workspace_size_host_checks(lib):
+    n = ctypes.c_size_t()
+    off = np.array([0, 4096, 8192], dtype=np.int64)
+    offp = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    assert lib.mm_plan_workspace_size(2, offp, 100, 3, 0, ctypes.byref(n)) == binding.MM_OK
+    assert n.value > 0 and n.value % 256 == 0
+    # T-only needs less than IQU
+    m = ctypes.c_size_t()
+    assert lib.mm_plan_workspace_size(2, offp, 100, 1, 0, ctypes.byref(m)) == binding.MM_OK
+    assert m.value < n.value
+    # bad ncomp, bad weight dtype, bad n_pix
+    assert lib.mm_plan_workspace_size(2, offp, 100, 2, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
+    assert lib.mm_plan_workspace_size(2, offp, 100, 3, 7, ctypes.byref(n)) == binding.MM_ERR_ARG
+    assert lib.mm_plan_workspace_size(2, offp, 0, 3, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
+    assert b"n_pix" in lib.mm_last_error()
+    # unsupported lengths: odd, not 2 x power of two, too short
+    for bad in ([0, 4095], [0, 3000], [0, 256]):
+        o = np.array(bad, dtype=np.int64)
+        r = lib.mm_plan_workspace_size(1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 10, 1,
+                                       0, ctypes.byref(n))
+        assert r == binding.MM_ERR_UNSUPPORTED, bad
+
+
+def test_null_arguments_rejected_on_host(lib):
+    h = ctypes.c_void_p()
+    off = np.array([0, 1024], dtype=np.int64)
+    offp = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    # pix NULL
+    r = lib.mm_plan_pointing(ctypes.byref(h), 1, offp, None, None, None, 0, 16, 1, 1e-3, None, 0, None)
+    assert r == binding.MM_ERR_ARG
+    assert lib.mm_messenger_iterate(None, None, 0, 0, None, None, None) == binding.MM_ERR_ARG
+    lib.mm_plan_destroy(None)
+
+
+def test_workspace_too_small_is_nomem(lib):
+    h = ctypes.c_void_p()
+    off = np.array([0, 1024], dtype=np.int64)
+    offp = off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: the size check comes first
+    r = lib.mm_plan_pointing(ctypes.byref(h), 1, offp, fake, None, None, 0, 16, 1, 1e-3,
+                             ctypes.c_void_p(0x100000), 16, None)
+    assert r == binding.MM_ERR_NOMEM
+    assert b"workspace too small" in lib.mm_last_error()
