@@ -103,10 +103,15 @@ mm_status mm_lambda_max(mm_plan p, double* out, void* stream);
 mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int precision,
                                double* map_inout, double* chi2_out, void* stream);
 
+/* Chunks run in batches: a batch's four-step FFT intermediate is sized (32 MB by default,
+ * environment variable MM_YBUF_MB) to stay resident in L2 between the column and row passes.
+ * *n_batches receives their number; batches run one after another on the caller's stream. */
+mm_status mm_plan_batches(mm_plan p, int* n_batches);
+
 /* One stage of a messenger iteration, for callers that interleave their own work (or
- * CUDA events) between the kernels of an iteration.  mm_messenger_iterate runs, per
- * iteration, GATHER_FFT, FILTER, IFFT_BIN, MAP after one LOAD; the same sequence through
- * this entry point gives identical results.
+ * CUDA events) between the kernels of an iteration.  mm_messenger_iterate runs one LOAD,
+ * then per iteration: for each batch b, GATHER_FFT(b), FILTER(b), IFFT_BIN(b); then MAP.
+ * The same sequence through this entry point gives identical results.
  *   MM_STAGE_LOAD:       map_inout (device float64 [n_pix][ncomp]) -> internal FP32 map;
  *   MM_STAGE_GATHER_FFT: P m gathered from the internal map, packed, column DFTs (Eq. 1);
  *   MM_STAGE_FILTER:     row DFTs, per-mode messenger filter at `lambda` (>= 1 or INFINITY),
@@ -115,11 +120,13 @@ mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int
  *   MM_STAGE_IFFT_BIN:   inverse column DFTs and P^T T^-1 t into FP64 accumulators;
  *   MM_STAGE_MAP:        m = (P^T T^-1 P)^-1 acc per pixel; written to map_inout if non-NULL,
  *                        and to the internal map for the next GATHER_FFT.
- * Unused arguments may be NULL / 0. */
+ * `batch` selects the batch of the three per-batch stages and is ignored otherwise; a
+ * batch's GATHER_FFT, FILTER and IFFT_BIN must run in that order before the next batch's
+ * GATHER_FFT (they share one intermediate buffer).  Unused pointers may be NULL. */
 enum { MM_STAGE_LOAD = 0, MM_STAGE_GATHER_FFT = 1, MM_STAGE_FILTER = 2, MM_STAGE_IFFT_BIN = 3,
        MM_STAGE_MAP = 4 };
-mm_status mm_messenger_stage(mm_plan p, int stage, double lambda, double* map_inout,
-                             double* chi2_slot, void* stream);
+mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double lambda,
+                             double* map_inout, double* chi2_slot, void* stream);
 
 /* Bytes of device state mm_pcg_iterate needs (caller-owned, 256-byte aligned). */
 mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes);

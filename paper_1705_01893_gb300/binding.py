@@ -37,7 +37,9 @@ SIGNATURES = {
     "mm_set_noise_psd": (ctypes.c_int, [_vp, _vp, _dp, _dp, _vp, _vp]),
     "mm_lambda_max": (ctypes.c_int, [_vp, _dp, _vp]),
     "mm_messenger_iterate": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
-    "mm_messenger_stage": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, _vp, _vp, _vp]),
+    "mm_plan_batches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "mm_messenger_stage": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp,
+                                          _vp]),
     "mm_pcg_state_bytes": (ctypes.c_int, [_vp, _szp]),
     "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
@@ -172,9 +174,16 @@ class Plan:
             self._h, lam.ctypes.data_as(_dp), len(lam), MM_FP32_MIXED, _ptr(map_inout),
             _ptr(chi2_out), _stream(stream)))
 
-    def stage(self, stage: int, lam: float = 1.0, map_inout=None, chi2_slot=None, stream=None):
+    def n_batches(self) -> int:
+        n = ctypes.c_int()
+        _check("mm_plan_batches", load().mm_plan_batches(self._h, ctypes.byref(n)))
+        return n.value
+
+    def stage(self, stage: int, batch: int = 0, lam: float = 1.0, map_inout=None, chi2_slot=None,
+              stream=None):
         _check("mm_messenger_stage", load().mm_messenger_stage(
-            self._h, int(stage), float(lam), _ptr(map_inout), _ptr(chi2_slot), _stream(stream)))
+            self._h, int(stage), int(batch), float(lam), _ptr(map_inout), _ptr(chi2_slot),
+            _stream(stream)))
 
     def pcg_state(self):
         import torch

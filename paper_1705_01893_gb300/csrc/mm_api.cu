@@ -7,7 +7,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "mm_internal.cuh"
@@ -46,6 +48,32 @@ extern "C" const char* mm_last_error(void) { return g_err; }
 
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+cudaError_t mm::resident_ctas(const void* kernel, int threads, size_t smem, int* out) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const void* key = static_cast<const char*>(kernel) + dev;  // one entry per device
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) { *out = it->second; return cudaSuccess; }
+  }
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  int nsm = 0, occ = 0;
+  if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem)) != cudaSuccess)
+    return e;
+  const int r = (occ < 1 ? 1 : occ) * nsm;
+  std::lock_guard<std::mutex> g(mu);
+  cache[key] = r;
+  *out = r;
+  return cudaSuccess;
+}
+
 // ------------------------------------------------------------------------ FFT shapes
 // M = 2^p complex points per chunk (n = 2M real samples): columns M1, rows M2 = M / M1.
 // Rows stay <= 8192 (two rows in shared memory), columns <= 1024.
@@ -73,7 +101,7 @@ static int log_lo_of(int M) {
 
 static size_t tw_count(int M, int M1, int M2) {
   const int lo = log_lo_of(M);
-  return (size_t)M1 + M2 + (size_t(1) << lo) + (size_t)(M >> lo) + M1 + M2;
+  return (size_t)tw_size(M1) + tw_size(M2) + (size_t(1) << lo) + (size_t)(M >> lo) + M1 + M2;
 }
 
 // -------------------------------------------------------------------- workspace layout
@@ -81,12 +109,20 @@ struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
       ybuf, scal, total;
   int n_groups;
-  int gM[kMaxGroups], gM1[kMaxGroups], gM2[kMaxGroups], gcount[kMaxGroups];
+  int gM[kMaxGroups], gM1[kMaxGroups], gM2[kMaxGroups], gcount[kMaxGroups], gbatch[kMaxGroups];
   std::vector<int> chunk_group;
   int64_t spec_total, n_total;
 };
 
 static size_t up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Bytes of four-step intermediate one batch may use (MM_YBUF_MB overrides; default 32 MB,
+// a quarter of L2, so a batch's intermediate survives between its column and row passes).
+static size_t ybuf_budget() {
+  const char* e = getenv("MM_YBUF_MB");
+  const long mb = e ? atol(e) : 32;
+  return (size_t)(mb > 0 ? mb : 32) << 20;
+}
 
 static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, int ncomp,
                              Layout* L) {
@@ -123,8 +159,17 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   }
   L->n_total = off[n_chunks];
   MM_ARG(L->n_total < (int64_t(1) << 31) * 2, "too many samples");
-  size_t tw = 0;
-  for (int g = 0; g < L->n_groups; ++g) tw += tw_count(L->gM[g], L->gM1[g], L->gM2[g]);
+  size_t tw = 0, ybytes = 0;
+  const size_t budget = ybuf_budget();
+  for (int g = 0; g < L->n_groups; ++g) {
+    tw += tw_count(L->gM[g], L->gM1[g], L->gM2[g]);
+    const size_t per = sizeof(float2) * (size_t)L->gM[g];
+    size_t b = budget / per;
+    if (b < 1) b = 1;
+    if (b > (size_t)L->gcount[g]) b = L->gcount[g];
+    L->gbatch[g] = (int)b;
+    if (b * per > ybytes) ybytes = b * per;
+  }
   const size_t np = (size_t)n_pix;
   const size_t blk = ncomp == 3 ? 6 : 1;
   size_t o = 0;
@@ -145,7 +190,7 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->nbar = take(sizeof(float) * L->spec_total);
   L->nyq = take(sizeof(float) * n_chunks);
   L->c0 = take(sizeof(double) * n_chunks);
-  L->ybuf = take(sizeof(float2) * L->spec_total);
+  L->ybuf = take(ybytes);
   L->scal = take(sizeof(double) * kScalCount);
   L->total = o;
   return MM_OK;
@@ -164,6 +209,26 @@ extern "C" mm_status mm_plan_workspace_size(int n_chunks, const int64_t* offsets
 }
 
 // ---------------------------------------------------------------------- set-up kernels
+// Per-pass Stockham twiddles of a length-L DFT: entry r * Ns + k of pass (Ns, R) holds
+// w_{Ns R}^{r k}, computed in FP64 and rounded to FP32.
+__global__ void k_pass_twiddles(float2* out, int L) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= tw_size(L)) return;
+  int off = 0, ns = 1;
+  while (true) {
+    const int r = pick_radix(L / ns);
+    if (e < off + ns * r) {
+      const int loc = e - off, rr = loc / ns, k = loc % ns;
+      double sn, cs;
+      sincospi(-2.0 * (double)(rr * k) / (double)(ns * r), &sn, &cs);
+      out[e] = make_float2((float)cs, (float)sn);
+      return;
+    }
+    off += ns * r;
+    ns *= r;
+  }
+}
+
 __global__ void k_twiddles(float2* out, int count, int denom_mul, int L) {
   // out[m] = exp(-2 pi i m * denom_mul / L) computed in FP64, rounded to FP32
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -712,6 +777,8 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
     p->h_chunk_group[c] = g;
   }
   p->n_groups = L.n_groups;
+  p->h_batches = nullptr;
+  p->n_batches = 0;
   size_t tw_off = 0;
   for (int g = 0; g < L.n_groups; ++g) {
     Group& G = p->groups[g];
@@ -719,16 +786,28 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
     G.log_lo = log_lo_of(G.M);
     G.chunks = d_chunks + order.size();
     G.n_chunks = 0;
+    G.batch = L.gbatch[g];
     for (int c = 0; c < n_chunks; ++c)
       if (L.chunk_group[c] == g) { order.push_back(c); G.n_chunks++; }
     float2* t = p->tw_pool + tw_off;
-    G.tw_col = t; t += G.M1;
-    G.tw_row = t; t += G.M2;
+    G.tw_col = t; t += tw_size(G.M1);
+    G.tw_row = t; t += tw_size(G.M2);
     G.tw_lo = t; t += (1 << G.log_lo);
     G.tw_hi = t; t += (G.M >> G.log_lo);
     G.tw_pack_a = t; t += G.M1;
     G.tw_pack_b = t; t += G.M2;
     tw_off += tw_count(G.M, G.M1, G.M2);
+  }
+  {
+    int nb = 0;
+    for (int g = 0; g < L.n_groups; ++g) nb += (p->groups[g].n_chunks + L.gbatch[g] - 1) / L.gbatch[g];
+    p->h_batches = new (std::nothrow) Batch[nb];
+    if (!p->h_batches) { mm_plan_destroy(p); mm_set_error("host allocation failed"); return MM_ERR_NOMEM; }
+    for (int g = 0; g < L.n_groups; ++g)
+      for (int f = 0; f < p->groups[g].n_chunks; f += L.gbatch[g]) {
+        const int cnt = p->groups[g].n_chunks - f < L.gbatch[g] ? p->groups[g].n_chunks - f : L.gbatch[g];
+        p->h_batches[p->n_batches++] = Batch{g, f, cnt};
+      }
   }
   cudaStream_t s = S(stream);
   auto fail = [&](const char* what, cudaError_t e) {
@@ -743,8 +822,9 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
                            cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail("chunk list upload", e);
   for (int g = 0; g < L.n_groups; ++g) {
     const Group& G = p->groups[g];
-    struct { float2* o; int cnt, mul, L; } tabs[6] = {
-        {G.tw_col, G.M1, 1, G.M1},       {G.tw_row, G.M2, 1, G.M2},
+    k_pass_twiddles<<<blocks_for(tw_size(G.M1), 256), 256, 0, s>>>(G.tw_col, G.M1);
+    k_pass_twiddles<<<blocks_for(tw_size(G.M2), 256), 256, 0, s>>>(G.tw_row, G.M2);
+    struct { float2* o; int cnt, mul, L; } tabs[4] = {
         {G.tw_lo, 1 << G.log_lo, 1, G.M}, {G.tw_hi, G.M >> G.log_lo, 1 << G.log_lo, G.M},
         {G.tw_pack_a, G.M1, 1, 2 * G.M}, {G.tw_pack_b, G.M2, G.M1, 2 * G.M}};
     for (auto& tb : tabs) {
@@ -774,19 +854,24 @@ extern "C" void mm_plan_destroy(mm_plan p) {
   if (!p) return;
   delete[] p->h_desc;
   delete[] p->h_chunk_group;
+  delete[] p->h_batches;
   delete p;
 }
 
-// Run fn over the groups, failing on the first launch error.
-#define FOR_GROUPS(call)                                                  \
-  for (int g_ = 0; g_ < p->n_groups; ++g_) {                              \
-    const Group& G = p->groups[g_];                                       \
-    cudaError_t e_ = (call);                                              \
+// Run a sequence of launches over every batch (in order, on one stream), failing on the
+// first launch error.  `B` names the current batch inside `seq`.
+#define FOR_BATCHES(seq)                                                  \
+  for (int b_ = 0; b_ < p->n_batches; ++b_) {                             \
+    const Batch& B = p->h_batches[b_];                                    \
+    (void)B;                                                              \
+    cudaError_t e_ = cudaSuccess;                                         \
+    seq;                                                                  \
     if (e_ != cudaSuccess) {                                              \
-      mm_set_error("%s: %s", #call, cudaGetErrorString(e_));              \
+      mm_set_error("%s: %s", #seq, cudaGetErrorString(e_));               \
       return MM_ERR_CUDA;                                                 \
     }                                                                     \
   }
+#define L_(call) if (e_ == cudaSuccess) e_ = (call)
 
 static mm_status check_launch(const char* what) {
   cudaError_t e = cudaGetLastError();
@@ -875,15 +960,13 @@ extern "C" mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const do
   // d~ = rfft(d) into the row-layout table
   {
     RowArgs a{kRowSpectrum, 1.0, nullptr, nullptr};
-    FOR_GROUPS(launch_col_forward(p, G, kSrcTod, tod, s));
-    FOR_GROUPS(launch_row(p, G, a, s));
+    FOR_BATCHES(L_(launch_col_forward(p, B, kSrcTod, tod, s)); L_(launch_row(p, B, a, s)));
   }
   // b = P^T N^-1 d and d^T N^-1 d
   {
     MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * p->ncomp * p->n_pix, s));
     RowArgs a{kRowPcgRhs, 1.0, p->scal + kScalCdd, nullptr};
-    FOR_GROUPS(launch_row(p, G, a, s));
-    FOR_GROUPS(launch_col_inverse(p, G, s));
+    FOR_BATCHES(L_(launch_row(p, B, a, s)); L_(launch_col_inverse(p, B, s)));
     const int64_t len = p->ncomp * p->n_pix;
     k_finish_b<<<blocks_for(len, 256), 256, 0, s>>>(len, p->ncomp, p->acc, p->valid, p->bvec);
     LAUNCHED("k_finish_b");
@@ -934,16 +1017,8 @@ extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int 
   if (chi2_out) MM_CUDA(cudaMemsetAsync(chi2_out, 0, sizeof(double) * n_iter, s));
   for (int it = 0; it < n_iter; ++it) {
     RowArgs a{kRowMessenger, lambdas[it], chi2_out ? chi2_out + it : nullptr, nullptr};
-    for (int g = 0; g < p->n_groups; ++g) {
-      const Group& G = p->groups[g];
-      cudaError_t e;
-      if ((e = launch_col_forward(p, G, kSrcGather, nullptr, s)) != cudaSuccess ||
-          (e = launch_row(p, G, a, s)) != cudaSuccess ||
-          (e = launch_col_inverse(p, G, s)) != cudaSuccess) {
-        mm_set_error("messenger launch: %s", cudaGetErrorString(e));
-        return MM_ERR_CUDA;
-      }
-    }
+    FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
+                L_(launch_col_inverse(p, B, s)));
     double* mo = it == n_iter - 1 ? map_inout : nullptr;
     if (p->ncomp == 3) k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, mo);
     else k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, mo);
@@ -952,35 +1027,51 @@ extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int 
   return MM_OK;
 }
 
-extern "C" mm_status mm_messenger_stage(mm_plan p, int stage, double lambda, double* map_inout,
-                                        double* chi2_slot, void* stream) {
+extern "C" mm_status mm_plan_batches(mm_plan p, int* n_batches) {
+  MM_ARG(p != nullptr && n_batches != nullptr, "NULL argument");
+  *n_batches = p->n_batches;
+  return MM_OK;
+}
+
+extern "C" mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double lambda,
+                                        double* map_inout, double* chi2_slot, void* stream) {
   MM_ARG(p != nullptr, "plan is NULL");
   if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
   cudaStream_t s = S(stream);
+  const bool per_batch = stage == MM_STAGE_GATHER_FFT || stage == MM_STAGE_FILTER ||
+                         stage == MM_STAGE_IFFT_BIN;
+  if (per_batch) MM_ARG(batch >= 0 && batch < p->n_batches, "batch %d out of range", batch);
+  cudaError_t e = cudaSuccess;
   switch (stage) {
     case MM_STAGE_LOAD:
       MM_ARG(map_inout != nullptr, "map_inout is NULL");
       return load_map(p, map_inout, s);
     case MM_STAGE_GATHER_FFT:
-      FOR_GROUPS(launch_col_forward(p, G, kSrcGather, nullptr, s));
-      return MM_OK;
+      e = launch_col_forward(p, p->h_batches[batch], kSrcGather, nullptr, s);
+      break;
     case MM_STAGE_FILTER: {
       MM_ARG(lambda >= 1.0 || isinf(lambda), "lambda = %g must be >= 1 or inf", lambda);
       RowArgs a{kRowMessenger, lambda, chi2_slot, nullptr};
-      FOR_GROUPS(launch_row(p, G, a, s));
-      return MM_OK;
+      e = launch_row(p, p->h_batches[batch], a, s);
+      break;
     }
     case MM_STAGE_IFFT_BIN:
-      FOR_GROUPS(launch_col_inverse(p, G, s));
-      return MM_OK;
+      e = launch_col_inverse(p, p->h_batches[batch], s);
+      break;
     case MM_STAGE_MAP:
       if (p->ncomp == 3) k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, map_inout);
       else k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, map_inout);
       LAUNCHED("k_bin_apply");
       return MM_OK;
+    default:
+      mm_set_error("unknown stage %d", stage);
+      return MM_ERR_ARG;
   }
-  mm_set_error("unknown stage %d", stage);
-  return MM_ERR_ARG;
+  if (e != cudaSuccess) {
+    mm_set_error("stage %d launch: %s", stage, cudaGetErrorString(e));
+    return MM_ERR_CUDA;
+  }
+  return MM_OK;
 }
 
 extern "C" mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes) {
@@ -991,9 +1082,8 @@ extern "C" mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes) {
 
 static mm_status apply_A(mm_plan p, cudaStream_t s) {
   RowArgs a{kRowPcgApply, 1.0, nullptr, nullptr};
-  FOR_GROUPS(launch_col_forward(p, G, kSrcGather, nullptr, s));
-  FOR_GROUPS(launch_row(p, G, a, s));
-  FOR_GROUPS(launch_col_inverse(p, G, s));
+  FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
+              L_(launch_col_inverse(p, B, s)));
   return MM_OK;
 }
 
@@ -1058,8 +1148,7 @@ extern "C" mm_status mm_chi2(mm_plan p, const double* map, double lambda, double
   mm_status st = load_map(p, map, s);
   if (st != MM_OK) return st;
   RowArgs a{kRowChi2, lambda, chi2_dev, nullptr};
-  FOR_GROUPS(launch_col_forward(p, G, kSrcGather, nullptr, s));
-  FOR_GROUPS(launch_row(p, G, a, s));
+  FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s)));
   return MM_OK;
 }
 
@@ -1091,8 +1180,7 @@ extern "C" mm_status mm_rfft(mm_plan p, const float* tod, float* spec_out, void*
   MM_ARG(p != nullptr && tod != nullptr && spec_out != nullptr, "NULL argument");
   cudaStream_t s = S(stream);
   RowArgs a{kRowNatural, 1.0, nullptr, reinterpret_cast<float2*>(spec_out)};
-  FOR_GROUPS(launch_col_forward(p, G, kSrcTod, tod, s));
-  FOR_GROUPS(launch_row(p, G, a, s));
+  FOR_BATCHES(L_(launch_col_forward(p, B, kSrcTod, tod, s)); L_(launch_row(p, B, a, s)));
   return MM_OK;
 }
 

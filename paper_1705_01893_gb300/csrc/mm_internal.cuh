@@ -26,9 +26,10 @@ struct ChunkDesc {
 struct Group {
   int M, M1, M2, log_lo;   // w_M^e = tw_hi[e >> log_lo] * tw_lo[e & (2^log_lo - 1)]
   int n_chunks;
+  int batch;               // chunks per batch
   int* chunks;             // device: chunk indices of this group
-  float2* tw_col;          // [M1]  exp(-2 pi i m / M1)
-  float2* tw_row;          // [M2]  exp(-2 pi i m / M2)
+  float2* tw_col;          // per-pass twiddles of the length-M1 DFT (see tw_offset)
+  float2* tw_row;          // per-pass twiddles of the length-M2 DFT
   float2* tw_lo;           // [2^log_lo]          exp(-2 pi i m / M)
   float2* tw_hi;           // [M >> log_lo]        exp(-2 pi i m 2^log_lo / M)
   float2* tw_pack_a;       // [M1]  exp(-2 pi i m / (2M))     (real-pack twiddle, k1 part)
@@ -36,6 +37,15 @@ struct Group {
 };
 
 constexpr int kMaxGroups = 16;
+
+// A batch: `count` consecutive chunks of one group whose four-step intermediates share the
+// ybuf slot.  Batches are sized so the slot (default 32 MB) stays resident in L2 between
+// the column and row passes; they run one after another on the caller's stream.
+struct Batch {
+  int group;
+  int first;          // index into the group's chunk list
+  int count;
+};
 
 }  // namespace mm
 
@@ -51,6 +61,8 @@ struct mm_plan_s {
   int n_groups;
   mm::Group groups[mm::kMaxGroups];
   int* h_chunk_group;
+  mm::Batch* h_batches;
+  int n_batches;
   bool noise_set;
   // device regions inside the caller's workspace
   mm::ChunkDesc* d_desc;
@@ -66,7 +78,7 @@ struct mm_plan_s {
   float* nbar;      // [spec_total] Nbar on the same slots (slot 0: Nbar_0)
   float* nyq;       // [n_chunks] Nbar at the Nyquist bin
   double* c0;       // [n_chunks] (1/n) sum_k w_k / N_k
-  float2* ybuf;     // [spec_total] intermediate of the four-step FFT
+  float2* ybuf;     // one batch's four-step intermediate (L2-resident between passes)
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;
@@ -144,11 +156,45 @@ __device__ __forceinline__ void dft8(float2* v) {
   v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
 }
 
+// v *= exp(DIR * 2 pi i e / 16) for the constant exponents a radix-16 butterfly needs.
+template <int DIR, int E>
+__device__ __forceinline__ float2 w16(float2 v) {
+  constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;
+  constexpr float h = 0.70710678118654752440f;
+  constexpr float cx = E == 1 ? c1 : E == 2 ? h : E == 3 ? s1 : E == 6 ? -h : E == 9 ? -c1 : 0.f;
+  constexpr float sy = E == 1 ? s1 : E == 2 ? h : E == 3 ? c1 : E == 6 ? h : E == 9 ? -s1 : 1.f;
+  constexpr float cy = DIR < 0 ? -sy : sy;
+  if constexpr (E == 4) return mul_i<DIR>(v);
+  return make_float2(v.x * cx - v.y * cy, v.x * cy + v.y * cx);
+}
+
+// DFT of 16 points as 4 x 4: DFT4 over the stride-4 subsequences, constant twiddles
+// w16^(n1 k1), DFT4 over the contiguous quadruples; the result sits 4x4-transposed in
+// registers and is renamed back into natural order.
+template <int DIR>
+__device__ __forceinline__ void dft16(float2* v) {
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) dft4<DIR>(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]);
+  v[5] = w16<DIR, 1>(v[5]);  v[9] = w16<DIR, 2>(v[9]);   v[13] = w16<DIR, 3>(v[13]);
+  v[6] = w16<DIR, 2>(v[6]);  v[10] = w16<DIR, 4>(v[10]); v[14] = w16<DIR, 6>(v[14]);
+  v[7] = w16<DIR, 3>(v[7]);  v[11] = w16<DIR, 6>(v[11]); v[15] = w16<DIR, 9>(v[15]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<DIR>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  float2 t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[i];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2 + 4 * k1];
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void dftR(float2* v) {
   if constexpr (R == 2) dft2<DIR>(v[0], v[1]);
   else if constexpr (R == 4) dft4<DIR>(v[0], v[1], v[2], v[3]);
-  else dft8<DIR>(v);
+  else if constexpr (R == 8) dft8<DIR>(v);
+  else dft16<DIR>(v);
 }
 
 // ----------------------------------------------------------------- shared-memory layouts
@@ -168,13 +214,36 @@ struct RowLayout {
   static constexpr bool kBFast = false;
 };
 
-// One radix-R Stockham pass (auto-sorting, out of place in registers / in place in shared
-// memory): for butterfly j of transform b with k = j mod Ns, gather x[j + r L/R], twiddle
-// by w_{Ns R}^{r k}, DFT_R, scatter to (j - k) R + k + q Ns.
+// Radix plan of a length-L DFT: ceil(log2(L)/4) passes with radices 2^r as equal as
+// possible, larger radices first (4096 = 16.16.16, 2048 = 16.16.8, 512 = 8.8.8).
+__host__ __device__ constexpr int pick_radix(int rem) {
+  const int m = ilog2(rem);
+  const int P = (m + 3) / 4;
+  const int r = (m + P - 1) / P;
+  return 1 << r;
+}
+// Offset of the twiddle table of the pass whose input sub-transforms have length Ns; the
+// pass (Ns, R) stores w_{Ns R}^{r k} at [r * Ns + k], so lanes with consecutive k read
+// consecutive words.
+__host__ __device__ constexpr int tw_offset(int L, int Ns) {
+  int off = 0, ns = 1;
+  while (ns < Ns) {
+    const int r = pick_radix(L / ns);
+    off += ns * r;
+    ns *= r;
+  }
+  return off;
+}
+__host__ __device__ constexpr int tw_size(int L) { return tw_offset(L, L); }
+
+// One radix-R Stockham pass (auto-sorting, in place in shared memory through registers):
+// for butterfly j of transform b with k = j mod Ns, gather x[j + r L/R], twiddle by
+// w_{Ns R}^{r k}, DFT_R, scatter to (j - k) R + k + q Ns.
 template <int L, int NB, class Lay, int T, int DIR, int R, int Ns>
 __device__ __forceinline__ void fft_pass(float2* s, const float2* __restrict__ tw) {
   constexpr int NBF = NB * (L / R);
   constexpr int U = (NBF + T - 1) / T;
+  constexpr int TWO = tw_offset(L, Ns);
   float2 v[U][R];
   int jj[U], bb[U];
 #pragma unroll
@@ -191,7 +260,7 @@ __device__ __forceinline__ void fft_pass(float2* s, const float2* __restrict__ t
       const int k = j % Ns;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(&tw[(r * k) * (L / (Ns * R))]);
+        float2 w = tw[TWO + r * Ns + k];
         if (DIR > 0) w.y = -w.y;
         v[u][r] = cmul(v[u][r], w);
       }
@@ -212,25 +281,40 @@ __device__ __forceinline__ void fft_pass(float2* s, const float2* __restrict__ t
   __syncthreads();
 }
 
-template <int Rem>
-__host__ __device__ constexpr int pick_radix() {
-  return Rem == 2 ? 2 : (ilog2(Rem) % 3 == 0 ? 8 : 4);
-}
-
 template <int L, int NB, class Lay, int T, int DIR, int Ns>
 __device__ __forceinline__ void fft_passes(float2* s, const float2* __restrict__ tw) {
   if constexpr (Ns < L) {
-    constexpr int R = pick_radix<L / Ns>();
+    constexpr int R = pick_radix(L / Ns);
     fft_pass<L, NB, Lay, T, DIR, R, Ns>(s, tw);
     fft_passes<L, NB, Lay, T, DIR, Ns * R>(s, tw);
   }
 }
 
 // NB unnormalised length-L DFTs (kernel exp(DIR 2 pi i jk / L)) in shared memory, natural
-// order in and out.  tw[m] = exp(-2 pi i m / L).  Ends with a __syncthreads.
+// order in and out.  tw: the per-pass tables (tw_size(L) entries, shared or global memory).
+// Ends with a __syncthreads.
 template <int L, int NB, class Lay, int T, int DIR>
 __device__ __forceinline__ void smem_fft(float2* s, const float2* __restrict__ tw) {
   fft_passes<L, NB, Lay, T, DIR, 1>(s, tw);
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Resident CTAs of `kernel` on the whole GPU (opting it in to `smem` bytes of dynamic
+// shared memory on first use); cached per kernel.
+cudaError_t resident_ctas(const void* kernel, int threads, size_t smem, int* out);
+
+// Grid of a persistent kernel: resident CTAs per SM x SMs, at most `work` CTAs.
+template <typename K>
+static cudaError_t persistent_grid(K kernel, int threads, size_t smem, int work, int* grid) {
+  int resident = 0;
+  cudaError_t e = resident_ctas(reinterpret_cast<const void*>(kernel), threads, smem, &resident);
+  if (e != cudaSuccess) return e;
+  *grid = work < resident ? work : resident;
+  return cudaSuccess;
 }
 
 // w_M^e for 0 <= e < M from the two-level table (FP64-accurate entries, FP32 product).
@@ -259,10 +343,10 @@ struct RowArgs {
 // Source of the forward column pass.
 enum ColSrc { kSrcGather = 0, kSrcTod = 1 };
 
-cudaError_t launch_col_forward(const mm_plan_s* p, const Group& g, int src, const float* tod,
+cudaError_t launch_col_forward(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                cudaStream_t st);
-cudaError_t launch_row(const mm_plan_s* p, const Group& g, const RowArgs& a, cudaStream_t st);
-cudaError_t launch_col_inverse(const mm_plan_s* p, const Group& g, cudaStream_t st);
+cudaError_t launch_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
+cudaError_t launch_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st);
 
 }  // namespace mm
 

@@ -19,26 +19,26 @@ struct RowParams {
   const ChunkDesc* desc;
   const int* chunks;
   Group g;
-  float2* ybuf;
+  float2* ybuf;                  // batch slot: chunk ci of the batch at ybuf + ci * M
+  int count;                     // chunks in the batch
   float2* dtab;
-  const float* nbar;
-  const float* nyq;
+  const float* __restrict__ nbar;
+  const float* __restrict__ nyq;
   RowArgs a;
 };
 
 template <int M2, int T>
-__global__ void __launch_bounds__(T) k_row(RowParams q) {
-  extern __shared__ float2 sm[];
+__device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, const float2* tws,
+                                                float* red, int ci, int rA_) {
   using Lay = RowLayout<M2>;
-  __shared__ float red[32];
-  const int c = q.chunks[blockIdx.y];
+  const int c = q.chunks[ci];
   const ChunkDesc d = q.desc[c];
   const int M1 = d.M1, M = d.M;
-  const int rA = blockIdx.x;
+  const int rA = rA_;
   const int rB = (M1 - rA) & (M1 - 1);
   const bool self = rA == rB;
   const int mode = q.a.mode;
-  float2* y = q.ybuf + d.spec;
+  float2* y = q.ybuf + (int64_t)ci * d.M;
   const bool fwd = mode != kRowPcgRhs;
   const bool inv = mode == kRowMessenger || mode == kRowPcgApply || mode == kRowPcgRhs;
 
@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(T) k_row(RowParams q) {
       sm[Lay::at(1, i)] = self ? a : y[(int64_t)rB * M2 + i];
     }
     __syncthreads();
-    smem_fft<M2, 2, Lay, T, -1>(sm, q.g.tw_row);
+    smem_fft<M2, 2, Lay, T, -1>(sm, tws);
   }
 
   // per-mode constants
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(T) k_row(RowParams q) {
       o[M - k] = Xp;
       continue;
     }
-    const float2 Dk = dt[sk], Dp = dt[sp];
-    const float nk = nb[sk], np = nb[sp];
+    const float2 Dk = __ldcs(dt + sk), Dp = __ldcs(dt + sp);
+    const float nk = __ldcs(nb + sk), np = __ldcs(nb + sp);
     if (want_x2) {
       const float2 ek = csub(Dk, Xk), ep = csub(Dp, Xp);
       float t = (ek.x * ek.x + ek.y * ek.y) / (nk + cn);
@@ -169,10 +169,43 @@ __global__ void __launch_bounds__(T) k_row(RowParams q) {
   }
   if (!inv) return;
   __syncthreads();
-  smem_fft<M2, 2, Lay, T, +1>(sm, q.g.tw_row);
+  smem_fft<M2, 2, Lay, T, +1>(sm, tws);
   for (int i = threadIdx.x; i < M2; i += T) {
     y[(int64_t)rA * M2 + i] = cmulc(sm[Lay::at(0, i)], tw_big(q.g, rA * i));
     if (!self) y[(int64_t)rB * M2 + i] = cmulc(sm[Lay::at(1, i)], tw_big(q.g, rB * i));
+  }
+}
+
+template <int M2, int T>
+__global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_row(RowParams q) {
+  extern __shared__ float2 sm[];
+  using Lay = RowLayout<M2>;
+  __shared__ float red[32];
+  const int jobs_pc = q.g.M1 / 2 + 1;
+  const int njobs = q.count * jobs_pc;
+  const int mode = q.a.mode;
+  const bool reads_d = mode == kRowMessenger || mode == kRowPcgRhs || mode == kRowChi2 ||
+                       mode == kRowPcgApply;
+  // per-pass twiddles of the row DFT, staged once per CTA after the 2 rows of data
+  float2* tws = sm + 2 * M2;
+  for (int i = threadIdx.x; i < tw_size(M2); i += T) tws[i] = q.g.tw_row[i];
+  __syncthreads();
+  for (int job = blockIdx.x; job < njobs; job += gridDim.x) {
+    const int ci = job / jobs_pc;
+    const int jn = job + gridDim.x;
+    if (reads_d && jn < njobs && threadIdx.x == 0) {
+      // the next job's spectrum rows of d~ and Nbar into L2
+      const ChunkDesc dn = q.desc[q.chunks[jn / jobs_pc]];
+      const int ra = jn % jobs_pc, rb = (dn.M1 - ra) & (dn.M1 - 1);
+      prefetch_l2(q.dtab + dn.spec + (int64_t)ra * M2, 8 * M2);
+      prefetch_l2(q.nbar + dn.spec + (int64_t)ra * M2, 4 * M2);
+      if (rb != ra) {
+        prefetch_l2(q.dtab + dn.spec + (int64_t)rb * M2, 8 * M2);
+        prefetch_l2(q.nbar + dn.spec + (int64_t)rb * M2, 4 * M2);
+      }
+    }
+    kernel_body_job<M2, T>(q, sm, tws, red, ci, job % jobs_pc);
+    __syncthreads();
   }
 }
 
@@ -181,38 +214,41 @@ constexpr int row_threads(int M2) {
 }
 
 template <int M2>
-static cudaError_t row_m2(const mm_plan_s* p, const Group& g, const RowArgs& a,
+static cudaError_t row_m2(const mm_plan_s* p, const Batch& b, const RowArgs& a,
                           cudaStream_t st) {
   constexpr int T = row_threads(M2);
+  const Group& g = p->groups[b.group];
   RowParams q;
   q.desc = p->d_desc;
-  q.chunks = g.chunks;
+  q.chunks = g.chunks + b.first;
+  q.count = b.count;
   q.g = g;
   q.ybuf = p->ybuf;
   q.dtab = p->dtab;
   q.nbar = p->nbar;
   q.nyq = p->nyq;
   q.a = a;
-  const size_t smem = sizeof(float2) * 2 * M2;
+  const size_t smem = sizeof(float2) * (2 * M2 + tw_size(M2));
   auto k = k_row<M2, T>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int grid = 0;
+  cudaError_t e = persistent_grid(k, T, smem, (g.M1 / 2 + 1) * b.count, &grid);
   if (e != cudaSuccess) return e;
-  k<<<dim3(g.M1 / 2 + 1, g.n_chunks), T, smem, st>>>(q);
+  k<<<grid, T, smem, st>>>(q);
   return cudaGetLastError();
 }
 
-cudaError_t launch_row(const mm_plan_s* p, const Group& g, const RowArgs& a, cudaStream_t st) {
-  switch (g.M2) {
-    case 16: return row_m2<16>(p, g, a, st);
-    case 32: return row_m2<32>(p, g, a, st);
-    case 64: return row_m2<64>(p, g, a, st);
-    case 128: return row_m2<128>(p, g, a, st);
-    case 256: return row_m2<256>(p, g, a, st);
-    case 512: return row_m2<512>(p, g, a, st);
-    case 1024: return row_m2<1024>(p, g, a, st);
-    case 2048: return row_m2<2048>(p, g, a, st);
-    case 4096: return row_m2<4096>(p, g, a, st);
-    case 8192: return row_m2<8192>(p, g, a, st);
+cudaError_t launch_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
+  switch (p->groups[b.group].M2) {
+    case 16: return row_m2<16>(p, b, a, st);
+    case 32: return row_m2<32>(p, b, a, st);
+    case 64: return row_m2<64>(p, b, a, st);
+    case 128: return row_m2<128>(p, b, a, st);
+    case 256: return row_m2<256>(p, b, a, st);
+    case 512: return row_m2<512>(p, b, a, st);
+    case 1024: return row_m2<1024>(p, b, a, st);
+    case 2048: return row_m2<2048>(p, b, a, st);
+    case 4096: return row_m2<4096>(p, b, a, st);
+    case 8192: return row_m2<8192>(p, b, a, st);
   }
   return cudaErrorInvalidValue;
 }
