@@ -103,8 +103,9 @@ mm_status mm_lambda_max(mm_plan p, double* out, void* stream);
 mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int precision,
                                double* map_inout, double* chi2_out, void* stream);
 
-/* Chunks run in batches: a batch's four-step FFT intermediate is sized (32 MB by default,
- * environment variable MM_YBUF_MB) to stay resident in L2 between the column and row passes.
+/* Chunks run in batches that share one four-step FFT intermediate buffer of at most 1 GB by
+ * default (environment variable MM_YBUF_MB, read when the plan is made; a budget of about a
+ * quarter of L2 keeps each batch's intermediate resident in L2 between passes).
  * *n_batches receives their number; batches run one after another on the caller's stream. */
 mm_status mm_plan_batches(mm_plan p, int* n_batches);
 

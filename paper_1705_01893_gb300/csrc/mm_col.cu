@@ -22,6 +22,7 @@ struct ColParams {
   const float* tod;
   float2* ybuf;        // batch slot: chunk ci of the batch at ybuf + ci * M
   int count;           // chunks in the batch
+  int prefetch;        // L2 bulk prefetch of the next tile
   double* acc;         // [n_pix][NC]
 };
 
@@ -51,6 +52,126 @@ __device__ __forceinline__ float gather_sample(const ColParams& q, int64_t s) {
 
 // L2 prefetch (TMA bulk prefetch, no registers or shared memory) of one tile's streamed
 // input: M1 runs of 2*CB consecutive samples of the pointing (or of the source timestream).
+// Four consecutive samples (s a multiple of 4): one 16-byte load per stream.
+__device__ __forceinline__ float4 load_w4(const void* w, int half_w, int64_t s) {
+  if (half_w) {
+    const uint2 b = __ldcs(reinterpret_cast<const uint2*>(static_cast<const __half*>(w) + s));
+    const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&b.x));
+    const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&b.y));
+    return make_float4(lo.x, lo.y, hi.x, hi.y);
+  }
+  return __ldcs(reinterpret_cast<const float4*>(static_cast<const float*>(w) + s));
+}
+
+template <int NC>
+__device__ __forceinline__ float gather_one(const ColParams& q, int p, float cw, float sw) {
+  if (p < 0) return 0.f;
+  if constexpr (NC == 1) {
+    return __ldg(reinterpret_cast<const float*>(q.map4) + p);
+  } else {
+    const float4 m = __ldg(reinterpret_cast<const float4*>(q.map4) + p);
+    return fmaf(sw, m.z, fmaf(cw, m.y, m.x));
+  }
+}
+
+// (P m) for samples s..s+3.
+template <int NC>
+__device__ __forceinline__ float4 gather4(const ColParams& q, int64_t s) {
+  const int4 p = __ldcs(reinterpret_cast<const int4*>(q.pix + s));
+  float4 c = make_float4(0.f, 0.f, 0.f, 0.f), w = c;
+  if constexpr (NC == 3) {
+    c = load_w4(q.cosw, q.half_w, s);
+    w = load_w4(q.sinw, q.half_w, s);
+  }
+  return make_float4(gather_one<NC>(q, p.x, c.x, w.x), gather_one<NC>(q, p.y, c.y, w.y),
+                     gather_one<NC>(q, p.z, c.z, w.z), gather_one<NC>(q, p.w, c.w, w.w));
+}
+
+template <int NC>
+__device__ __forceinline__ void emit_run(double* acc, int p, float a0, float a1, float a2) {
+  if (p < 0) return;
+  double* a = acc + (int64_t)p * NC;
+  atomicAdd(a, f32_to_f64(a0));
+  if constexpr (NC == 3) {
+    atomicAdd(a + 1, f32_to_f64(a1));
+    atomicAdd(a + 2, f32_to_f64(a2));
+  }
+}
+
+// P^T t for samples s..s+3 (t4 = t_s..t_s+3), one lane of a row of 8 lanes (32 samples).
+// Reduce by pixel: runs inside the lane are summed in registers; runs that cross lanes are
+// closed by a linear-recurrence scan over the lanes of the row (S_u = X_u + G_u S_{u+1},
+// X_u = the lane's leading run when it continues the previous lane's trailing run, G_u = the
+// lane is one such run and the next lane continues it).  Each run's first sample's lane
+// issues one FP64 add per component.
+template <int NC>
+__device__ __forceinline__ void scatter4(const ColParams& q, int64_t s, float4 t4, int qpos) {
+  const int4 p4 = __ldcs(reinterpret_cast<const int4*>(q.pix + s));
+  const int p[4] = {p4.x, p4.y, p4.z, p4.w};
+  const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
+  float v[3][4];
+  float4 c = make_float4(0.f, 0.f, 0.f, 0.f), w = c;
+  if constexpr (NC == 3) {
+    c = load_w4(q.cosw, q.half_w, s);
+    w = load_w4(q.sinw, q.half_w, s);
+  }
+  const float cw[4] = {c.x, c.y, c.z, c.w}, sw[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[0][i] = tv[i];
+    v[1][i] = tv[i] * cw[i];
+    v[2][i] = tv[i] * sw[i];
+  }
+  const bool b1 = p[1] != p[0], b2 = p[2] != p[1], b3 = p[3] != p[2];
+  const bool single = !(b1 || b2 || b3);
+  const int f = b1 ? 1 : (b2 ? 2 : (b3 ? 3 : 4));   // leading run [0, f)
+  const int l = b3 ? 3 : (b2 ? 2 : (b1 ? 1 : 0));   // trailing run [l, 4)
+  float lead[3], trail[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lead[k] = 0.f;
+    trail[k] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      lead[k] += i < f ? v[k][i] : 0.f;
+      trail[k] += i >= l ? v[k][i] : 0.f;
+    }
+  }
+  const int prev3 = __shfl_up_sync(0xffffffffu, p[3], 1);
+  const bool cont = qpos != 0 && p[0] == prev3;
+  float S[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) S[k] = cont ? lead[k] : 0.f;
+  bool Gs = cont && single && qpos != 7;
+#pragma unroll
+  for (int d = 1; d < 8; d <<= 1) {
+    float Sd[3];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) Sd[k] = __shfl_down_sync(0xffffffffu, S[k], d);
+    const bool Gd = __shfl_down_sync(0xffffffffu, Gs, d);
+    if (Gs) {
+#pragma unroll
+      for (int k = 0; k < NC; ++k) S[k] += Sd[k];
+    }
+    Gs = Gs && Gd;
+  }
+  float carry[3];
+#pragma unroll
+  for (int k = 0; k < NC; ++k) {
+    const float cd = __shfl_down_sync(0xffffffffu, S[k], 1);
+    carry[k] = qpos != 7 ? cd : 0.f;
+  }
+  if (!(single && cont))
+    emit_run<NC>(q.acc, p[3], trail[0] + carry[0], trail[1] + carry[1], trail[2] + carry[2]);
+  if (!cont && !single) emit_run<NC>(q.acc, p[0], lead[0], lead[1], lead[2]);
+  if (b1 && l > 1) {   // middle run [1, e)
+    const bool two = b2;
+    emit_run<NC>(q.acc, p[1], two ? v[0][1] : v[0][1] + v[0][2], two ? v[1][1] : v[1][1] + v[1][2],
+                 two ? v[2][1] : v[2][1] + v[2][2]);
+  }
+  if (b2 && l > 2) emit_run<NC>(q.acc, p[2], v[0][2], v[1][2], v[2][2]);
+}
+
 template <int M1, int CB, int T, int NC, bool POINTING>
 __device__ __forceinline__ void prefetch_tile(const ColParams& q, int64_t base, int M2) {
   for (int j1 = threadIdx.x; j1 < M1; j1 += T) {
@@ -71,117 +192,116 @@ __device__ __forceinline__ void prefetch_tile(const ColParams& q, int64_t base, 
 // Persistent over the batch's tiles (chunk ci, column block cb); each CTA prefetches its
 // next tile into L2 before working on the current one, so the HBM stream of the pointing
 // overlaps the FFT arithmetic.
+// First-pass sources and last-pass sink of the column DFTs.  Element (b, i) of a tile is
+// column j2 = j2_0 + b, row j1 = i: samples s = base + 2 (i M2 + b) and s + 1.
+template <int NC>
+struct SrcGather {   // z = ((P m)_s, (P m)_s+1), Eq. 1
+  const ColParams* q;
+  int64_t base;
+  int M2;
+  __device__ __forceinline__ float2 operator()(int b, int i) const {
+    const int64_t s = base + 2ll * ((int64_t)i * M2 + b);
+    const int2 p = __ldcs(reinterpret_cast<const int2*>(q->pix + s));
+    float cw0 = 0.f, cw1 = 0.f, sw0 = 0.f, sw1 = 0.f;
+    if constexpr (NC == 3) {
+      if (q->half_w) {
+        const float2 c = __half22float2(__ldcs(reinterpret_cast<const __half2*>(static_cast<const __half*>(q->cosw) + s)));
+        const float2 w = __half22float2(__ldcs(reinterpret_cast<const __half2*>(static_cast<const __half*>(q->sinw) + s)));
+        cw0 = c.x; cw1 = c.y; sw0 = w.x; sw1 = w.y;
+      } else {
+        const float2 c = __ldcs(reinterpret_cast<const float2*>(static_cast<const float*>(q->cosw) + s));
+        const float2 w = __ldcs(reinterpret_cast<const float2*>(static_cast<const float*>(q->sinw) + s));
+        cw0 = c.x; cw1 = c.y; sw0 = w.x; sw1 = w.y;
+      }
+    }
+    return make_float2(gather_one<NC>(*q, p.x, cw0, sw0), gather_one<NC>(*q, p.y, cw1, sw1));
+  }
+};
+
+struct SrcTod {      // z = (d_s, d_s+1)
+  const float* tod;
+  int64_t base;
+  int M2;
+  __device__ __forceinline__ float2 operator()(int b, int i) const {
+    return __ldcs(reinterpret_cast<const float2*>(tod + base + 2ll * ((int64_t)i * M2 + b)));
+  }
+};
+
+struct DstY {        // y[k1][j2] = Z * w_M^(k1 j2): the four-step twiddle on the way out
+  float2* y;
+  const Group* g;
+  int j2_0;
+  int M2;
+  __device__ __forceinline__ void operator()(int b, int k1, float2 v) const {
+    const int j2 = j2_0 + b;
+    y[(int64_t)k1 * M2 + j2] = cmul(v, tw_big(*g, k1 * j2));
+  }
+};
+
+struct SrcY {        // filtered spectrum rows for the inverse column DFTs
+  const float2* y;
+  int j2_0;
+  int M2;
+  __device__ __forceinline__ float2 operator()(int b, int k1) const {
+    return y[(int64_t)k1 * M2 + j2_0 + b];
+  }
+};
+
+// Persistent over the batch's tiles (chunk ci, column block cb).
 template <int M1, int CB, int T, int NC, int SRC>
-__global__ void __launch_bounds__(T) k_col_forward(ColParams q) {
+__global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_forward(ColParams q) {
   extern __shared__ float2 sm[];
   const int M2 = q.g.M2;
   const int tpc = M2 / CB;
   const int ntiles = q.count * tpc;
-  constexpr int RUN = 2 * CB;
-  constexpr int NS = M1 * RUN;
-  float* smf = reinterpret_cast<float*>(sm);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int ci = t / tpc;
     const ChunkDesc d = q.desc[q.chunks[ci]];
     const int j2_0 = (t % tpc) * CB;
     const int64_t base = d.off + 2ll * j2_0;
     const int tn = t + gridDim.x;
-    if (tn < ntiles) {
+    if (q.prefetch && tn < ntiles) {
       const int64_t nb = q.desc[q.chunks[tn / tpc]].off + 2ll * (tn % tpc) * CB;
       prefetch_tile<M1, CB, T, NC, SRC == kSrcGather>(q, nb, M2);
     }
-#pragma unroll 4
-    for (int e = threadIdx.x; e < NS; e += T) {
-      const int j1 = e / RUN, h = e % RUN;
-      const int64_t s = base + 2ll * j1 * M2 + h;
-      float v;
-      if constexpr (SRC == kSrcTod) v = __ldcs(q.tod + s);
-      else v = gather_sample<NC>(q, s);
-      smf[e] = v;  // float2 slot j1*CB + h/2 = column layout element (h/2, j1)
-    }
-    __syncthreads();
-    smem_fft<M1, CB, ColLayout<CB>, T, -1>(sm, q.g.tw_col);
-    float2* y = q.ybuf + (int64_t)ci * d.M;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < M1 * CB; e += T) {
-      const int k1 = e / CB, col = e % CB;
-      const int j2 = j2_0 + col;
-      y[(int64_t)k1 * M2 + j2] = cmul(sm[e], tw_big(q.g, k1 * j2));
-    }
+    const DstY dst{q.ybuf + (int64_t)ci * d.M, &q.g, j2_0, M2};
+    if constexpr (SRC == kSrcTod)
+      smem_fft<M1, CB, ColLayout<CB>, T, -1>(sm, q.g.tw_col, SrcTod{q.tod, base, M2}, dst);
+    else
+      smem_fft<M1, CB, ColLayout<CB>, T, -1>(sm, q.g.tw_col, SrcGather<NC>{&q, base, M2}, dst);
     __syncthreads();
   }
 }
 
 template <int M1, int CB, int T, int NC>
-__global__ void __launch_bounds__(T) k_col_inverse(ColParams q) {
+__global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse(ColParams q) {
   extern __shared__ float2 sm[];
   const int M2 = q.g.M2;
   const int tpc = M2 / CB;
   const int ntiles = q.count * tpc;
   constexpr int RUN = 2 * CB;
   constexpr int NS = M1 * RUN;
-  static_assert(NS % 32 == 0 && T % 32 == 0, "warp-uniform scatter loop");
+  static_assert(RUN == 32 && (NS / 4) % T == 0 && T % 32 == 0,
+                "rows of 8 lanes and a warp-uniform scatter loop");
   const float* smf = reinterpret_cast<const float*>(sm);
-  const int lane = threadIdx.x & 31;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int ci = t / tpc;
     const ChunkDesc d = q.desc[q.chunks[ci]];
     const int j2_0 = (t % tpc) * CB;
     const int tn = t + gridDim.x;
-    if (tn < ntiles) {
+    if (q.prefetch && tn < ntiles) {
       const int64_t nb = q.desc[q.chunks[tn / tpc]].off + 2ll * (tn % tpc) * CB;
       prefetch_tile<M1, CB, T, NC, true>(q, nb, M2);
     }
-    const float2* y = q.ybuf + (int64_t)ci * d.M;
-#pragma unroll 4
-    for (int e = threadIdx.x; e < M1 * CB; e += T) {
-      const int k1 = e / CB, col = e % CB;
-      sm[e] = y[(int64_t)k1 * M2 + j2_0 + col];
-    }
-    __syncthreads();
-    smem_fft<M1, CB, ColLayout<CB>, T, +1>(sm, q.g.tw_col);
-
+    smem_fft<M1, CB, ColLayout<CB>, T, +1>(sm, q.g.tw_col,
+                                           SrcY{q.ybuf + (int64_t)ci * d.M, j2_0, M2});
     const int64_t base = d.off + 2ll * j2_0;
-    for (int e = threadIdx.x; e < NS; e += T) {
+#pragma unroll 2
+    for (int e4 = threadIdx.x; e4 < NS / 4; e4 += T) {
+      const int e = 4 * e4;
       const int j1 = e / RUN, h = e % RUN;
       const int64_t s = base + 2ll * j1 * M2 + h;
-      const float tv = smf[e];
-      const int p = __ldcs(q.pix + s);
-      float v0 = tv, v1 = 0.f, v2 = 0.f;
-      if constexpr (NC == 3) {
-        v1 = tv * load_w(q.cosw, q.half_w, s);
-        v2 = tv * load_w(q.sinw, q.half_w, s);
-      }
-      // Runs of equal pixel among this warp's contiguous samples: the head lane of each run
-      // gathers the run total by suffix doubling (as many steps as the longest run needs)
-      // and issues the FP64 adds.
-      const int pp = __shfl_up_sync(0xffffffffu, p, 1);
-      const bool head = (lane == 0) || (h == 0) || (pp != p);
-      const unsigned H = __ballot_sync(0xffffffffu, head);
-      const unsigned after = H & (0xfffffffeu << lane);
-      const int end = after ? (__ffs(after) - 2) : 31;
-      const int maxlen =
-          (int)__reduce_max_sync(0xffffffffu, head ? (unsigned)(end - lane + 1) : 0u);
-      for (int dd = 1; dd < maxlen; dd <<= 1) {
-        const float a0 = __shfl_down_sync(0xffffffffu, v0, dd);
-        float a1 = 0.f, a2 = 0.f;
-        if constexpr (NC == 3) {
-          a1 = __shfl_down_sync(0xffffffffu, v1, dd);
-          a2 = __shfl_down_sync(0xffffffffu, v2, dd);
-        }
-        if (lane + dd <= end) {
-          v0 += a0;
-          if constexpr (NC == 3) { v1 += a1; v2 += a2; }
-        }
-      }
-      if (head && p >= 0) {
-        double* a = q.acc + (int64_t)p * NC;
-        atomicAdd(a, (double)v0);
-        if constexpr (NC == 3) {
-          atomicAdd(a + 1, (double)v1);
-          atomicAdd(a + 2, (double)v2);
-        }
-      }
+      scatter4<NC>(q, s, *reinterpret_cast<const float4*>(smf + e), (h >> 2) & 7);
     }
     __syncthreads();
   }
@@ -201,6 +321,7 @@ static ColParams make_params(const mm_plan_s* p, const Batch& b, const float* to
   q.desc = p->d_desc;
   q.chunks = g.chunks + b.first;
   q.count = b.count;
+  q.prefetch = p->prefetch;
   q.g = g;
   q.pix = p->pix;
   q.cosw = p->cosw;

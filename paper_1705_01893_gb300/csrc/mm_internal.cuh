@@ -6,6 +6,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "../../include/mm.h"
 
 namespace mm {
@@ -63,6 +65,7 @@ struct mm_plan_s {
   int* h_chunk_group;
   mm::Batch* h_batches;
   int n_batches;
+  int prefetch;     // L2 bulk prefetch of each persistent CTA's next tile (MM_PREFETCH)
   bool noise_set;
   // device regions inside the caller's workspace
   mm::ChunkDesc* d_desc;
@@ -236,11 +239,19 @@ __host__ __device__ constexpr int tw_offset(int L, int Ns) {
 }
 __host__ __device__ constexpr int tw_size(int L) { return tw_offset(L, L); }
 
-// One radix-R Stockham pass (auto-sorting, in place in shared memory through registers):
-// for butterfly j of transform b with k = j mod Ns, gather x[j + r L/R], twiddle by
-// w_{Ns R}^{r k}, DFT_R, scatter to (j - k) R + k + q Ns.
-template <int L, int NB, class Lay, int T, int DIR, int R, int Ns>
-__device__ __forceinline__ void fft_pass(float2* s, const float2* __restrict__ tw) {
+// Tag: a pass reads from / writes to the shared-memory buffer itself.
+struct SmemIO {};
+
+// One radix-R Stockham pass (auto-sorting): for butterfly j of transform b with k = j mod Ns,
+// gather x[j + r L/R], twiddle by w_{Ns R}^{r k}, DFT_R, scatter to (j - k) R + k + q Ns.
+// Input comes from shared memory or, for a first pass, from src(b, i); output goes to
+// shared memory or, for a last pass, to dst(b, i, value) (where (j - k) R + k = j, so
+// consecutive threads write consecutive i).  In place in shared memory through registers.
+template <int L, int NB, class Lay, int T, int DIR, int R, int Ns, class Src, class Dst>
+__device__ __forceinline__ void fft_pass_io(float2* s, const float2* __restrict__ tw,
+                                            const Src& src, const Dst& dst) {
+  constexpr bool kSrcSm = std::is_same<Src, SmemIO>::value;
+  constexpr bool kDstSm = std::is_same<Dst, SmemIO>::value;
   constexpr int NBF = NB * (L / R);
   constexpr int U = (NBF + T - 1) / T;
   constexpr int TWO = tw_offset(L, Ns);
@@ -255,7 +266,10 @@ __device__ __forceinline__ void fft_pass(float2* s, const float2* __restrict__ t
     else { j = g % (L / R); b = g / (L / R); }
     jj[u] = j; bb[u] = b;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[u][r] = s[Lay::at(b, j + r * (L / R))];
+    for (int r = 0; r < R; ++r) {
+      if constexpr (kSrcSm) v[u][r] = s[Lay::at(b, j + r * (L / R))];
+      else v[u][r] = src(b, j + r * (L / R));
+    }
     if constexpr (Ns > 1) {
       const int k = j % Ns;
 #pragma unroll
@@ -267,7 +281,7 @@ __device__ __forceinline__ void fft_pass(float2* s, const float2* __restrict__ t
     }
     dftR<R, DIR>(v[u]);
   }
-  __syncthreads();
+  if constexpr (kSrcSm && kDstSm) __syncthreads();
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int g = threadIdx.x + u * T;
@@ -276,26 +290,38 @@ __device__ __forceinline__ void fft_pass(float2* s, const float2* __restrict__ t
     const int k = j % Ns;
     const int o = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) s[Lay::at(b, o + r * Ns)] = v[u][r];
+    for (int r = 0; r < R; ++r) {
+      if constexpr (kDstSm) s[Lay::at(b, o + r * Ns)] = v[u][r];
+      else dst(b, o + r * Ns, v[u][r]);
+    }
   }
-  __syncthreads();
+  if constexpr (kDstSm) __syncthreads();
 }
 
-template <int L, int NB, class Lay, int T, int DIR, int Ns>
-__device__ __forceinline__ void fft_passes(float2* s, const float2* __restrict__ tw) {
+template <int L, int NB, class Lay, int T, int DIR, int Ns, class Src, class Dst>
+__device__ __forceinline__ void fft_passes_io(float2* s, const float2* __restrict__ tw,
+                                              const Src& src, const Dst& dst) {
   if constexpr (Ns < L) {
     constexpr int R = pick_radix(L / Ns);
-    fft_pass<L, NB, Lay, T, DIR, R, Ns>(s, tw);
-    fft_passes<L, NB, Lay, T, DIR, Ns * R>(s, tw);
+    constexpr bool first = Ns == 1, last = Ns * R == L;
+    if constexpr (first && last) fft_pass_io<L, NB, Lay, T, DIR, R, Ns, Src, Dst>(s, tw, src, dst);
+    else if constexpr (first)
+      fft_pass_io<L, NB, Lay, T, DIR, R, Ns, Src, SmemIO>(s, tw, src, SmemIO{});
+    else if constexpr (last)
+      fft_pass_io<L, NB, Lay, T, DIR, R, Ns, SmemIO, Dst>(s, tw, SmemIO{}, dst);
+    else fft_pass_io<L, NB, Lay, T, DIR, R, Ns, SmemIO, SmemIO>(s, tw, SmemIO{}, SmemIO{});
+    fft_passes_io<L, NB, Lay, T, DIR, Ns * R>(s, tw, src, dst);
   }
 }
 
-// NB unnormalised length-L DFTs (kernel exp(DIR 2 pi i jk / L)) in shared memory, natural
-// order in and out.  tw: the per-pass tables (tw_size(L) entries, shared or global memory).
-// Ends with a __syncthreads.
-template <int L, int NB, class Lay, int T, int DIR>
-__device__ __forceinline__ void smem_fft(float2* s, const float2* __restrict__ tw) {
-  fft_passes<L, NB, Lay, T, DIR, 1>(s, tw);
+// NB unnormalised length-L DFTs (kernel exp(DIR 2 pi i jk / L)), natural order in and out.
+// Input from src (or shared memory), output to dst (or shared memory).  tw: the per-pass
+// tables (tw_size(L) entries).  A shared-memory destination ends with a __syncthreads; a
+// caller that reads from a functor must have finished every earlier use of `s`.
+template <int L, int NB, class Lay, int T, int DIR, class Src = SmemIO, class Dst = SmemIO>
+__device__ __forceinline__ void smem_fft(float2* s, const float2* __restrict__ tw,
+                                         const Src& src = Src{}, const Dst& dst = Dst{}) {
+  fft_passes_io<L, NB, Lay, T, DIR, 1>(s, tw, src, dst);
 }
 
 // Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (p and bytes multiples of 16).
@@ -315,6 +341,18 @@ static cudaError_t persistent_grid(K kernel, int threads, size_t smem, int work,
   if (e != cudaSuccess) return e;
   *grid = work < resident ? work : resident;
   return cudaSuccess;
+}
+
+// Exact FP32 -> FP64 widening with integer operations only (sign, exponent rebias, mantissa
+// shift), keeping the conversion off GB300's narrow FP64 pipe; the FP64 additions then
+// happen in the L2 atomic units.  Zero and subnormal inputs give +-0 (|x| < 1.2e-38).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long ed = e == 0xffu ? 0x7ffull : (unsigned long long)(e + 896u);
+  const unsigned long long mag = (ed << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)(e == 0u ? sgn : (sgn | mag)));
 }
 
 // w_M^e for 0 <= e < M from the two-level table (FP64-accurate entries, FP32 product).

@@ -21,10 +21,33 @@ struct RowParams {
   Group g;
   float2* ybuf;                  // batch slot: chunk ci of the batch at ybuf + ci * M
   int count;                     // chunks in the batch
+  int prefetch;                  // L2 bulk prefetch of the next job's d~ and Nbar rows
   float2* dtab;
   const float* __restrict__ nbar;
   const float* __restrict__ nyq;
   RowArgs a;
+};
+
+// First pass of the forward row DFTs reads rows rA (b = 0) and rB (b = 1) straight from the
+// intermediate; the last inverse pass writes them back with the conjugate four-step twiddle.
+struct SrcRows {
+  const float2* y;
+  int offA, offB;
+  __device__ __forceinline__ float2 operator()(int b, int i) const {
+    return y[(b ? offB : offA) + i];
+  }
+};
+
+struct DstRows {
+  float2* y;
+  const Group* g;
+  int rA, rB;
+  bool self;
+  __device__ __forceinline__ void operator()(int b, int i, float2 v) const {
+    if (b && self) return;
+    const int r = b ? rB : rA;
+    y[(int64_t)r * g->M2 + i] = cmulc(v, tw_big(*g, r * i));
+  }
 };
 
 template <int M2, int T>
@@ -43,13 +66,8 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   const bool inv = mode == kRowMessenger || mode == kRowPcgApply || mode == kRowPcgRhs;
 
   if (fwd) {
-    for (int i = threadIdx.x; i < M2; i += T) {
-      const float2 a = y[(int64_t)rA * M2 + i];
-      sm[Lay::at(0, i)] = a;
-      sm[Lay::at(1, i)] = self ? a : y[(int64_t)rB * M2 + i];
-    }
-    __syncthreads();
-    smem_fft<M2, 2, Lay, T, -1>(sm, tws);
+    const SrcRows src{y, rA * M2, rB * M2};
+    smem_fft<M2, 2, Lay, T, -1>(sm, tws, src);
   }
 
   // per-mode constants
@@ -169,11 +187,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   }
   if (!inv) return;
   __syncthreads();
-  smem_fft<M2, 2, Lay, T, +1>(sm, tws);
-  for (int i = threadIdx.x; i < M2; i += T) {
-    y[(int64_t)rA * M2 + i] = cmulc(sm[Lay::at(0, i)], tw_big(q.g, rA * i));
-    if (!self) y[(int64_t)rB * M2 + i] = cmulc(sm[Lay::at(1, i)], tw_big(q.g, rB * i));
-  }
+  smem_fft<M2, 2, Lay, T, +1>(sm, tws, SmemIO{}, DstRows{y, &q.g, rA, rB, self});
 }
 
 template <int M2, int T>
@@ -193,7 +207,7 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_row(RowParams q) {
   for (int job = blockIdx.x; job < njobs; job += gridDim.x) {
     const int ci = job / jobs_pc;
     const int jn = job + gridDim.x;
-    if (reads_d && jn < njobs && threadIdx.x == 0) {
+    if (q.prefetch && reads_d && jn < njobs && threadIdx.x == 0) {
       // the next job's spectrum rows of d~ and Nbar into L2
       const ChunkDesc dn = q.desc[q.chunks[jn / jobs_pc]];
       const int ra = jn % jobs_pc, rb = (dn.M1 - ra) & (dn.M1 - 1);
@@ -222,6 +236,7 @@ static cudaError_t row_m2(const mm_plan_s* p, const Batch& b, const RowArgs& a,
   q.desc = p->d_desc;
   q.chunks = g.chunks + b.first;
   q.count = b.count;
+  q.prefetch = p->prefetch;
   q.g = g;
   q.ybuf = p->ybuf;
   q.dtab = p->dtab;
