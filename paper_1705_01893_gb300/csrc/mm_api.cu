@@ -107,7 +107,7 @@ static size_t tw_count(int M, int M1, int M2) {
 // -------------------------------------------------------------------- workspace layout
 struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
-      ybuf, scal, total;
+      ybuf, scal, tpix, tcos, tsin, total;
   int n_groups;
   int gM[kMaxGroups], gM1[kMaxGroups], gM2[kMaxGroups], gcount[kMaxGroups], gbatch[kMaxGroups];
   std::vector<int> chunk_group;
@@ -126,7 +126,7 @@ static size_t ybuf_budget() {
 }
 
 static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, int ncomp,
-                             Layout* L) {
+                             int wdtype, Layout* L) {
   MM_ARG(n_chunks >= 1, "n_chunks must be >= 1 (got %d)", n_chunks);
   MM_ARG(off != nullptr, "offsets is NULL");
   MM_ARG(n_pix >= 1 && n_pix < (int64_t(1) << 31), "n_pix out of range (%lld)", (long long)n_pix);
@@ -193,6 +193,11 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->c0 = take(sizeof(double) * n_chunks);
   L->ybuf = take(ybytes);
   L->scal = take(sizeof(double) * kScalCount);
+  // pointing copied into column-tile order for the streaming passes
+  const size_t wb = ncomp == 3 ? (wdtype == MM_W_F16 ? 2 : 4) : 0;
+  L->tpix = take(sizeof(int32_t) * (size_t)L->n_total);
+  L->tcos = take(wb * (size_t)L->n_total);
+  L->tsin = take(wb * (size_t)L->n_total);
   L->total = o;
   return MM_OK;
 }
@@ -203,7 +208,7 @@ extern "C" mm_status mm_plan_workspace_size(int n_chunks, const int64_t* offsets
   MM_ARG(weight_dtype == MM_W_F32 || weight_dtype == MM_W_F16, "bad weight_dtype %d",
          weight_dtype);
   Layout L;
-  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, &L);
+  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, weight_dtype, &L);
   if (st != MM_OK) return st;
   *bytes = L.total;
   return MM_OK;
@@ -721,7 +726,7 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   MM_ARG(weight_dtype == MM_W_F32 || weight_dtype == MM_W_F16, "bad weight_dtype %d",
          weight_dtype);
   Layout L;
-  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, &L);
+  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, weight_dtype, &L);
   if (st != MM_OK) return st;
   MM_ARG((ncomp == 3) == (cos2psi != nullptr && sin2psi != nullptr),
          "cos2psi/sin2psi must be given iff ncomp == 3");
@@ -740,10 +745,6 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   p->n_pix = n_pix; p->n_total = L.n_total; p->spec_total = L.spec_total;
   p->rcond_min = rcond_min; p->pix = pix; p->cosw = cos2psi; p->sinw = sin2psi;
   p->noise_set = false;
-  {
-    const char* e = getenv("MM_PREFETCH");
-    p->prefetch = e ? atoi(e) != 0 : 0;
-  }
   char* ws = static_cast<char*>(workspace);
   p->d_desc = reinterpret_cast<ChunkDesc*>(ws + L.desc);
   int* d_chunks = reinterpret_cast<int*>(ws + L.chunks);
@@ -763,6 +764,9 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   p->ybuf = reinterpret_cast<float2*>(ws + L.ybuf);
   p->scal = reinterpret_cast<double*>(ws + L.scal);
   p->params = reinterpret_cast<double*>(ws + L.params);
+  p->tpix = reinterpret_cast<int32_t*>(ws + L.tpix);
+  p->tcos = ncomp == 3 ? static_cast<void*>(ws + L.tcos) : nullptr;
+  p->tsin = ncomp == 3 ? static_cast<void*>(ws + L.tsin) : nullptr;
 
   // host descriptors, grouped chunk lists
   p->h_desc = new (std::nothrow) ChunkDesc[n_chunks];
@@ -841,6 +845,7 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   if ((e = cudaMemsetAsync(p->acc, 0, sizeof(double) * ncomp * n_pix, s)) != cudaSuccess) return fail("memset", e);
   if (L.n_total > 0)
     k_hits<<<blocks_for(L.n_total, 256), 256, 0, s>>>(pix, L.n_total, n_pix, p->hits, p->scal + kScalTmp);
+  if ((e = launch_tile_pointing(p, s)) != cudaSuccess) return fail("pointing tile copy", e);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail("set-up kernels", e);
   double flag = 0.0;
   if ((e = cudaMemcpyAsync(&flag, p->scal + kScalTmp, sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

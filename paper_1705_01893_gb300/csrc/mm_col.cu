@@ -14,6 +14,8 @@ struct ColParams {
   const ChunkDesc* desc;
   const int* chunks;
   Group g;
+  // pointing in tile order: the samples of tile (chunk, column block cb) are contiguous,
+  // row j1 after row j1 - 1, 2*CB samples per row (see k_tile_pointing)
   const int32_t* __restrict__ pix;
   const void* cosw;
   const void* sinw;
@@ -22,7 +24,6 @@ struct ColParams {
   const float* tod;
   float2* ybuf;        // batch slot: chunk ci of the batch at ybuf + ci * M
   int count;           // chunks in the batch
-  int prefetch;        // L2 bulk prefetch of the next tile
   double* acc;         // [n_pix][NC]
 };
 
@@ -50,8 +51,6 @@ __device__ __forceinline__ float gather_sample(const ColParams& q, int64_t s) {
   }
 }
 
-// L2 prefetch (TMA bulk prefetch, no registers or shared memory) of one tile's streamed
-// input: M1 runs of 2*CB consecutive samples of the pointing (or of the source timestream).
 // Four consecutive samples (s a multiple of 4): one 16-byte load per stream.
 __device__ __forceinline__ float4 load_w4(const void* w, int half_w, int64_t s) {
   if (half_w) {
@@ -172,35 +171,14 @@ __device__ __forceinline__ void scatter4(const ColParams& q, int64_t s, float4 t
   if (b2 && l > 2) emit_run<NC>(q.acc, p[2], v[0][2], v[1][2], v[2][2]);
 }
 
-template <int M1, int CB, int T, int NC, bool POINTING>
-__device__ __forceinline__ void prefetch_tile(const ColParams& q, int64_t base, int M2) {
-  for (int j1 = threadIdx.x; j1 < M1; j1 += T) {
-    const int64_t s = base + 2ll * j1 * M2;
-    if constexpr (POINTING) {
-      prefetch_l2(q.pix + s, 8 * CB);
-      if constexpr (NC == 3) {
-        const int wb = q.half_w ? 2 : 4;
-        prefetch_l2(static_cast<const char*>(q.cosw) + s * wb, 2 * CB * wb);
-        prefetch_l2(static_cast<const char*>(q.sinw) + s * wb, 2 * CB * wb);
-      }
-    } else {
-      prefetch_l2(q.tod + s, 8 * CB);
-    }
-  }
-}
-
-// Persistent over the batch's tiles (chunk ci, column block cb); each CTA prefetches its
-// next tile into L2 before working on the current one, so the HBM stream of the pointing
-// overlaps the FFT arithmetic.
 // First-pass sources and last-pass sink of the column DFTs.  Element (b, i) of a tile is
 // column j2 = j2_0 + b, row j1 = i: samples s = base + 2 (i M2 + b) and s + 1.
-template <int NC>
-struct SrcGather {   // z = ((P m)_s, (P m)_s+1), Eq. 1
+template <int NC, int CB>
+struct SrcGather {   // z = ((P m)_s, (P m)_s+1), Eq. 1; tile-ordered pointing from `tbase`
   const ColParams* q;
-  int64_t base;
-  int M2;
+  int64_t tbase;
   __device__ __forceinline__ float2 operator()(int b, int i) const {
-    const int64_t s = base + 2ll * ((int64_t)i * M2 + b);
+    const int64_t s = tbase + 2 * (CB * i + b);
     const int2 p = __ldcs(reinterpret_cast<const int2*>(q->pix + s));
     float cw0 = 0.f, cw1 = 0.f, sw0 = 0.f, sw1 = 0.f;
     if constexpr (NC == 3) {
@@ -257,18 +235,15 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_forward(ColParams
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int ci = t / tpc;
     const ChunkDesc d = q.desc[q.chunks[ci]];
-    const int j2_0 = (t % tpc) * CB;
-    const int64_t base = d.off + 2ll * j2_0;
-    const int tn = t + gridDim.x;
-    if (q.prefetch && tn < ntiles) {
-      const int64_t nb = q.desc[q.chunks[tn / tpc]].off + 2ll * (tn % tpc) * CB;
-      prefetch_tile<M1, CB, T, NC, SRC == kSrcGather>(q, nb, M2);
-    }
+    const int cb = t % tpc;
+    const int j2_0 = cb * CB;
     const DstY dst{q.ybuf + (int64_t)ci * d.M, &q.g, j2_0, M2};
     if constexpr (SRC == kSrcTod)
-      smem_fft<M1, CB, ColLayout<CB>, T, -1>(sm, q.g.tw_col, SrcTod{q.tod, base, M2}, dst);
+      smem_fft<M1, CB, ColLayout<CB>, T, -1>(sm, q.g.tw_col,
+                                             SrcTod{q.tod, d.off + 2ll * j2_0, M2}, dst);
     else
-      smem_fft<M1, CB, ColLayout<CB>, T, -1>(sm, q.g.tw_col, SrcGather<NC>{&q, base, M2}, dst);
+      smem_fft<M1, CB, ColLayout<CB>, T, -1>(
+          sm, q.g.tw_col, SrcGather<NC, CB>{&q, d.off + (int64_t)cb * (2 * CB * M1)}, dst);
     __syncthreads();
   }
 }
@@ -287,21 +262,15 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse(ColParams
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int ci = t / tpc;
     const ChunkDesc d = q.desc[q.chunks[ci]];
-    const int j2_0 = (t % tpc) * CB;
-    const int tn = t + gridDim.x;
-    if (q.prefetch && tn < ntiles) {
-      const int64_t nb = q.desc[q.chunks[tn / tpc]].off + 2ll * (tn % tpc) * CB;
-      prefetch_tile<M1, CB, T, NC, true>(q, nb, M2);
-    }
+    const int cb = t % tpc;
     smem_fft<M1, CB, ColLayout<CB>, T, +1>(sm, q.g.tw_col,
-                                           SrcY{q.ybuf + (int64_t)ci * d.M, j2_0, M2});
-    const int64_t base = d.off + 2ll * j2_0;
+                                           SrcY{q.ybuf + (int64_t)ci * d.M, cb * CB, M2});
+    // tile-ordered pointing: the tile's samples are contiguous, in the same order as t
+    const int64_t tbase = d.off + (int64_t)cb * NS;
 #pragma unroll 2
     for (int e4 = threadIdx.x; e4 < NS / 4; e4 += T) {
       const int e = 4 * e4;
-      const int j1 = e / RUN, h = e % RUN;
-      const int64_t s = base + 2ll * j1 * M2 + h;
-      scatter4<NC>(q, s, *reinterpret_cast<const float4*>(smf + e), (h >> 2) & 7);
+      scatter4<NC>(q, tbase + e, *reinterpret_cast<const float4*>(smf + e), e4 & 7);
     }
     __syncthreads();
   }
@@ -315,17 +284,52 @@ constexpr int col_threads(int M1) {
 }
 
 
+// Copy the caller's pointing into tile order: sample 2 (j1 M2 + j2) + h of a chunk goes to
+// cb (2 CB M1) + j1 (2 CB) + 2 (j2 - cb CB) + h with cb = j2 / CB.  Coalesced writes.
+template <int CB>
+__global__ void k_tile_pointing(const int32_t* __restrict__ pix, const void* cosw, const void* sinw,
+                                int wbytes, int64_t off, int M1, int M2, int32_t* __restrict__ tpix,
+                                void* tcos, void* tsin) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o >= 2ll * M1 * M2) return;
+  const int64_t tile = 2ll * CB * M1;
+  const int cb = (int)(o / tile);
+  const int r = (int)(o % tile);
+  const int j1 = r / (2 * CB), w = r % (2 * CB);
+  const int64_t src = off + 2ll * ((int64_t)j1 * M2 + cb * CB) + w;
+  tpix[off + o] = pix[src];
+  if (cosw) {
+    if (wbytes == 2) {
+      static_cast<__half*>(tcos)[off + o] = static_cast<const __half*>(cosw)[src];
+      static_cast<__half*>(tsin)[off + o] = static_cast<const __half*>(sinw)[src];
+    } else {
+      static_cast<float*>(tcos)[off + o] = static_cast<const float*>(cosw)[src];
+      static_cast<float*>(tsin)[off + o] = static_cast<const float*>(sinw)[src];
+    }
+  }
+}
+
+cudaError_t launch_tile_pointing(const mm_plan_s* p, cudaStream_t st) {
+  const int wb = p->wdtype == MM_W_F16 ? 2 : 4;
+  for (int c = 0; c < p->n_chunks; ++c) {
+    const ChunkDesc& d = p->h_desc[c];
+    const int64_t n = d.n;
+    k_tile_pointing<kColCB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        p->pix, p->cosw, p->sinw, wb, d.off, d.M1, d.M2, p->tpix, p->tcos, p->tsin);
+  }
+  return cudaGetLastError();
+}
+
 static ColParams make_params(const mm_plan_s* p, const Batch& b, const float* tod) {
   ColParams q;
   const Group& g = p->groups[b.group];
   q.desc = p->d_desc;
   q.chunks = g.chunks + b.first;
   q.count = b.count;
-  q.prefetch = p->prefetch;
   q.g = g;
-  q.pix = p->pix;
-  q.cosw = p->cosw;
-  q.sinw = p->sinw;
+  q.pix = p->tpix;
+  q.cosw = p->tcos;
+  q.sinw = p->tsin;
   q.half_w = p->wdtype == MM_W_F16;
   q.map4 = p->map4;
   q.tod = tod;

@@ -65,7 +65,6 @@ struct mm_plan_s {
   int* h_chunk_group;
   mm::Batch* h_batches;
   int n_batches;
-  int prefetch;     // L2 bulk prefetch of each persistent CTA's next tile (MM_PREFETCH)
   bool noise_set;
   // device regions inside the caller's workspace
   mm::ChunkDesc* d_desc;
@@ -85,6 +84,9 @@ struct mm_plan_s {
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;
+  int32_t* tpix;    // pointing copied into column-tile order (see k_tile_pointing)
+  void* tcos;
+  void* tsin;
 };
 
 namespace mm {
@@ -385,6 +387,7 @@ cudaError_t launch_col_forward(const mm_plan_s* p, const Batch& b, int src, cons
                                cudaStream_t st);
 cudaError_t launch_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
 cudaError_t launch_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st);
+cudaError_t launch_tile_pointing(const mm_plan_s* p, cudaStream_t st);
 
 }  // namespace mm
 

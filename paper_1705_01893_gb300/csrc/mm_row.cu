@@ -21,7 +21,6 @@ struct RowParams {
   Group g;
   float2* ybuf;                  // batch slot: chunk ci of the batch at ybuf + ci * M
   int count;                     // chunks in the batch
-  int prefetch;                  // L2 bulk prefetch of the next job's d~ and Nbar rows
   float2* dtab;
   const float* __restrict__ nbar;
   const float* __restrict__ nyq;
@@ -91,85 +90,115 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   auto filt = [&](float2 X, float2 D, float nbv) -> float2 {
     if (mode == kRowMessenger) {
       if (lam_inf) return cscale(D, sc);
-      const float r = sc / (lt + nbv);
+      const float r = __fdividef(sc, lt + nbv);
       return make_float2((lt * D.x + nbv * X.x) * r, (lt * D.y + nbv * X.y) * r);
     }
-    if (mode == kRowPcgApply) return cscale(X, sc / (nbv + tau));
-    return cscale(D, sc / (nbv + tau));  // kRowPcgRhs
+    if (mode == kRowPcgApply) return cscale(X, __fdividef(sc, nbv + tau));
+    return cscale(D, __fdividef(sc, nbv + tau));  // kRowPcgRhs
   };
   const bool want_x2 = q.a.chi2 != nullptr &&
                        (mode == kRowMessenger || mode == kRowChi2 || mode == kRowPcgRhs);
+  const bool spec_out = mode == kRowSpectrum || mode == kRowNatural;
+  const bool load_d = !spec_out && mode != kRowPcgApply;
 
-  for (int p = threadIdx.x; p < M2; p += T) {
-    int qs, qi;  // partner slot (0 = row rA, 1 = row rB) and index
-    if (!self) { qs = 1; qi = M2 - 1 - p; }
-    else if (rA == 0) { qs = 0; qi = (M2 - p) & (M2 - 1); if (p > qi) continue; }
-    else { qs = 0; qi = M2 - 1 - p; if (p > qi) continue; }
-    const int rowq = qs ? rB : rA;
-    const int sk = rA * M2 + p, sp = rowq * M2 + qi;   // spectrum slots of k and M-k
-    const float2 Zk = fwd ? sm[Lay::at(0, p)] : make_float2(0.f, 0.f);
-    const float2 Zp = fwd ? sm[Lay::at(qs, qi)] : make_float2(0.f, 0.f);
+  // Pairs (k, M - k): p in row rA with partner qi in row rB (or in row rA itself when the
+  // row pairs with itself).  PB pairs per thread have their d~ / Nbar loads in flight at once.
+  constexpr int PB = 4;
+  for (int p0 = threadIdx.x; p0 < M2; p0 += PB * T) {
+    float2 Dk[PB], Dp[PB];
+    float nk[PB], np[PB];
+    int qsv[PB], qiv[PB];
+    bool act[PB];
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      const int p = p0 + u * T;
+      int qs = 1, qi = M2 - 1 - p;
+      bool a = p < M2;
+      if (self) {
+        qs = 0;
+        qi = rA == 0 ? ((M2 - p) & (M2 - 1)) : (M2 - 1 - p);
+        a = a && p <= qi;
+      }
+      act[u] = a; qsv[u] = qs; qiv[u] = qi;
+      Dk[u] = Dp[u] = make_float2(0.f, 0.f);
+      nk[u] = np[u] = 0.f;
+      if (a && !spec_out) {
+        const int sk = rA * M2 + p, sp = (qs ? rB : rA) * M2 + qi;
+        if (load_d) { Dk[u] = __ldcs(dt + sk); Dp[u] = __ldcs(dt + sp); }
+        nk[u] = __ldcs(nb + sk);
+        np[u] = __ldcs(nb + sp);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+      if (!act[u]) continue;
+      const int p = p0 + u * T;
+      const int qs = qsv[u], qi = qiv[u];
+      const int rowq = qs ? rB : rA;
+      const int sk = rA * M2 + p, sp = rowq * M2 + qi;   // spectrum slots of k and M-k
+      const float2 Zk = fwd ? sm[Lay::at(0, p)] : make_float2(0.f, 0.f);
+      const float2 Zp = fwd ? sm[Lay::at(qs, qi)] : make_float2(0.f, 0.f);
 
-    if (rA == 0 && p == 0) {
-      // k = 0 and k = M (both real): X_0 = Re Z_0 + Im Z_0, X_M = Re Z_0 - Im Z_0
-      const float X0 = Zk.x + Zk.y, XM = Zk.x - Zk.y;
-      if (mode == kRowSpectrum) { q.dtab[d.spec] = make_float2(X0, XM); continue; }
-      if (mode == kRowNatural) {
-        float2* o = q.a.natural + d.spec + c;
-        o[0] = make_float2(X0, 0.f);
-        o[M] = make_float2(XM, 0.f);
+      if (rA == 0 && p == 0) {
+        // k = 0 and k = M (both real): X_0 = Re Z_0 + Im Z_0, X_M = Re Z_0 - Im Z_0;
+        // slot 0 of d~ holds (d~_0, d~_M) and the Nyquist Nbar is kept per chunk
+        const float X0 = Zk.x + Zk.y, XM = Zk.x - Zk.y;
+        if (mode == kRowSpectrum) { q.dtab[d.spec] = make_float2(X0, XM); continue; }
+        if (mode == kRowNatural) {
+          float2* o = q.a.natural + d.spec + c;
+          o[0] = make_float2(X0, 0.f);
+          o[M] = make_float2(XM, 0.f);
+          continue;
+        }
+        const float2 D = dt[0];
+        const float n0 = nb[0], nM = __ldg(q.nyq + c);
+        if (want_x2) {
+          const float e0 = D.x - X0, eM = D.y - XM;
+          x2 += __fdividef(e0 * e0, n0 + cn) + __fdividef(eM * eM, nM + cn);
+        }
+        if (!inv) continue;
+        const float Y0 = filt(make_float2(X0, 0.f), make_float2(D.x, 0.f), n0).x;
+        const float YM = filt(make_float2(XM, 0.f), make_float2(D.y, 0.f), nM).x;
+        sm[Lay::at(0, 0)] = make_float2(Y0 + YM, Y0 - YM);
         continue;
       }
-      const float2 D = dt[0];
-      const float n0 = nb[0], nM = __ldg(q.nyq + c);
+
+      const float2 w = cmul(wa, __ldg(&q.g.tw_pack_b[p]));   // w_{2M}^k, k = rA + M1 p
+      const float2 E = cscale(cadd(Zk, cconj(Zp)), 0.5f);
+      const float2 O = cscale(mul_i<-1>(csub(Zk, cconj(Zp))), 0.5f);
+      const float2 wO = cmul(w, O);
+      const float2 Xk = cadd(E, wO);
+      const float2 Xp = cconj(csub(E, wO));
+      const bool same = (qs == 0 && qi == p);   // k == M - k (k = M/2)
+      if (mode == kRowSpectrum) {
+        q.dtab[d.spec + sk] = Xk;
+        if (!same) q.dtab[d.spec + sp] = Xp;
+        continue;
+      }
+      if (mode == kRowNatural) {
+        float2* o = q.a.natural + d.spec + c;
+        const int k = rA + M1 * p;
+        o[k] = Xk;
+        o[M - k] = Xp;
+        continue;
+      }
       if (want_x2) {
-        const float e0 = D.x - X0, eM = D.y - XM;
-        x2 += e0 * e0 / (n0 + cn) + eM * eM / (nM + cn);
+        const float2 ek = csub(Dk[u], Xk), ep = csub(Dp[u], Xp);
+        float t = __fdividef(ek.x * ek.x + ek.y * ek.y, nk[u] + cn);
+        if (!same) t += __fdividef(ep.x * ep.x + ep.y * ep.y, np[u] + cn);
+        x2 += 2.f * t;
       }
       if (!inv) continue;
-      const float Y0 = filt(make_float2(X0, 0.f), make_float2(D.x, 0.f), n0).x;
-      const float YM = filt(make_float2(XM, 0.f), make_float2(D.y, 0.f), nM).x;
-      sm[Lay::at(0, 0)] = make_float2(Y0 + YM, Y0 - YM);
-      continue;
-    }
-
-    const float2 w = cmul(wa, __ldg(&q.g.tw_pack_b[p]));   // w_{2M}^k, k = rA + M1 p
-    const float2 E = cscale(cadd(Zk, cconj(Zp)), 0.5f);
-    const float2 O = cscale(mul_i<-1>(csub(Zk, cconj(Zp))), 0.5f);
-    const float2 wO = cmul(w, O);
-    const float2 Xk = cadd(E, wO);
-    const float2 Xp = cconj(csub(E, wO));
-    const bool same = (qs == 0 && qi == p);   // k == M - k (k = M/2)
-    if (mode == kRowSpectrum) {
-      q.dtab[d.spec + sk] = Xk;
-      if (!same) q.dtab[d.spec + sp] = Xp;
-      continue;
-    }
-    if (mode == kRowNatural) {
-      float2* o = q.a.natural + d.spec + c;
-      const int k = rA + M1 * p;
-      o[k] = Xk;
-      o[M - k] = Xp;
-      continue;
-    }
-    const float2 Dk = __ldcs(dt + sk), Dp = __ldcs(dt + sp);
-    const float nk = __ldcs(nb + sk), np = __ldcs(nb + sp);
-    if (want_x2) {
-      const float2 ek = csub(Dk, Xk), ep = csub(Dp, Xp);
-      float t = (ek.x * ek.x + ek.y * ek.y) / (nk + cn);
-      if (!same) t += (ep.x * ep.x + ep.y * ep.y) / (np + cn);
-      x2 += 2.f * t;
-    }
-    if (!inv) continue;
-    const float2 Yk = filt(Xk, Dk, nk);
-    const float2 Yp = filt(Xp, Dp, np);
-    // Z'_k = (Y_k + conj Y_p) + i conj(w) (Y_k - conj Y_p);
-    // Z'_p = (Y_p + conj Y_k) - i w (Y_p - conj Y_k)
-    const float2 zk = cadd(cadd(Yk, cconj(Yp)), mul_i<+1>(cmulc(csub(Yk, cconj(Yp)), w)));
-    sm[Lay::at(0, p)] = zk;
-    if (!same) {
-      const float2 zp = csub(cadd(Yp, cconj(Yk)), mul_i<+1>(cmul(w, csub(Yp, cconj(Yk)))));
-      sm[Lay::at(qs, qi)] = zp;
+      const float2 Yk = filt(Xk, Dk[u], nk[u]);
+      const float2 Yp = filt(Xp, Dp[u], np[u]);
+      // Z'_k = (Y_k + conj Y_p) + i conj(w) (Y_k - conj Y_p);
+      // Z'_p = (Y_p + conj Y_k) - i w (Y_p - conj Y_k)
+      const float2 zk = cadd(cadd(Yk, cconj(Yp)), mul_i<+1>(cmulc(csub(Yk, cconj(Yp)), w)));
+      sm[Lay::at(0, p)] = zk;
+      if (!same) {
+        const float2 zp = csub(cadd(Yp, cconj(Yk)), mul_i<+1>(cmul(w, csub(Yp, cconj(Yk)))));
+        sm[Lay::at(qs, qi)] = zp;
+      }
     }
   }
 
@@ -206,11 +235,10 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_row(RowParams q) {
   __syncthreads();
   for (int job = blockIdx.x; job < njobs; job += gridDim.x) {
     const int ci = job / jobs_pc;
-    const int jn = job + gridDim.x;
-    if (q.prefetch && reads_d && jn < njobs && threadIdx.x == 0) {
-      // the next job's spectrum rows of d~ and Nbar into L2
-      const ChunkDesc dn = q.desc[q.chunks[jn / jobs_pc]];
-      const int ra = jn % jobs_pc, rb = (dn.M1 - ra) & (dn.M1 - 1);
+    if (reads_d && threadIdx.x == 0) {
+      // this job's d~ and Nbar rows into L2 while the forward row DFTs run
+      const ChunkDesc dn = q.desc[q.chunks[ci]];
+      const int ra = job % jobs_pc, rb = (dn.M1 - ra) & (dn.M1 - 1);
       prefetch_l2(q.dtab + dn.spec + (int64_t)ra * M2, 8 * M2);
       prefetch_l2(q.nbar + dn.spec + (int64_t)ra * M2, 4 * M2);
       if (rb != ra) {
@@ -236,7 +264,6 @@ static cudaError_t row_m2(const mm_plan_s* p, const Batch& b, const RowArgs& a,
   q.desc = p->d_desc;
   q.chunks = g.chunks + b.first;
   q.count = b.count;
-  q.prefetch = p->prefetch;
   q.g = g;
   q.ybuf = p->ybuf;
   q.dtab = p->dtab;
