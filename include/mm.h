@@ -162,6 +162,24 @@ mm_status mm_rfft(mm_plan p, const float* tod, float* spec_out, void* stream);
 mm_status mm_plan_maps(mm_plan p, int32_t* hits, uint8_t* valid, double* weight,
                        void* stream);
 
+/* Binned map that allocates nothing (this entry point has no counterpart in the paper; it
+ * exists for callers that cannot allocate device memory -- code being captured into a CUDA
+ * graph, running under an allocator that must not grow, or handed only device pointers):
+ *   map_out[p] = (P^T P)_p^-1 (P^T d)_p   for pixels with >= 1 hit and, for IQU,
+ *   eigmin/eigmax of (P^T P)_p >= rcond_min; 0 elsewhere.
+ * pix (int32 [n], -1 or any index outside [0, n_pix) = sample ignored), cos2psi / sin2psi
+ * ([n], FP32 or FP16 as weight_dtype; NULL iff ncomp == 1) and tod (float32 [n]) are
+ * device inputs; map_out is device float64 [n_pix][ncomp].  No workspace: the FP64
+ * accumulators sit in one fixed device array of 2^18 pixels x 9 doubles (18.9 MB) that
+ * every GPU loading the library keeps until the process exits; n_pix > 262144 returns
+ * MM_ERR_ARG.  The first call on a device looks up that array's address on the current
+ * device, so make the first call before any stream capture.  Each call clears the part of
+ * the array it uses; all calls on a device share the one array, so calls whose kernels
+ * overlap on the GPU (e.g. on two streams) race.  Asynchronous on `stream`. */
+mm_status mm_binned_map_noalloc(const int32_t* pix, const void* cos2psi, const void* sin2psi,
+                                int weight_dtype, const float* tod, int64_t n, int64_t n_pix,
+                                int ncomp, double rcond_min, double* map_out, void* stream);
+
 /* Release the plan's host memory (the caller frees the workspace). NULL is a no-op. */
 void mm_plan_destroy(mm_plan p);
 

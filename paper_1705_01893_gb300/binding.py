@@ -47,6 +47,9 @@ SIGNATURES = {
     "mm_apply_pointing_T": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mm_rfft": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mm_plan_maps": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "mm_binned_map_noalloc": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, _vp, ctypes.c_int64,
+                                             ctypes.c_int64, ctypes.c_int, ctypes.c_double, _vp,
+                                             _vp]),
     "mm_plan_destroy": (None, [_vp]),
     "mm_last_error": (ctypes.c_char_p, []),
 }
@@ -237,6 +240,17 @@ def plan_from_synth(s: dict, device="cuda:0", rcond_min: float = 1e-3, tau=None,
     plan.set_noise(tod, params=s["params"], tau=tau, stream=stream)
     plan.tod = tod
     return plan
+
+
+def binned_map_noalloc(pix, cos2psi, sin2psi, tod, n_pix: int, ncomp: int, map_out,
+                       rcond_min: float = 1e-3, stream=None):
+    """(P^T P)^-1 P^T d per pixel with no device allocation by the library (its scratch is a
+    fixed device array of 2^18 pixels); for callers that must not allocate."""
+    import torch
+    wd = MM_W_F16 if (cos2psi is not None and cos2psi.dtype == torch.float16) else MM_W_F32
+    _check("mm_binned_map_noalloc", load().mm_binned_map_noalloc(
+        _ptr(pix), _ptr(cos2psi), _ptr(sin2psi), wd, _ptr(tod), int(pix.numel()), int(n_pix),
+        int(ncomp), float(rcond_min), _ptr(map_out), _stream(stream)))
 
 
 def cooling_schedule(lam_max: float, levels: int, iters: int) -> np.ndarray:
