@@ -129,6 +129,27 @@ enum { MM_STAGE_LOAD = 0, MM_STAGE_GATHER_FFT = 1, MM_STAGE_FILTER = 2, MM_STAGE
 mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double lambda,
                              double* map_inout, double* chi2_slot, void* stream);
 
+/* Bytes of device work space mm_messenger_adjoint needs for n_iter iterations with a
+ * checkpoint every ckpt_every iterations (caller-owned, 256-byte aligned). */
+mm_status mm_adjoint_work_bytes(mm_plan p, int n_iter, int ckpt_every, size_t* bytes);
+
+/* Gradient through n_iter messenger iterations (the forward of mm_messenger_iterate from
+ * map_in with the cooling sequence `lambdas`, held constant): given grad_map_out =
+ * dL/dm_{n_iter} (device float64 [n_pix][ncomp]) of any scalar loss L, writes
+ *   grad_tod   = dL/dd   (device float32 [n], original sample order, overwritten), and
+ *   grad_theta = dL/d(sigma, f_knee, alpha) per chunk (device float64 [n_chunks][3],
+ *                overwritten; NULL to skip) -- defined when the noise came from `params`
+ *                with tau = sigma^2 (MM_ERR_UNSUPPORTED otherwise).
+ * The transposed step of Sec. 2.1's iteration (u = W gbar, v = P u; dL/dd += irfft(a v~)/tau,
+ * dL/dm = P^T irfft(b v~)/tau, with a = lambda tau / (lambda tau + Nbar), b = 1 - a) runs on
+ * the GPU for every iteration in reverse; forward iterates are recomputed from checkpoints
+ * taken every ckpt_every iterations (the plan's own buffers are reused).  FP32 timestreams
+ * and FFTs, FP64 accumulation.  Chunks up to 2^22 samples.  Asynchronous on `stream`. */
+mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int n_iter,
+                               const double* map_in, const double* grad_map_out,
+                               float* grad_tod, double* grad_theta, int ckpt_every,
+                               void* work, size_t work_bytes, void* stream);
+
 /* Bytes of device state mm_pcg_iterate needs (caller-owned, 256-byte aligned). */
 mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes);
 

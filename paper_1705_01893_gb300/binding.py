@@ -40,6 +40,9 @@ SIGNATURES = {
     "mm_plan_batches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "mm_messenger_stage": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp,
                                           _vp]),
+    "mm_adjoint_work_bytes": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _szp]),
+    "mm_messenger_adjoint": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
+                                            _vp, ctypes.c_size_t, _vp]),
     "mm_pcg_state_bytes": (ctypes.c_int, [_vp, _szp]),
     "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
@@ -188,6 +191,21 @@ class Plan:
             self._h, int(stage), int(batch), float(lam), _ptr(map_inout), _ptr(chi2_slot),
             _stream(stream)))
 
+    def adjoint(self, lambdas, map_in, grad_map_out, grad_tod, grad_theta=None,
+                ckpt_every: int = 10, stream=None):
+        """dL/dd (and dL/dtheta) through len(lambdas) iterations from map_in, given dL/dm_K."""
+        import torch
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        n = ctypes.c_size_t()
+        _check("mm_adjoint_work_bytes", load().mm_adjoint_work_bytes(self._h, len(lam), int(ckpt_every),
+                                                                     ctypes.byref(n)))
+        work = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=self.device)
+        wp = (work.data_ptr() + 255) // 256 * 256
+        _check("mm_messenger_adjoint", load().mm_messenger_adjoint(
+            self._h, lam.ctypes.data_as(_dp), len(lam), _ptr(map_in), _ptr(grad_map_out),
+            _ptr(grad_tod), _ptr(grad_theta), int(ckpt_every), wp, int(n.value), _stream(stream)))
+        self._adj_work = work   # keep alive until the stream has run the call
+
     def pcg_state(self):
         import torch
         if self._pcg_state is None:
@@ -260,3 +278,31 @@ def cooling_schedule(lam_max: float, levels: int, iters: int) -> np.ndarray:
     else:
         lv = [lam_max ** ((levels - 1 - j) / (levels - 1)) for j in range(levels)]
     return np.array([math.inf] + [v for v in lv for _ in range(iters)])
+
+
+def messenger_fn():
+    """torch.autograd.Function running K cooled messenger iterations on the GPU, with the
+    hand-written adjoint as its backward.  apply(plan, lambdas, map_in, tod, theta) ->
+    m_K; gradients flow to tod (float32 [n]) and theta (float64 [n_chunks, 3] =
+    sigma, f_knee, alpha), which must be the data and parameters the plan was set up with."""
+    import torch
+
+    class MessengerFn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, plan, lambdas, map_in, tod, theta):
+            m = map_in.detach().clone()
+            plan.messenger(m, lambdas)
+            ctx.plan, ctx.lambdas = plan, np.asarray(lambdas, dtype=np.float64)
+            ctx.save_for_backward(map_in)
+            return m
+
+        @staticmethod
+        def backward(ctx, grad_m):
+            (map_in,) = ctx.saved_tensors
+            plan = ctx.plan
+            gt = torch.empty(int(plan.offsets[-1]), dtype=torch.float32, device=grad_m.device)
+            gth = torch.empty(plan.n_chunks, 3, dtype=torch.float64, device=grad_m.device)
+            plan.adjoint(ctx.lambdas, map_in, grad_m.contiguous().to(torch.float64), gt, gth)
+            return None, None, None, gt, gth
+
+    return MessengerFn

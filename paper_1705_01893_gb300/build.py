@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmm.so")
-SOURCES = ["mm_api.cu", "mm_col.cu", "mm_row.cu", "mm_noalloc.cu"]
+SOURCES = ["mm_api.cu", "mm_col.cu", "mm_row.cu", "mm_adjoint.cu", "mm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--use_fast_math=false"]
 
@@ -38,7 +38,8 @@ def _stale(obj: str, deps: list[str]) -> bool:
 def build(verbose: bool = False, force: bool = False) -> str:
     """Compile (if needed) and return the path of libmm.so."""
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "mm_internal.cuh"), os.path.join(ROOT, "include", "mm.h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
+    headers.append(os.path.join(ROOT, "include", "mm.h"))
     cc = nvcc()
     jobs = []
     for src in SOURCES:

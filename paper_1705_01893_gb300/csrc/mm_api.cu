@@ -107,7 +107,7 @@ static size_t tw_count(int M, int M1, int M2) {
 // -------------------------------------------------------------------- workspace layout
 struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
-      ybuf, scal, tpix, tcos, tsin, total;
+      ybuf, scal, tpix, tcos, tsin, total, ybytes;
   int n_groups;
   int gM[kMaxGroups], gM1[kMaxGroups], gM2[kMaxGroups], gcount[kMaxGroups], gbatch[kMaxGroups];
   std::vector<int> chunk_group;
@@ -192,6 +192,7 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->nyq = take(sizeof(float) * n_chunks);
   L->c0 = take(sizeof(double) * n_chunks);
   L->ybuf = take(ybytes);
+  L->ybytes = ybytes;
   L->scal = take(sizeof(double) * kScalCount);
   // pointing copied into column-tile order for the streaming passes
   const size_t wb = ncomp == 3 ? (wdtype == MM_W_F16 ? 2 : 4) : 0;
@@ -762,6 +763,8 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   p->nyq = reinterpret_cast<float*>(ws + L.nyq);
   p->c0 = reinterpret_cast<double*>(ws + L.c0);
   p->ybuf = reinterpret_cast<float2*>(ws + L.ybuf);
+  p->ybuf_bytes = L.ybytes;
+  p->theta_ok = false;
   p->scal = reinterpret_cast<double*>(ws + L.scal);
   p->params = reinterpret_cast<double*>(ws + L.params);
   p->tpix = reinterpret_cast<int32_t*>(ws + L.tpix);
@@ -988,6 +991,7 @@ extern "C" mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const do
     mm_set_error("every pixel was cut (no pixel with hits and rcond >= %g)", p->rcond_min);
     return MM_ERR_SINGULAR;
   }
+  p->theta_ok = params != nullptr && tau == nullptr;
   p->noise_set = true;
   return MM_OK;
 }

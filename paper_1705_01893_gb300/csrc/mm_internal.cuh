@@ -81,6 +81,8 @@ struct mm_plan_s {
   float* nyq;       // [n_chunks] Nbar at the Nyquist bin
   double* c0;       // [n_chunks] (1/n) sum_k w_k / N_k
   float2* ybuf;     // one batch's four-step intermediate (L2-resident between passes)
+  size_t ybuf_bytes;
+  bool theta_ok;    // noise from (sigma, f_knee, alpha) with tau = sigma^2: theta gradients defined
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;
@@ -388,6 +390,14 @@ cudaError_t launch_col_forward(const mm_plan_s* p, const Batch& b, int src, cons
 cudaError_t launch_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
 cudaError_t launch_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st);
 cudaError_t launch_tile_pointing(const mm_plan_s* p, cudaStream_t st);
+// Forward column pass gathering from `map4` into `ybuf` (either NULL = the plan's own).
+cudaError_t launch_col_forward_ex(const mm_plan_s* p, const Batch& b, int src, const float* tod,
+                                  const void* map4, float2* ybuf, cudaStream_t st);
+// Threads of the column kernels for column length M1 (16 complex values per thread per pass).
+constexpr int kColCB = 16;
+__host__ __device__ constexpr int col_threads(int M1) {
+  return M1 * kColCB / 16 < 64 ? 64 : (M1 * kColCB / 16 > 1024 ? 1024 : M1 * kColCB / 16);
+}
 
 }  // namespace mm
 
