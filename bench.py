@@ -267,6 +267,8 @@ def run_gpu(args):
     e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * npix * nc,
            "d2h_bytes_per_step": 8 * npix * nc + 8}
 
+    tol = time_to_tolerance(plan, s, dev, stream, args) if not args.no_tolerance else None
+
     if rank != 0:
         return
     wbytes = 8 if s["cos"] is not None and s["cos"].dtype == np.float32 else (4 if nc == 3 else 0)
@@ -305,6 +307,7 @@ def run_gpu(args):
                      "bytes_per_launch": bps[dom], "peak_source": peak_src},
         "e2e": e2e,
         "gpu_launches": args.steps * (3 * nb + 1),
+        "time_to_chi2_tol": tol,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -312,6 +315,61 @@ def run_gpu(args):
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": "1 full iteration of the 8 x 2^22 workload, numpy FP64, 1 thread"}
     print(json.dumps(line), flush=True)
+
+
+def time_to_tolerance(plan, s, dev, stream, args):
+    """Iterations and device time for the cooled messenger (10 levels x 10, then lambda = 1)
+    and for PCG (the paper's comparison solver, on the same kernels) to bring chi^2 within
+    1e-3 and 1e-4 (relative) of chi2_*, the lowest chi^2 either reaches in a long run."""
+    import torch
+    from paper_1705_01893_gb300 import binding
+    npix, nc = s["npix"], s["ncomp"]
+    lam_max = plan.lambda_max()
+    total = 1 + 100 + args.tol_iters
+    runs = {}
+    for label, (lv, it) in (("10x10", (10, 10)), ("8x5", (8, 5))):
+        cool = binding.cooling_schedule(lam_max, lv, it)
+        lam_m = np.concatenate([cool, np.ones(total - len(cool))])
+        m = torch.zeros(npix, nc, dtype=torch.float64, device=dev)
+        chi = torch.zeros(len(lam_m), dtype=torch.float64, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.messenger(m, lam_m, chi)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        runs[label] = (chi.cpu().numpy(), e0.elapsed_time(e1) / len(lam_m))
+    ms_m = runs["10x10"][1]
+    n_pcg = total
+    x = torch.zeros(npix, nc, dtype=torch.float64, device=dev)
+    chi_p = torch.zeros(n_pcg, dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.pcg(x, n_pcg, restart=True, chi2_out=chi_p)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_p = e0.elapsed_time(e1) / n_pcg
+    cp = chi_p.cpu().numpy()
+    star = float(min(min(r[0].min() for r in runs.values()), cp.min()))
+
+    def reach(ch, tol_rel):
+        ok = np.flatnonzero((ch - star) / star <= tol_rel)
+        return int(ok[0]) if ok.size else None
+
+    out = {"chi2_star": star, "n_samples": int(s["offsets"][-1]), "iterations_run": total,
+           "pcg": {"preconditioner": "3x3 pixel-block Jacobi", "ms_per_iter": ms_p,
+                   "final_rel": float((cp[-1] - star) / star)}}
+    series = [("pcg", cp, ms_p)]
+    for label, (ch, ms) in runs.items():
+        key = "messenger_" + label
+        out[key] = {"schedule": "1 x inf, %s geometric to 1, then lambda = 1" % label,
+                    "ms_per_iter": ms, "final_rel": float((ch[-1] - star) / star)}
+        series.append((key, ch, ms))
+    for name, ch, ms in series:
+        for t in (1e-3, 1e-4):
+            it = reach(ch, t)
+            out[name]["iters_%g" % t] = it
+            out[name]["ms_%g" % t] = None if it is None else it * ms
+    return out
 
 
 def plan_groups(s):
@@ -326,6 +384,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tolerance", action="store_true")
+    ap.add_argument("--tol-iters", type=int, default=400,
+                    help="lambda = 1 iterations after the cooling schedule (and PCG length)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
