@@ -129,6 +129,16 @@ enum { MM_STAGE_LOAD = 0, MM_STAGE_GATHER_FFT = 1, MM_STAGE_FILTER = 2, MM_STAGE
 mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double lambda,
                              double* map_inout, double* chi2_slot, void* stream);
 
+/* The same iterations as mm_messenger_iterate, launched as one CUDA graph per iteration:
+ * the plan captures one iteration (every batch's kernels and the map step) on its first
+ * call, with the cooling parameter and the chi^2 slot read from a device-side schedule
+ * table and iteration counter, and replays it n_iter times (n_iter <= 65536).  `lambdas`
+ * (host) is copied to the device before the call returns.  The first call does the
+ * capture on a stream the plan owns, so it must not itself be made while `stream` is
+ * being captured.  Results equal mm_messenger_iterate's. */
+mm_status mm_messenger_graph(mm_plan p, const double* lambdas, int n_iter, double* map_inout,
+                             double* chi2_out, void* stream);
+
 /* Bytes of device work space mm_messenger_adjoint needs for n_iter iterations with a
  * checkpoint every ckpt_every iterations (caller-owned, 256-byte aligned). */
 mm_status mm_adjoint_work_bytes(mm_plan p, int n_iter, int ckpt_every, size_t* bytes);

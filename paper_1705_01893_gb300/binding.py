@@ -38,6 +38,7 @@ SIGNATURES = {
     "mm_lambda_max": (ctypes.c_int, [_vp, _dp, _vp]),
     "mm_messenger_iterate": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     "mm_plan_batches": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "mm_messenger_graph": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp]),
     "mm_messenger_stage": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp,
                                           _vp]),
     "mm_adjoint_work_bytes": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _szp]),
@@ -179,6 +180,13 @@ class Plan:
         _check("mm_messenger_iterate", load().mm_messenger_iterate(
             self._h, lam.ctypes.data_as(_dp), len(lam), MM_FP32_MIXED, _ptr(map_inout),
             _ptr(chi2_out), _stream(stream)))
+
+    def messenger_graph(self, map_inout, lambdas, chi2_out=None, stream=None):
+        """Same as messenger(), replaying one captured CUDA graph per iteration."""
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        _check("mm_messenger_graph", load().mm_messenger_graph(
+            self._h, lam.ctypes.data_as(_dp), len(lam), _ptr(map_inout), _ptr(chi2_out),
+            _stream(stream)))
 
     def n_batches(self) -> int:
         n = ctypes.c_int()

@@ -107,7 +107,8 @@ static size_t tw_count(int M, int M1, int M2) {
 // -------------------------------------------------------------------- workspace layout
 struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
-      ybuf, scal, tpix, tcos, tsin, total, ybytes;
+      ybuf, scal, tpix, tcos, tsin, lam, iter, map64, total, ybytes;
+  int lam_cap;
   int n_groups;
   int gM[kMaxGroups], gM1[kMaxGroups], gM2[kMaxGroups], gcount[kMaxGroups], gbatch[kMaxGroups];
   std::vector<int> chunk_group;
@@ -199,6 +200,11 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->tpix = take(sizeof(int32_t) * (size_t)L->n_total);
   L->tcos = take(wb * (size_t)L->n_total);
   L->tsin = take(wb * (size_t)L->n_total);
+  // graph mode: schedule table, iteration counter + chi^2 pointer slot, FP64 map
+  L->lam_cap = 65536;
+  L->lam = take(sizeof(double) * L->lam_cap);
+  L->iter = take(128);
+  L->map64 = take(sizeof(double) * ncomp * np);
   L->total = o;
   return MM_OK;
 }
@@ -460,8 +466,9 @@ __device__ __forceinline__ void store_map4(void* map4, int64_t p, const double* 
 // m = (P^T T^-1 P)^-1 acc (the map step of Sec. 2.1); acc is cleared for the next pass.
 template <int NC>
 __global__ void k_bin_apply(int64_t n_pix, double* __restrict__ acc, const double* __restrict__ W,
-                            void* map4, double* __restrict__ map_out) {
+                            void* map4, double* __restrict__ map_out, int* iter = nullptr) {
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (iter && p == 0) *iter += 1;   // graph mode: next iteration of the schedule
   if (p >= n_pix) return;
   constexpr int B = NC == 3 ? 6 : 1;
   double a[NC], w[B], m[NC];
@@ -765,6 +772,13 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   p->ybuf = reinterpret_cast<float2*>(ws + L.ybuf);
   p->ybuf_bytes = L.ybytes;
   p->theta_ok = false;
+  p->graph_exec = nullptr;
+  p->graph_stream = nullptr;
+  p->lam_cap = L.lam_cap;
+  p->lam_table = reinterpret_cast<double*>(ws + L.lam);
+  p->iter = reinterpret_cast<int*>(ws + L.iter);
+  p->chi2_base = reinterpret_cast<double**>(ws + L.iter + 64);
+  p->map64 = reinterpret_cast<double*>(ws + L.map64);
   p->scal = reinterpret_cast<double*>(ws + L.scal);
   p->params = reinterpret_cast<double*>(ws + L.params);
   p->tpix = reinterpret_cast<int32_t*>(ws + L.tpix);
@@ -868,6 +882,8 @@ extern "C" void mm_plan_destroy(mm_plan p) {
   delete[] p->h_desc;
   delete[] p->h_chunk_group;
   delete[] p->h_batches;
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->graph_stream) cudaStreamDestroy(p->graph_stream);
   delete p;
 }
 
@@ -1085,6 +1101,74 @@ extern "C" mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double 
     mm_set_error("stage %d launch: %s", stage, cudaGetErrorString(e));
     return MM_ERR_CUDA;
   }
+  return MM_OK;
+}
+
+// Capture one messenger iteration (every batch's three kernels, then the map step) as a CUDA
+// graph whose cooling parameter and chi^2 slot come from device memory.
+static mm_status capture_iteration_graph(mm_plan p) {
+  if (p->graph_exec) return MM_OK;
+  if (!p->graph_stream)
+    MM_CUDA(cudaStreamCreateWithFlags(&p->graph_stream, cudaStreamNonBlocking));
+  cudaStream_t s = p->graph_stream;
+  RowArgs a{kRowMessenger, 1.0, nullptr, nullptr};
+  a.lam_table = p->lam_table;
+  a.iter = p->iter;
+  a.chi2_base = p->chi2_base;
+  // relaxed: the launchers may query occupancy / set kernel attributes on first use
+  MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < p->n_batches && e == cudaSuccess; ++b) {
+    const Batch& B = p->h_batches[b];
+    if ((e = launch_col_forward(p, B, kSrcGather, nullptr, s)) != cudaSuccess) break;
+    if ((e = launch_row(p, B, a, s)) != cudaSuccess) break;
+    e = launch_col_inverse(p, B, s);
+  }
+  if (e == cudaSuccess) {
+    if (p->ncomp == 3)
+      k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, p->map64, p->iter);
+    else
+      k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, p->map64, p->iter);
+    e = cudaGetLastError();
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    mm_set_error("graph capture failed: %s", cudaGetErrorString(e != cudaSuccess ? e : ec));
+    return MM_ERR_CUDA;
+  }
+  e = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    p->graph_exec = nullptr;
+    mm_set_error("graph instantiate failed: %s", cudaGetErrorString(e));
+    return MM_ERR_CUDA;
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_messenger_graph(mm_plan p, const double* lambdas, int n_iter,
+                                        double* map_inout, double* chi2_out, void* stream) {
+  MM_ARG(p != nullptr && map_inout != nullptr, "NULL argument");
+  MM_ARG(n_iter >= 0 && n_iter <= p->lam_cap, "n_iter must be in [0, %d]", p->lam_cap);
+  MM_ARG(n_iter == 0 || lambdas != nullptr, "lambdas is NULL");
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  for (int i = 0; i < n_iter; ++i)
+    MM_ARG(lambdas[i] >= 1.0 || isinf(lambdas[i]), "lambdas[%d] = %g must be >= 1 or inf", i, lambdas[i]);
+  if (n_iter == 0) return MM_OK;
+  mm_status st = capture_iteration_graph(p);
+  if (st != MM_OK) return st;
+  cudaStream_t s = S(stream);
+  MM_CUDA(cudaMemcpyAsync(p->lam_table, lambdas, sizeof(double) * n_iter, cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemsetAsync(p->iter, 0, sizeof(int), s));
+  MM_CUDA(cudaMemcpyAsync(p->chi2_base, &chi2_out, sizeof(double*), cudaMemcpyHostToDevice, s));
+  if (chi2_out) MM_CUDA(cudaMemsetAsync(chi2_out, 0, sizeof(double) * n_iter, s));
+  st = load_map(p, map_inout, s);
+  if (st != MM_OK) return st;
+  for (int it = 0; it < n_iter; ++it) MM_CUDA(cudaGraphLaunch(p->graph_exec, s));
+  MM_CUDA(cudaMemcpyAsync(map_inout, p->map64, sizeof(double) * p->ncomp * p->n_pix,
+                          cudaMemcpyDeviceToDevice, s));
   return MM_OK;
 }
 

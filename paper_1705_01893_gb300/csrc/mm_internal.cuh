@@ -82,7 +82,15 @@ struct mm_plan_s {
   double* c0;       // [n_chunks] (1/n) sum_k w_k / N_k
   float2* ybuf;     // one batch's four-step intermediate (L2-resident between passes)
   size_t ybuf_bytes;
-  bool theta_ok;    // noise from (sigma, f_knee, alpha) with tau = sigma^2: theta gradients defined
+  bool theta_ok;
+  // CUDA graph of one messenger iteration (captured on first use of mm_messenger_graph)
+  cudaGraphExec_t graph_exec;
+  cudaStream_t graph_stream;
+  double* lam_table;   // device [lam_cap] schedule
+  int lam_cap;
+  int* iter;           // device iteration counter
+  double** chi2_base;  // device pointer slot: chi^2 output array or NULL
+  double* map64;       // device FP64 copy of the current map (graph mode)    // noise from (sigma, f_knee, alpha) with tau = sigma^2: theta gradients defined
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;
@@ -380,6 +388,12 @@ struct RowArgs {
   double lambda;       // cooling parameter (messenger) / N' = N + (lambda-1) tau (chi^2)
   double* chi2;        // device accumulator or nullptr
   float2* natural;     // kRowNatural output
+  // Graph mode (lam_table != nullptr): lambda = lam_table[*iter] and the chi^2 slot is
+  // chi2_base[0] + *iter when chi2_base[0] is set; the values live in device memory so one
+  // captured CUDA graph serves every iteration of a schedule.
+  const double* lam_table = nullptr;
+  const int* iter = nullptr;
+  double* const* chi2_base = nullptr;
 };
 
 // Source of the forward column pass.

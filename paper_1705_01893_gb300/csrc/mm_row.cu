@@ -72,14 +72,21 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   // per-mode constants
   const float tau = (float)d.tau;
   const float inv_n = 1.0f / (float)d.n;
+  double lambda = q.a.lambda;
+  double* chi2 = q.a.chi2;
+  if (q.a.lam_table) {          // graph mode: schedule and chi^2 slot from device memory
+    const int it = *q.a.iter;
+    lambda = q.a.lam_table[it];
+    chi2 = q.a.chi2_base[0] ? q.a.chi2_base[0] + it : nullptr;
+  }
   float lt = 0.f;               // lambda * tau
   bool lam_inf = false;
   if (mode == kRowMessenger) {
-    lam_inf = isinf(q.a.lambda);
-    lt = lam_inf ? 0.f : (float)(q.a.lambda * d.tau);
+    lam_inf = isinf(lambda);
+    lt = lam_inf ? 0.f : (float)(lambda * d.tau);
   }
   // N' = Nbar + cn for chi^2: tau (Eq. 3) or lambda tau (chi^2(m, lambda))
-  const float cn = mode == kRowChi2 ? (float)(q.a.lambda * d.tau) : tau;
+  const float cn = mode == kRowChi2 ? (float)(lambda * d.tau) : tau;
   // output scale: irfft normalisation 1/n, and T^-1 = 1/tau for the messenger map step
   const float sc = mode == kRowMessenger ? inv_n / tau : inv_n;
   const float2* dt = q.dtab + d.spec;
@@ -96,7 +103,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
     if (mode == kRowPcgApply) return cscale(X, __fdividef(sc, nbv + tau));
     return cscale(D, __fdividef(sc, nbv + tau));  // kRowPcgRhs
   };
-  const bool want_x2 = q.a.chi2 != nullptr &&
+  const bool want_x2 = chi2 != nullptr &&
                        (mode == kRowMessenger || mode == kRowChi2 || mode == kRowPcgRhs);
   const bool spec_out = mode == kRowSpectrum || mode == kRowNatural;
   const bool load_d = !spec_out && mode != kRowPcgApply;
@@ -211,7 +218,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int i = 0; i < T / 32; ++i) s += red[i];
-      atomicAdd(q.a.chi2, s / (double)d.n);
+      atomicAdd(chi2, s / (double)d.n);
     }
   }
   if (!inv) return;

@@ -313,3 +313,24 @@ def test_batches_and_stage_api_match_iterate(monkeypatch):
     assert rel(m2.cpu().numpy(), m1.cpu().numpy()) <= 1e-12
     m_ref, _ = O.run_messenger(prob, lam)
     assert rel(m2.cpu().numpy(), m_ref) <= 1e-5
+
+
+def test_graph_replay_matches_iterate():
+    """One captured CUDA graph per iteration (schedule and chi^2 slot in device memory) gives
+    the iterate and the chi^2 sequence of mm_messenger_iterate; a second call reuses it."""
+    s = synth.config_iqu(32, 4, 1 << 14, 33)
+    prob = O.problem_from_synth(s)
+    lam = O.cooling_schedule(O.lambda_max(prob), 4, 3)
+    plan = gpu_plan(s)
+    a = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    ca = torch.zeros(len(lam), dtype=torch.float64, device=DEV)
+    plan.messenger(a, lam, ca)
+    for _ in range(2):
+        b = torch.zeros_like(a)
+        cb = torch.zeros_like(ca)
+        plan.messenger_graph(b, lam, cb)
+        torch.cuda.synchronize()
+        assert rel(b.cpu().numpy(), a.cpu().numpy()) <= 1e-12
+        assert np.max(np.abs(cb.cpu().numpy() - ca.cpu().numpy()) / ca.cpu().numpy()) <= 1e-12
+    m_ref, _ = O.run_messenger(prob, lam)
+    assert rel(b.cpu().numpy(), m_ref) <= 1e-5
