@@ -260,6 +260,20 @@ def run_gpu(args):
     ms_step = graph_ms
     value = world / (graph_ms / 1e3)
 
+    # the plain FP64 single-launch-per-iteration step on the same GPU (comparison bar)
+    plain_ms = None
+    if not args.no_plain:
+        mp = m.clone()
+        lam_p = np.array([float(sched[k % len(sched)]) for k in range(5)])
+        plan.messenger_plain_fp64(mp, lam_p[:1])
+        torch.cuda.synchronize(dev)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        plan.messenger_plain_fp64(mp, lam_p)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms = p0.elapsed_time(p1) / len(lam_p)
+
     # end to end through the public call, host buffers: map in (pinned), one iteration,
     # map and chi^2 out, synchronised every step
     m_host = torch.zeros(npix, nc, dtype=torch.float64).pin_memory()
@@ -324,6 +338,8 @@ def run_gpu(args):
                   "the launching stream); roofline/stage_ms_per_launch: K iterations launched "
                   "stage by stage with events between the kernels",
         "stage_loop_ms_per_step": stage_ms_step,
+        "fp64_plain_ms_per_step": plain_ms,
+        "speedup_vs_fp64_plain": None if plain_ms is None else plain_ms / ms_step,
         "stage_ms_per_launch": {k: round(v, 5) for k, v in avg.items()},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
@@ -408,6 +424,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tolerance", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--tol-iters", type=int, default=400,
                     help="lambda = 1 iterations after the cooling schedule (and PCG length)")
     args = ap.parse_args()

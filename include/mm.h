@@ -139,6 +139,22 @@ mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double lambda,
 mm_status mm_messenger_graph(mm_plan p, const double* lambdas, int n_iter, double* map_inout,
                              double* chi2_out, void* stream);
 
+/* Bytes of device work space mm_messenger_plain_fp64 needs (all chunks one length). */
+mm_status mm_plain_work_bytes(mm_plan p, size_t* bytes);
+
+/* The plain FP64 messenger iteration, the same-GPU comparison bar of the FP32 path: per
+ * iteration one cooperative launch doing, all in float64, the gather of d - P m, radix-2
+ * Stockham FFTs through global memory, the filter t = d - irfft(b (d - Pm)~) (b = Nbar /
+ * (lambda tau + Nbar), the residual form of Sec. 2.1's update), FP64 binning and the 3x3
+ * solve, with grid-wide barriers between phases.  tod: the device float32 data given to
+ * mm_set_noise_psd (the plan does not keep it).  Otherwise the arguments and results of
+ * mm_messenger_iterate (to FP32 rounding of that path), plus a work buffer sized by
+ * mm_plain_work_bytes.  Synchronises `stream`; a barrier that does not complete within about
+ * two seconds returns MM_ERR_TIMEOUT. */
+mm_status mm_messenger_plain_fp64(mm_plan p, const float* tod, const double* lambdas,
+                                  int n_iter, double* map_inout, double* chi2_out, void* work,
+                                  size_t work_bytes, void* stream);
+
 /* Bytes of device work space mm_messenger_adjoint needs for n_iter iterations with a
  * checkpoint every ckpt_every iterations (caller-owned, 256-byte aligned). */
 mm_status mm_adjoint_work_bytes(mm_plan p, int n_iter, int ckpt_every, size_t* bytes);

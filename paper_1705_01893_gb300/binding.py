@@ -41,6 +41,9 @@ SIGNATURES = {
     "mm_messenger_graph": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp]),
     "mm_messenger_stage": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, _vp, _vp,
                                           _vp]),
+    "mm_plain_work_bytes": (ctypes.c_int, [_vp, _szp]),
+    "mm_messenger_plain_fp64": (ctypes.c_int, [_vp, _vp, _dp, ctypes.c_int, _vp, _vp, _vp,
+                                               ctypes.c_size_t, _vp]),
     "mm_adjoint_work_bytes": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _szp]),
     "mm_messenger_adjoint": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
                                             _vp, ctypes.c_size_t, _vp]),
@@ -187,6 +190,21 @@ class Plan:
         _check("mm_messenger_graph", load().mm_messenger_graph(
             self._h, lam.ctypes.data_as(_dp), len(lam), _ptr(map_inout), _ptr(chi2_out),
             _stream(stream)))
+
+    def messenger_plain_fp64(self, map_inout, lambdas, chi2_out=None, tod=None, stream=None):
+        """The plain FP64 single-launch-per-iteration messenger step (comparison bar); tod
+        defaults to the data the plan was set up with (plan_from_synth keeps it)."""
+        import torch
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        n = ctypes.c_size_t()
+        _check("mm_plain_work_bytes", load().mm_plain_work_bytes(self._h, ctypes.byref(n)))
+        if getattr(self, "_plain_work", None) is None or self._plain_work.numel() < n.value + 256:
+            self._plain_work = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=self.device)
+        wp = (self._plain_work.data_ptr() + 255) // 256 * 256
+        tod = self.tod if tod is None else tod
+        _check("mm_messenger_plain_fp64", load().mm_messenger_plain_fp64(
+            self._h, _ptr(tod), lam.ctypes.data_as(_dp), len(lam), _ptr(map_inout),
+            _ptr(chi2_out), wp, int(n.value), _stream(stream)))
 
     def n_batches(self) -> int:
         n = ctypes.c_int()

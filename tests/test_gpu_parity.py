@@ -334,3 +334,21 @@ def test_graph_replay_matches_iterate():
         assert np.max(np.abs(cb.cpu().numpy() - ca.cpu().numpy()) / ca.cpu().numpy()) <= 1e-12
     m_ref, _ = O.run_messenger(prob, lam)
     assert rel(b.cpu().numpy(), m_ref) <= 1e-5
+
+
+@pytest.mark.parametrize("cfg", ["iqu", "t64"])
+def test_plain_fp64_step(cfg):
+    """The plain FP64 comparison step reproduces the FP64 oracle (to FP64 rounding of its
+    FFTs and the FP32 Nbar table) and the FP32 path."""
+    s = synth.config_iqu(32, 4, 1 << 14, 34) if cfg == "iqu" else synth.config_temperature_64()
+    prob = O.problem_from_synth(s)
+    lam = O.cooling_schedule(O.lambda_max(prob), 3, 2)
+    plan = gpu_plan(s)
+    nc = s["ncomp"]
+    m = torch.zeros(s["npix"], nc, dtype=torch.float64, device=DEV)
+    chi = torch.zeros(len(lam), dtype=torch.float64, device=DEV)
+    plan.messenger_plain_fp64(m, lam, chi)
+    torch.cuda.synchronize()
+    m_ref, chi_ref = O.run_messenger(prob, lam)
+    assert rel(m.cpu().numpy(), m_ref) <= 1e-5
+    assert np.max(np.abs(chi.cpu().numpy() - chi_ref) / chi_ref) <= 1e-6
