@@ -109,6 +109,39 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def _multi_rank():
+    import torch.distributed as dist
+    return dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
+
+
+def fence(dev):
+    """Barrier + device synchronize: every rank enters (or leaves) a timed region together."""
+    import torch
+    if dev.type == "cuda":
+        torch.cuda.synchronize(dev)
+    if _multi_rank():
+        torch.distributed.barrier()
+    if dev.type == "cuda":
+        torch.cuda.synchronize(dev)
+
+
+def max_over_ranks(x, dev):
+    """The largest of every rank's value of x (the slowest replica sets the job's time)."""
+    if not _multi_rank():
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ms_per_step_local, world, dev):
+    """(whole-job iterations/s, ms per step): every rank runs its own replica, so the job
+    completes world iterations per step in the slowest rank's time."""
+    ms = max_over_ranks(ms_per_step_local, dev)
+    return world / (ms / 1e3), ms
+
+
 # ----------------------------------------------------------------------- CPU oracle
 def time_oracle(s, steps, warmup, one_chunk=True):
     """Time the FP64 oracle's messenger step on the host (chunk 0 only when one_chunk,
@@ -208,10 +241,7 @@ def run_gpu(args):
     plan.stage(B.MM_STAGE_LOAD, map_inout=m)
     for i in range(args.warmup):
         step(i)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
+    fence(dev)
 
     uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", local))
     sampler = ClockSampler(("GPU-" + uuid) if "-" in uuid and not uuid.startswith("GPU") else uuid)
@@ -224,41 +254,27 @@ def run_gpu(args):
     for k in range(args.steps):
         step(args.warmup + k, evs[k])
     t_end.record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        torch.distributed.barrier()
+    fence(dev)
     total_ms = t_start.elapsed_time(t_end)
     stage_names = ["gather_fft", "filter", "ifft_bin"]
     # per-launch durations of each kernel kind (one launch per batch per iteration)
     stage_ms = {nm: [evs[k][b][j].elapsed_time(evs[k][b][j + 1]) for k in range(args.steps)
                      for b in range(nb)] for j, nm in enumerate(stage_names)}
     stage_ms["map"] = [evs[k][nb][0].elapsed_time(evs[k][nb][1]) for k in range(args.steps)]
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    _, stage_ms_step = job_rate(total_ms / args.steps, world, dev)
 
     # the same iterations replayed as one captured CUDA graph per iteration
     mg = m.clone()
     lam_g = np.array([float(sched[(args.warmup + k) % len(sched)]) for k in range(args.steps)])
     plan.messenger_graph(mg, lam_g[:2])
-    torch.cuda.synchronize(dev)
+    fence(dev)
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
     plan.messenger_graph(mg, lam_g)
     g1.record(stream)
-    torch.cuda.synchronize(dev)
-    graph_ms = g0.elapsed_time(g1) / args.steps
+    fence(dev)
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([graph_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        graph_ms = float(t.item())
-    stage_ms_step = ms_step
-    ms_step = graph_ms
-    value = world / (graph_ms / 1e3)
+    value, ms_step = job_rate(g0.elapsed_time(g1) / args.steps, world, dev)
 
     # the plain FP64 single-launch-per-iteration step on the same GPU (comparison bar)
     plain_ms = None
@@ -273,6 +289,29 @@ def run_gpu(args):
         p1.record(stream)
         torch.cuda.synchronize(dev)
         plain_ms = p0.elapsed_time(p1) / len(lam_p)
+
+    # cuFFT (through torch.fft, a library call timed only as a comparison) against this
+    # library's rfft of the same chunks (column + row kernels, natural-order output)
+    fft_cmp = None
+    if not args.no_plain:
+        tod_dev = plan.tod.view(len(s["offsets"]) - 1, -1)
+        spec = torch.empty(tod_dev.shape[0] * (tod_dev.shape[1] // 2 + 1), 2, dtype=torch.float32,
+                           device=dev)
+        for _ in range(3):
+            torch.fft.rfft(tod_dev, dim=1)
+            plan.rfft(plan.tod, spec)
+        f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        reps = 10
+        f0.record(stream)
+        for _ in range(reps):
+            torch.fft.rfft(tod_dev, dim=1)
+        f1.record(stream)
+        for _ in range(reps):
+            plan.rfft(plan.tod, spec)
+        f2.record(stream)
+        torch.cuda.synchronize(dev)
+        fft_cmp = {"cufft_rfft_ms": f0.elapsed_time(f1) / reps, "mm_rfft_ms": f1.elapsed_time(f2) / reps,
+                   "what": "rfft of 8 x 2^22 float32 samples, complex64 out"}
 
     # end to end through the public call, host buffers: map in (pinned), one iteration,
     # map and chi^2 out, synchronised every step
@@ -289,6 +328,7 @@ def run_gpu(args):
         m_back.copy_(m_dev, non_blocking=True)
         c_back.copy_(c_dev, non_blocking=True)
         torch.cuda.synchronize(dev)
+    fence(dev)
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         m_dev.copy_(m_back if i else m_host, non_blocking=True)
@@ -297,7 +337,9 @@ def run_gpu(args):
         c_back.copy_(c_dev, non_blocking=True)
         torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * npix * nc,
+    fence(dev)
+    e2e_rate, _ = job_rate(e2e_s * 1e3, world, dev)
+    e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 8 * npix * nc,
            "d2h_bytes_per_step": 8 * npix * nc + 8}
 
     tol = time_to_tolerance(plan, s, dev, stream, args) if not args.no_tolerance else None
@@ -339,6 +381,7 @@ def run_gpu(args):
                   "stage by stage with events between the kernels",
         "stage_loop_ms_per_step": stage_ms_step,
         "fp64_plain_ms_per_step": plain_ms,
+        "fft_vs_cufft": fft_cmp,
         "speedup_vs_fp64_plain": None if plain_ms is None else plain_ms / ms_step,
         "stage_ms_per_launch": {k: round(v, 5) for k, v in avg.items()},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
