@@ -193,6 +193,15 @@ mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, void* state, 
 mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev,
                   void* stream);
 
+/* chi^2 per Fourier mode (the online convergence diagnostic of Sec. 3.1 / Sec. 4.1):
+ * modes[off_c + k] = |d~_k - (P m)~_k|^2 / (n_c N'_c(f_k)), k = 0..n_c/2 for every chunk c
+ * (off_c = sum of (n_c'/2 + 1) over the chunks before c; device float64), with N' = N +
+ * (lambda - 1) T.  Each value has unit mean for the true map and sum_k w_k modes[k] (w_k =
+ * 1 at DC and Nyquist, 2 elsewhere) is that chunk's chi^2.  *chi2_dev (or NULL) receives the
+ * total as mm_chi2 does. */
+mm_status mm_chi2_modes(mm_plan p, const double* map, double lambda, double* chi2_dev,
+                        double* modes, void* stream);
+
 /* Operators, for testing and for callers composing their own solvers.
  * mm_apply_pointing:   tod_out[s] = (P m)_s in FP32 (Eq. 1), cut pixels contribute 0.
  * mm_apply_pointing_T: acc_out[p][c] = sum_s P_sp,c tod[s] in FP64 over every sample with

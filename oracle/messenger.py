@@ -173,6 +173,17 @@ def chi2(prob, m, lam=1.0):
     return total
 
 
+def chi2_modes(prob, m, lam=1.0):
+    """chi^2 per Fourier mode of each chunk (Sec. 3.1 examines it per mode): for bin k,
+    |d~_k - (Pm)~_k|^2 / (n N'_k), which has unit mean when m is the true map."""
+    out = []
+    for c, (a, b) in enumerate(prob.chunks()):
+        n = b - a
+        r = prob.dtilde[c] - np.fft.rfft(prob.P(m, a, b))
+        out.append(np.abs(r) ** 2 / (n * (prob.psd[c] + (lam - 1.0) * prob.tau[c])))
+    return out
+
+
 # ---------------------------------------------------------------- messenger iteration
 def messenger_step(prob, m, lam):
     """One messenger iteration (Sec. 2.1):

@@ -50,6 +50,7 @@ SIGNATURES = {
     "mm_pcg_state_bytes": (ctypes.c_int, [_vp, _szp]),
     "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
+    "mm_chi2_modes": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "mm_apply_pointing": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mm_apply_pointing_T": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mm_rfft": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -254,6 +255,17 @@ class Plan:
         _check("mm_chi2", load().mm_chi2(self._h, _ptr(map_in), float(lam), _ptr(out),
                                          _stream(stream)))
         return out
+
+    def chi2_modes(self, map_in, lam: float = 1.0, stream=None):
+        """(total chi^2 [1], per-mode chi^2 [sum_c (n_c/2+1)]) as CUDA float64 tensors."""
+        import torch
+        n_modes = int(sum(int(self.offsets[c + 1] - self.offsets[c]) // 2 + 1
+                          for c in range(self.n_chunks)))
+        total = torch.zeros(1, dtype=torch.float64, device=self.device)
+        modes = torch.empty(n_modes, dtype=torch.float64, device=self.device)
+        _check("mm_chi2_modes", load().mm_chi2_modes(self._h, _ptr(map_in), float(lam), _ptr(total),
+                                                     _ptr(modes), _stream(stream)))
+        return total, modes
 
     # -------------------------------------------------------------------- operators
     def apply_pointing(self, map_in, tod_out, stream=None):

@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <new>
 #include <unordered_map>
@@ -1247,6 +1248,71 @@ extern "C" mm_status mm_chi2(mm_plan p, const double* map, double lambda, double
   if (st != MM_OK) return st;
   RowArgs a{kRowChi2, lambda, chi2_dev, nullptr};
   FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s)));
+  return MM_OK;
+}
+
+// In place over `io`: on entry the natural-order rfft X_k of P m for every chunk (float2,
+// chunk c at desc[c].spec + c, M + 1 bins), on exit |d~_k - X_k|^2 / (n N'_k) as float64
+// (same 8 bytes per bin).  One thread per bin; the chunk is found by bisection on the
+// bin offsets.  The weighted block sums go to *chi2 (when given) by one FP64 atomic each.
+__global__ void k_chi2_modes(const ChunkDesc* __restrict__ desc, int n_chunks, int64_t n_bins,
+                             const float2* __restrict__ dtab, const float* __restrict__ nbar,
+                             const float* __restrict__ nyq, double lambda, void* io,
+                             double* chi2) {
+  double w = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_bins;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = n_chunks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (desc[mid].spec + mid <= i) lo = mid; else hi = mid - 1;
+    }
+    const ChunkDesc d = desc[lo];
+    const int k = (int)(i - (d.spec + lo));
+    const float2 X = reinterpret_cast<const float2*>(io)[i];
+    double dre, dim = 0.0, nb;
+    if (k == 0) { dre = dtab[d.spec].x; nb = nbar[d.spec]; }
+    else if (k == d.M) { dre = dtab[d.spec].y; nb = nyq[lo]; }
+    else {
+      const int64_t slot = d.spec + (int64_t)(k & (d.M1 - 1)) * d.M2 + k / d.M1;
+      const float2 D = dtab[slot];
+      dre = D.x; dim = D.y; nb = nbar[slot];
+    }
+    const double er = dre - X.x, ei = dim - X.y;
+    const double v = (er * er + ei * ei) / ((nb + lambda * d.tau) * d.n);
+    reinterpret_cast<double*>(io)[i] = v;
+    w += (k == 0 || k == d.M) ? v : 2.0 * v;
+  }
+  if (chi2 == nullptr) return;
+  for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+    if (threadIdx.x == 0) atomicAdd(chi2, w);
+  }
+}
+
+extern "C" mm_status mm_chi2_modes(mm_plan p, const double* map, double lambda, double* chi2_dev,
+                                   double* modes, void* stream) {
+  MM_ARG(p != nullptr && map != nullptr && modes != nullptr, "NULL argument");
+  MM_ARG(lambda >= 1.0 && isfinite(lambda), "lambda must be finite and >= 1");
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  cudaStream_t s = S(stream);
+  if (chi2_dev) MM_CUDA(cudaMemsetAsync(chi2_dev, 0, sizeof(double), s));
+  mm_status st = load_map(p, map, s);
+  if (st != MM_OK) return st;
+  // the spectrum of P m, natural order, into the caller's buffer (8 bytes per bin either way)
+  RowArgs a{kRowNatural, 1.0, nullptr, reinterpret_cast<float2*>(modes)};
+  FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s)));
+  const int64_t n_bins = p->spec_total + p->n_chunks;
+  int grid = 0;
+  MM_CUDA(persistent_grid(k_chi2_modes, 256, 0, (int)std::min<int64_t>(blocks_for(n_bins, 256), 1 << 20), &grid));
+  k_chi2_modes<<<grid, 256, 0, s>>>(
+      p->d_desc, p->n_chunks, n_bins, p->dtab, p->nbar, p->nyq, lambda, modes, chi2_dev);
+  LAUNCHED("k_chi2_modes");
   return MM_OK;
 }
 

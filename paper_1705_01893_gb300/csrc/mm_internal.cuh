@@ -82,7 +82,7 @@ struct mm_plan_s {
   double* c0;       // [n_chunks] (1/n) sum_k w_k / N_k
   float2* ybuf;     // one batch's four-step intermediate (L2-resident between passes)
   size_t ybuf_bytes;
-  bool theta_ok;
+  bool theta_ok;     // noise from (sigma, f_knee, alpha) with tau = sigma^2: theta gradients defined
   // CUDA graph of one messenger iteration (captured on first use of mm_messenger_graph)
   cudaGraphExec_t graph_exec;
   cudaStream_t graph_stream;
@@ -90,7 +90,7 @@ struct mm_plan_s {
   int lam_cap;
   int* iter;           // device iteration counter
   double** chi2_base;  // device pointer slot: chi^2 output array or NULL
-  double* map64;       // device FP64 copy of the current map (graph mode)    // noise from (sigma, f_knee, alpha) with tau = sigma^2: theta gradients defined
+  double* map64;       // device FP64 copy of the current map (graph mode)
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;

@@ -352,3 +352,16 @@ def test_plain_fp64_step(cfg):
     m_ref, chi_ref = O.run_messenger(prob, lam)
     assert rel(m.cpu().numpy(), m_ref) <= 1e-5
     assert np.max(np.abs(chi.cpu().numpy() - chi_ref) / chi_ref) <= 1e-6
+
+
+def test_chi2_per_mode():
+    s = synth.config_iqu(16, 3, 1 << 12, 42)
+    prob = O.problem_from_synth(s)
+    plan = gpu_plan(s)
+    m = np.random.default_rng(7).standard_normal((s["npix"], 3)) * prob.valid[:, None]
+    for lam in (1.0, 20.0):
+        tot, modes = plan.chi2_modes(to_dev(m), lam)
+        ref = np.concatenate(O.chi2_modes(prob, m, lam))
+        got = modes.cpu().numpy()
+        assert rel(got, ref) <= 1e-5
+        assert abs(tot.item() - O.chi2(prob, m, lam)) <= 1e-5 * O.chi2(prob, m, lam)

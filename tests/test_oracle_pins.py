@@ -269,3 +269,17 @@ def test_planted_mistakes(monkeypatch, which):
         except (AssertionError, np.linalg.LinAlgError, FloatingPointError):
             failures += 1
     assert failures >= 1, which
+
+
+def test_chi2_modes_sum_and_unit_mean():
+    """Per-mode chi^2 (Sec. 3.1): its multiplicity-weighted sum is chi^2, and for data that
+    are pure noise around the true map each mode has unit mean (a chi^2 of 2 degrees of
+    freedom rescaled to unit mean)."""
+    s = synth.config_iqu(16, 2, 1 << 14, 41)
+    prob = O.problem_from_synth(s)
+    m = s["m_true"] * prob.valid[:, None]
+    modes = O.chi2_modes(prob, m)
+    tot = sum(np.sum(O.rfft_weights(len(md) * 2 - 2) * md) for md in modes)
+    assert abs(tot - O.chi2(prob, m)) <= 1e-10 * tot
+    allm = np.concatenate([md[1:-1] for md in modes])
+    assert abs(allm.mean() - 1.0) < 0.05
