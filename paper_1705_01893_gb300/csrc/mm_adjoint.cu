@@ -434,6 +434,10 @@ extern "C" mm_status mm_adjoint_work_bytes(mm_plan p, int n_iter, int ckpt_every
     mm_set_error("mm_adjoint_work_bytes: bad argument");
     return MM_ERR_ARG;
   }
+  if (p->n_gen > 0) {
+    mm_set_error("mm_adjoint_work_bytes: chunk lengths that are not powers of two are not supported");
+    return MM_ERR_UNSUPPORTED;
+  }
   *bytes = adj_layout(p, n_iter, ckpt_every).total;
   return MM_OK;
 }
@@ -456,6 +460,10 @@ extern "C" mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int 
     mm_set_error("mm_messenger_adjoint: NULL pointer or non-positive count");
     return MM_ERR_ARG;
   }
+  if (((uintptr_t)grad_tod & 15) != 0) {
+    mm_set_error("mm_messenger_adjoint: grad_tod must be 16-byte aligned");
+    return MM_ERR_ARG;
+  }
   if (!p->noise_set) {
     mm_set_error("mm_messenger_adjoint: mm_set_noise_psd has not run");
     return MM_ERR_STATE;
@@ -463,6 +471,10 @@ extern "C" mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int 
   if (grad_theta && !p->theta_ok) {
     mm_set_error("mm_messenger_adjoint: theta gradients need the parametric noise model with "
                  "tau = sigma^2");
+    return MM_ERR_UNSUPPORTED;
+  }
+  if (p->n_gen > 0) {
+    mm_set_error("mm_messenger_adjoint: chunk lengths that are not powers of two are not supported");
     return MM_ERR_UNSUPPORTED;
   }
   for (int g = 0; g < p->n_groups; ++g)

@@ -8,6 +8,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <mutex>
 #include <new>
 #include <unordered_map>
@@ -51,17 +53,26 @@ static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s)
 
 cudaError_t mm::resident_ctas(const void* kernel, int threads, size_t smem, int* out) {
   static std::mutex mu;
-  static std::unordered_map<const void*, int> cache;
+  static std::map<std::tuple<const void*, int, int, size_t>, int> cache;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  const void* key = static_cast<const char*>(kernel) + dev;  // one entry per device
+  const auto key = std::make_tuple(kernel, dev, threads, smem);
   {
     std::lock_guard<std::mutex> g(mu);
     auto it = cache.find(key);
     if (it != cache.end()) { *out = it->second; return cudaSuccess; }
   }
-  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+  // allow the kernel the device's whole opt-in shared memory once, so that launches of the
+  // same kernel with different tile sizes never depend on which one came first
+  int optin = 0;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+    return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, kernel)) != cudaSuccess) return e;
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;   // opt-in limit minus static shared memory
+  if (dyn_max < 0 || smem > (size_t)dyn_max) return cudaErrorInvalidValue;
+  if ((e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max)) !=
       cudaSuccess)
     return e;
   int nsm = 0, occ = 0;
@@ -94,13 +105,57 @@ static bool fft_shape(int64_t n, int* M, int* M1, int* M2) {
   return true;
 }
 
+static bool smooth235(int64_t x) {
+  if (x < 1) return false;
+  for (int f : {2, 3, 5})
+    while (x % f == 0) x /= f;
+  return x == 1;
+}
+
+// General path: n with prime factors 2, 3, 5 only.  Even n: M = n / 2 (packed real FFT),
+// odd n: M = n (complex FFT of the real sequence).  M1 is the divisor of M nearest sqrt(M)
+// with M1 <= kGenMaxM1 and M2 = M / M1 <= kGenMaxM2.
+static bool gen_shape(int64_t n, int* M, int* M1, int* M2, int* cplx) {
+  if (n < 4 || n > (int64_t(1) << 24) || !smooth235(n)) return false;
+  const int64_t m = (n & 1) ? n : n / 2;
+  int best = 0;
+  double bd = 1e300;
+  for (int64_t d = 1; d <= kGenMaxM1 && d <= m; ++d) {
+    if (m % d || m / d > kGenMaxM2) continue;
+    const double dist = fabs(log((double)d) - 0.5 * log((double)m));
+    if (dist < bd) { bd = dist; best = (int)d; }
+  }
+  if (best == 0) return false;
+  *M = (int)m;
+  *M1 = best;
+  *M2 = (int)(m / best);
+  *cplx = (int)(n & 1);
+  return true;
+}
+
+// Radix sequence of a general DFT length: radix 8 while 8 divides, then 4 or 2, then 5s,
+// then 3s (any order is a valid Stockham schedule; larger radices mean fewer passes).
+static int radix_plan(int L, int8_t* rad) {
+  int n = 0;
+  while (L % 8 == 0 && n < kMaxRadices) { rad[n++] = 8; L /= 8; }
+  if (L % 4 == 0 && n < kMaxRadices) { rad[n++] = 4; L /= 4; }
+  if (L % 2 == 0 && n < kMaxRadices) { rad[n++] = 2; L /= 2; }
+  while (L % 5 == 0 && n < kMaxRadices) { rad[n++] = 5; L /= 5; }
+  while (L % 3 == 0 && n < kMaxRadices) { rad[n++] = 3; L /= 3; }
+  return L == 1 ? n : -1;
+}
+
 static int log_lo_of(int M) {
   int p = 0;
   while ((1 << p) < M) ++p;
   return (p + 1) / 2;
 }
 
-static size_t tw_count(int M, int M1, int M2) {
+static const int kGenLogLo = 10;
+
+static size_t tw_count(int M, int M1, int M2, bool general) {
+  if (general)
+    return (size_t)M1 + M2 + (size_t(1) << kGenLogLo) + (size_t)(M >> kGenLogLo) + 1 + M1 + M2;
   const int lo = log_lo_of(M);
   return (size_t)tw_size(M1) + tw_size(M2) + (size_t(1) << lo) + (size_t)(M >> lo) + M1 + M2;
 }
@@ -108,11 +163,14 @@ static size_t tw_count(int M, int M1, int M2) {
 // -------------------------------------------------------------------- workspace layout
 struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
-      ybuf, scal, tpix, tcos, tsin, lam, iter, map64, total, ybytes;
+      ybuf, scal, tpix, tcos, tsin, lam, iter, map64, groups, gen, total, ybytes;
   int lam_cap;
   int n_groups;
   int gM[kMaxGroups], gM1[kMaxGroups], gM2[kMaxGroups], gcount[kMaxGroups], gbatch[kMaxGroups];
+  int gn[kMaxGroups], ggen[kMaxGroups], gcplx[kMaxGroups];
   std::vector<int> chunk_group;
+  std::vector<int> gen_list;            // general chunks in plan order
+  std::vector<Batch> gen_batches;
   int64_t spec_total, n_total;
 };
 
@@ -136,18 +194,27 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   MM_ARG(off[0] >= 0, "offsets[0] must be >= 0");
   L->n_groups = 0;
   L->chunk_group.assign(n_chunks, -1);
+  L->gen_list.clear();
+  L->gen_batches.clear();
   L->spec_total = 0;
   for (int c = 0; c < n_chunks; ++c) {
     const int64_t n = off[c + 1] - off[c];
-    int M, M1, M2;
-    if (!fft_shape(n, &M, &M1, &M2)) {
-      mm_set_error("chunk %d: length %lld unsupported (need n even, n/2 a power of two in "
-                   "[2^8, 2^23])", c, (long long)n);
-      return MM_ERR_UNSUPPORTED;
+    MM_ARG(n >= 1, "chunk %d is empty or offsets decrease", c);
+    int M, M1, M2, cplx = 0;
+    // power-of-two chunks on 16-byte boundaries take the compile-time kernels (vector loads)
+    bool general = false;
+    if (!(fft_shape(n, &M, &M1, &M2) && off[c] % 4 == 0)) {
+      if (!gen_shape(n, &M, &M1, &M2, &cplx)) {
+        mm_set_error("chunk %d: length %lld unsupported (need prime factors 2, 3, 5 only and "
+                     "n <= 2^24; n/2 up to 2^21 for lengths that are not powers of two)",
+                     c, (long long)n);
+        return MM_ERR_UNSUPPORTED;
+      }
+      general = true;
     }
     int g = -1;
     for (int i = 0; i < L->n_groups; ++i)
-      if (L->gM[i] == M) g = i;
+      if (L->gn[i] == n && L->ggen[i] == (int)general) g = i;
     if (g < 0) {
       if (L->n_groups == kMaxGroups) {
         mm_set_error("more than %d distinct chunk lengths", kMaxGroups);
@@ -155,17 +222,21 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
       }
       g = L->n_groups++;
       L->gM[g] = M; L->gM1[g] = M1; L->gM2[g] = M2; L->gcount[g] = 0;
+      L->gn[g] = (int)n; L->ggen[g] = general; L->gcplx[g] = cplx;
     }
     L->gcount[g]++;
     L->chunk_group[c] = g;
     L->spec_total += M;
+    if (general) L->gen_list.push_back(c);
   }
   L->n_total = off[n_chunks];
   MM_ARG(L->n_total < (int64_t(1) << 31) * 2, "too many samples");
   size_t tw = 0, ybytes = 0;
   const size_t budget = ybuf_budget();
   for (int g = 0; g < L->n_groups; ++g) {
-    tw += tw_count(L->gM[g], L->gM1[g], L->gM2[g]);
+    tw += tw_count(L->gM[g], L->gM1[g], L->gM2[g], L->ggen[g]);
+    L->gbatch[g] = 0;
+    if (L->ggen[g]) continue;
     const size_t per = sizeof(float2) * (size_t)L->gM[g];
     size_t b = budget / per;
     if (b < 1) b = 1;
@@ -173,6 +244,24 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
     L->gbatch[g] = (int)b;
     if (b * per > ybytes) ybytes = b * per;
   }
+  // general chunks: consecutive runs of the general list within the same budget
+  {
+    size_t cur = 0;
+    int first = 0;
+    const int ng = (int)L->gen_list.size();
+    for (int i = 0; i < ng; ++i) {
+      const size_t per = sizeof(float2) * (size_t)L->gM[L->chunk_group[L->gen_list[i]]];
+      if (i > first && cur + per > budget) {
+        L->gen_batches.push_back(Batch{-1, first, i - first});
+        first = i;
+        cur = 0;
+      }
+      cur += per;
+      if (cur > ybytes) ybytes = cur;
+    }
+    if (ng > first) L->gen_batches.push_back(Batch{-1, first, ng - first});
+  }
+  const size_t ngen = L->gen_list.size();
   const size_t np = (size_t)n_pix;
   const size_t blk = ncomp == 3 ? 6 : 1;
   size_t o = 0;
@@ -206,6 +295,9 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->lam = take(sizeof(double) * L->lam_cap);
   L->iter = take(128);
   L->map64 = take(sizeof(double) * ncomp * np);
+  // general path: device groups, chunk list and three prefix arrays
+  L->groups = take(sizeof(Group) * L->n_groups);
+  L->gen = take(sizeof(int) * (ngen + 1) + 3 * sizeof(int64_t) * (ngen + 1) + 64);
   L->total = o;
   return MM_OK;
 }
@@ -275,7 +367,7 @@ struct NoiseArgs {
 };
 
 __device__ __forceinline__ double psd_value(const NoiseArgs& a, int c, const ChunkDesc& d, int k) {
-  if (a.psd) return a.psd[d.spec + c + k];
+  if (a.psd) return a.psd[d.nat + k];
   const double* q = a.params + 4 * c;      // sigma, f_knee, alpha, f_sample
   const int kk = k == 0 ? 1 : k;           // DC bin floored to bin 1
   const double f = (double)kk * q[3] / (double)d.n;
@@ -291,14 +383,17 @@ __global__ void k_noise(NoiseArgs a) {
   for (int slot = blockIdx.x * blockDim.x + threadIdx.x; slot < d.M; slot += gridDim.x * blockDim.x) {
     const int k1 = slot / d.M2, k2 = slot % d.M2;
     const int k = k1 + d.M1 * k2;
-    const double N = psd_value(a, c, d, k);
+    // complex chunks hold every frequency 0..n-1; frequency k is rfft bin min(k, n - k)
+    const int kb = d.cplx && 2 * k > d.n ? d.n - k : k;
+    const double N = psd_value(a, c, d, kb);
     const double nb = N - d.tau;
     a.nbar[d.spec + slot] = (float)nb;
-    double w = k == 0 ? 1.0 : 2.0;
+    double w = k == 0 || d.cplx ? 1.0 : 2.0;
     sum += w / N;
     mx = fmax(mx, nb / d.tau);
     mn = fmin(mn, nb);
-    if (k == 0) {
+    if (k == 0 && d.cplx) a.nyq[c] = 0.f;
+    if (k == 0 && !d.cplx) {
       const double NM = psd_value(a, c, d, d.M);
       const double nbM = NM - d.tau;
       a.nyq[c] = (float)nbM;
@@ -333,7 +428,7 @@ __global__ void k_min_psd(const ChunkDesc* desc, const double* psd, double* out)
   const int c = blockIdx.x;
   const ChunkDesc d = desc[c];
   double mn = 1e300;
-  for (int k = threadIdx.x; k <= d.M; k += blockDim.x) mn = fmin(mn, psd[d.spec + c + k]);
+  for (int k = threadIdx.x; k <= d.n / 2; k += blockDim.x) mn = fmin(mn, psd[d.nat + k]);
   for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
   __shared__ double r[32];
   if ((threadIdx.x & 31) == 0) r[threadIdx.x >> 5] = mn;
@@ -724,6 +819,32 @@ __global__ void k_pcg_dir(int64_t n_pix, const double* __restrict__ z, double* _
 // ------------------------------------------------------------------------- plan API
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Prefix sums of the general chunk list for the current column-tile width, uploaded with
+// the list itself (synchronous with respect to the host arrays: the copy is staged).
+static cudaError_t gen_set_tiles(mm_plan_s* p, cudaStream_t s) {
+  const int ng = p->n_gen, nb = p->gen_tune.col_nb;
+  int64_t ct = 0, rj = 0, yo = 0;
+  for (int i = 0; i < ng; ++i) {
+    const ChunkDesc& d = p->h_desc[p->h_gen_chunks[i]];
+    p->h_gen_ctile[i] = ct;
+    p->h_gen_rjob[i] = rj;
+    p->h_gen_yoff[i] = yo;
+    ct += (d.M2 + nb - 1) / nb;
+    rj += d.M1 / 2 + 1;
+    yo += d.M;
+  }
+  p->h_gen_ctile[ng] = ct;
+  p->h_gen_rjob[ng] = rj;
+  p->h_gen_yoff[ng] = yo;
+  cudaError_t e;
+  const size_t b = sizeof(int64_t) * (ng + 1);
+  if ((e = cudaMemcpyAsync(p->gen_ctile, p->h_gen_ctile, b, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(p->gen_rjob, p->h_gen_rjob, b, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(p->gen_yoff, p->h_gen_yoff, b, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(p->gen_chunks, p->h_gen_chunks, sizeof(int) * ng, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
+
 extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t* offsets,
                                       const int32_t* pix, const void* cos2psi,
                                       const void* sin2psi, int weight_dtype, int64_t n_pix,
@@ -785,22 +906,39 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   p->tpix = reinterpret_cast<int32_t*>(ws + L.tpix);
   p->tcos = ncomp == 3 ? static_cast<void*>(ws + L.tcos) : nullptr;
   p->tsin = ncomp == 3 ? static_cast<void*>(ws + L.tsin) : nullptr;
+  p->d_groups = reinterpret_cast<Group*>(ws + L.groups);
+  p->n_gen = (int)L.gen_list.size();
+  {
+    char* gb = ws + L.gen;
+    const size_t ng1 = (size_t)p->n_gen + 1;
+    p->gen_ctile = reinterpret_cast<int64_t*>(gb);
+    p->gen_rjob = p->gen_ctile + ng1;
+    p->gen_yoff = p->gen_rjob + ng1;
+    p->gen_chunks = reinterpret_cast<int*>(p->gen_yoff + ng1);
+  }
+  p->h_gen_ctile = p->h_gen_rjob = p->h_gen_yoff = nullptr;
+  p->h_gen_chunks = nullptr;
+  p->gen_tune = GenTune{8, 256, 256};
 
   // host descriptors, grouped chunk lists
   p->h_desc = new (std::nothrow) ChunkDesc[n_chunks];
   p->h_chunk_group = new (std::nothrow) int[n_chunks];
   std::vector<int> order;
   if (!p->h_desc || !p->h_chunk_group) { mm_plan_destroy(p); mm_set_error("host allocation failed"); return MM_ERR_NOMEM; }
-  int64_t spec = 0;
+  int64_t spec = 0, nat = 0;
   for (int c = 0; c < n_chunks; ++c) {
     ChunkDesc& d = p->h_desc[c];
     const int g = L.chunk_group[c];
     d.off = offsets[c];
     d.spec = spec;
+    d.nat = nat;
     d.n = (int)(offsets[c + 1] - offsets[c]);
     d.M = L.gM[g]; d.M1 = L.gM1[g]; d.M2 = L.gM2[g];
+    d.grp = g;
+    d.cplx = L.gcplx[g];
     d.tau = 1.0;
     spec += d.M;
+    nat += d.n / 2 + 1;
     p->h_chunk_group[c] = g;
   }
   p->n_groups = L.n_groups;
@@ -810,31 +948,52 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   for (int g = 0; g < L.n_groups; ++g) {
     Group& G = p->groups[g];
     G.M = L.gM[g]; G.M1 = L.gM1[g]; G.M2 = L.gM2[g];
-    G.log_lo = log_lo_of(G.M);
+    G.general = L.ggen[g];
+    G.cplx = L.gcplx[g];
+    G.log_lo = G.general ? kGenLogLo : log_lo_of(G.M);
+    G.nr1 = G.nr2 = 0;
+    if (G.general) {
+      G.nr1 = radix_plan(G.M1, G.rad1);
+      G.nr2 = radix_plan(G.M2, G.rad2);
+    }
     G.chunks = d_chunks + order.size();
     G.n_chunks = 0;
     G.batch = L.gbatch[g];
     for (int c = 0; c < n_chunks; ++c)
       if (L.chunk_group[c] == g) { order.push_back(c); G.n_chunks++; }
     float2* t = p->tw_pool + tw_off;
-    G.tw_col = t; t += tw_size(G.M1);
-    G.tw_row = t; t += tw_size(G.M2);
+    G.tw_col = t; t += G.general ? G.M1 : tw_size(G.M1);
+    G.tw_row = t; t += G.general ? G.M2 : tw_size(G.M2);
     G.tw_lo = t; t += (1 << G.log_lo);
-    G.tw_hi = t; t += (G.M >> G.log_lo);
+    G.tw_hi = t; t += (G.M >> G.log_lo) + (G.general ? 1 : 0);
     G.tw_pack_a = t; t += G.M1;
     G.tw_pack_b = t; t += G.M2;
-    tw_off += tw_count(G.M, G.M1, G.M2);
+    tw_off += tw_count(G.M, G.M1, G.M2, G.general);
   }
   {
-    int nb = 0;
-    for (int g = 0; g < L.n_groups; ++g) nb += (p->groups[g].n_chunks + L.gbatch[g] - 1) / L.gbatch[g];
-    p->h_batches = new (std::nothrow) Batch[nb];
-    if (!p->h_batches) { mm_plan_destroy(p); mm_set_error("host allocation failed"); return MM_ERR_NOMEM; }
+    int nb = (int)L.gen_batches.size();
     for (int g = 0; g < L.n_groups; ++g)
+      if (!L.ggen[g]) nb += (p->groups[g].n_chunks + L.gbatch[g] - 1) / L.gbatch[g];
+    p->h_batches = new (std::nothrow) Batch[nb > 0 ? nb : 1];
+    if (!p->h_batches) { mm_plan_destroy(p); mm_set_error("host allocation failed"); return MM_ERR_NOMEM; }
+    for (int g = 0; g < L.n_groups; ++g) {
+      if (L.ggen[g]) continue;
       for (int f = 0; f < p->groups[g].n_chunks; f += L.gbatch[g]) {
         const int cnt = p->groups[g].n_chunks - f < L.gbatch[g] ? p->groups[g].n_chunks - f : L.gbatch[g];
         p->h_batches[p->n_batches++] = Batch{g, f, cnt};
       }
+    }
+    for (const Batch& b : L.gen_batches) p->h_batches[p->n_batches++] = b;
+  }
+  // general list and its prefix sums (column tiles of the tuned width, row jobs, offsets)
+  if (p->n_gen > 0) {
+    const int ng = p->n_gen;
+    p->h_gen_chunks = new (std::nothrow) int[ng];
+    p->h_gen_ctile = new (std::nothrow) int64_t[3 * (ng + 1)];
+    if (!p->h_gen_chunks || !p->h_gen_ctile) { mm_plan_destroy(p); mm_set_error("host allocation failed"); return MM_ERR_NOMEM; }
+    p->h_gen_rjob = p->h_gen_ctile + (ng + 1);
+    p->h_gen_yoff = p->h_gen_rjob + (ng + 1);
+    for (int i = 0; i < ng; ++i) p->h_gen_chunks[i] = L.gen_list[i];
   }
   cudaStream_t s = S(stream);
   auto fail = [&](const char* what, cudaError_t e) {
@@ -849,14 +1008,25 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
                            cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail("chunk list upload", e);
   for (int g = 0; g < L.n_groups; ++g) {
     const Group& G = p->groups[g];
-    k_pass_twiddles<<<blocks_for(tw_size(G.M1), 256), 256, 0, s>>>(G.tw_col, G.M1);
-    k_pass_twiddles<<<blocks_for(tw_size(G.M2), 256), 256, 0, s>>>(G.tw_row, G.M2);
+    if (G.general) {
+      k_twiddles<<<blocks_for(G.M1, 256), 256, 0, s>>>(G.tw_col, G.M1, 1, G.M1);
+      k_twiddles<<<blocks_for(G.M2, 256), 256, 0, s>>>(G.tw_row, G.M2, 1, G.M2);
+    } else {
+      k_pass_twiddles<<<blocks_for(tw_size(G.M1), 256), 256, 0, s>>>(G.tw_col, G.M1);
+      k_pass_twiddles<<<blocks_for(tw_size(G.M2), 256), 256, 0, s>>>(G.tw_row, G.M2);
+    }
+    const int nhi = (G.M >> G.log_lo) + (G.general ? 1 : 0);
     struct { float2* o; int cnt, mul, L; } tabs[4] = {
-        {G.tw_lo, 1 << G.log_lo, 1, G.M}, {G.tw_hi, G.M >> G.log_lo, 1 << G.log_lo, G.M},
+        {G.tw_lo, 1 << G.log_lo, 1, G.M}, {G.tw_hi, nhi, 1 << G.log_lo, G.M},
         {G.tw_pack_a, G.M1, 1, 2 * G.M}, {G.tw_pack_b, G.M2, G.M1, 2 * G.M}};
     for (auto& tb : tabs) {
       k_twiddles<<<blocks_for(tb.cnt, 256), 256, 0, s>>>(tb.o, tb.cnt, tb.mul, tb.L);
     }
+  }
+  if ((e = cudaMemcpyAsync(p->d_groups, p->groups, sizeof(Group) * L.n_groups,
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail("group upload", e);
+  if (p->n_gen > 0) {
+    if ((e = gen_set_tiles(p, s)) != cudaSuccess) return fail("general chunk tables", e);
   }
   if ((e = cudaMemsetAsync(p->hits, 0, sizeof(int32_t) * n_pix, s)) != cudaSuccess) return fail("memset", e);
   if ((e = cudaMemsetAsync(p->scal, 0, sizeof(double) * kScalCount, s)) != cudaSuccess) return fail("memset", e);
@@ -880,6 +1050,8 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
 
 extern "C" void mm_plan_destroy(mm_plan p) {
   if (!p) return;
+  delete[] p->h_gen_chunks;
+  delete[] p->h_gen_ctile;
   delete[] p->h_desc;
   delete[] p->h_chunk_group;
   delete[] p->h_batches;
@@ -922,6 +1094,7 @@ extern "C" mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const do
   MM_ARG(p != nullptr, "plan is NULL");
   MM_ARG((psd_dev != nullptr) != (params != nullptr), "give exactly one of psd / params");
   MM_ARG(tod != nullptr, "tod is NULL");
+  MM_ARG(((uintptr_t)tod & 7) == 0, "tod must be 8-byte aligned");
   cudaStream_t s = S(stream);
   const int C = p->n_chunks;
   std::vector<double> taus(C);
@@ -1265,23 +1438,23 @@ __global__ void k_chi2_modes(const ChunkDesc* __restrict__ desc, int n_chunks, i
     int lo = 0, hi = n_chunks - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (desc[mid].spec + mid <= i) lo = mid; else hi = mid - 1;
+      if (desc[mid].nat <= i) lo = mid; else hi = mid - 1;
     }
     const ChunkDesc d = desc[lo];
-    const int k = (int)(i - (d.spec + lo));
+    const int k = (int)(i - d.nat);
     const float2 X = reinterpret_cast<const float2*>(io)[i];
     double dre, dim = 0.0, nb;
-    if (k == 0) { dre = dtab[d.spec].x; nb = nbar[d.spec]; }
-    else if (k == d.M) { dre = dtab[d.spec].y; nb = nyq[lo]; }
+    if (k == 0 && !d.cplx) { dre = dtab[d.spec].x; nb = nbar[d.spec]; }
+    else if (k == d.M && !d.cplx) { dre = dtab[d.spec].y; nb = nyq[lo]; }
     else {
-      const int64_t slot = d.spec + (int64_t)(k & (d.M1 - 1)) * d.M2 + k / d.M1;
+      const int64_t slot = d.spec + (int64_t)(k % d.M1) * d.M2 + k / d.M1;
       const float2 D = dtab[slot];
       dre = D.x; dim = D.y; nb = nbar[slot];
     }
     const double er = dre - X.x, ei = dim - X.y;
     const double v = (er * er + ei * ei) / ((nb + lambda * d.tau) * d.n);
     reinterpret_cast<double*>(io)[i] = v;
-    w += (k == 0 || k == d.M) ? v : 2.0 * v;
+    w += (k == 0 || 2 * k == d.n) ? v : 2.0 * v;
   }
   if (chi2 == nullptr) return;
   for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
@@ -1298,6 +1471,7 @@ __global__ void k_chi2_modes(const ChunkDesc* __restrict__ desc, int n_chunks, i
 extern "C" mm_status mm_chi2_modes(mm_plan p, const double* map, double lambda, double* chi2_dev,
                                    double* modes, void* stream) {
   MM_ARG(p != nullptr && map != nullptr && modes != nullptr, "NULL argument");
+  MM_ARG(((uintptr_t)modes & 7) == 0, "modes must be 8-byte aligned");
   MM_ARG(lambda >= 1.0 && isfinite(lambda), "lambda must be finite and >= 1");
   if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
   cudaStream_t s = S(stream);
@@ -1307,7 +1481,8 @@ extern "C" mm_status mm_chi2_modes(mm_plan p, const double* map, double lambda, 
   // the spectrum of P m, natural order, into the caller's buffer (8 bytes per bin either way)
   RowArgs a{kRowNatural, 1.0, nullptr, reinterpret_cast<float2*>(modes)};
   FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s)));
-  const int64_t n_bins = p->spec_total + p->n_chunks;
+  const ChunkDesc& last = p->h_desc[p->n_chunks - 1];
+  const int64_t n_bins = last.nat + last.n / 2 + 1;
   int grid = 0;
   MM_CUDA(persistent_grid(k_chi2_modes, 256, 0, (int)std::min<int64_t>(blocks_for(n_bins, 256), 1 << 20), &grid));
   k_chi2_modes<<<grid, 256, 0, s>>>(
@@ -1342,6 +1517,8 @@ extern "C" mm_status mm_apply_pointing_T(mm_plan p, const float* tod, double* ac
 
 extern "C" mm_status mm_rfft(mm_plan p, const float* tod, float* spec_out, void* stream) {
   MM_ARG(p != nullptr && tod != nullptr && spec_out != nullptr, "NULL argument");
+  MM_ARG(((uintptr_t)tod & 7) == 0 && ((uintptr_t)spec_out & 7) == 0,
+         "tod and spec_out must be 8-byte aligned");
   cudaStream_t s = S(stream);
   RowArgs a{kRowNatural, 1.0, nullptr, reinterpret_cast<float2*>(spec_out)};
   FOR_BATCHES(L_(launch_col_forward(p, B, kSrcTod, tod, s)); L_(launch_row(p, B, a, s)));

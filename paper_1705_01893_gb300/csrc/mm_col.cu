@@ -93,6 +93,7 @@ cudaError_t launch_tile_pointing(const mm_plan_s* p, cudaStream_t st) {
   const int wb = p->wdtype == MM_W_F16 ? 2 : 4;
   for (int c = 0; c < p->n_chunks; ++c) {
     const ChunkDesc& d = p->h_desc[c];
+    if (p->groups[d.grp].general) continue;   // the general path reads the caller's order
     const int64_t n = d.n;
     k_tile_pointing<kColCB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
         p->pix, p->cosw, p->sinw, wb, d.off, d.M1, d.M2, p->tpix, p->tcos, p->tsin);
@@ -171,6 +172,10 @@ cudaError_t launch_col_forward(const mm_plan_s* p, const Batch& b, int src, cons
 
 cudaError_t launch_col_forward_ex(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                   const void* map4, float2* ybuf, cudaStream_t st) {
+  if (b.group < 0) {
+    if (map4 || ybuf) return cudaErrorInvalidValue;
+    return launch_gen_col_forward(p, b, src, tod, st);
+  }
   const Group& g = p->groups[b.group];
   switch (g.M1) {
     case 16: return col_forward_m1<16>(p, b, src, tod, map4, ybuf, st);
@@ -185,6 +190,7 @@ cudaError_t launch_col_forward_ex(const mm_plan_s* p, const Batch& b, int src, c
 }
 
 cudaError_t launch_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st) {
+  if (b.group < 0) return launch_gen_col_inverse(p, b, st);
   const Group& g = p->groups[b.group];
   switch (g.M1) {
     case 16: return col_inverse_m1<16>(p, b, st);

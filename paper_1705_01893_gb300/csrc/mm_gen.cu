@@ -1,0 +1,556 @@
+// General-length chunks: the three FFT stages of the messenger step (kernels A, B and C of
+// the power-of-two path) for chunk lengths whose prime factors are 2, 3 and 5, with the
+// radix sequence chosen at run time, so that chunks of many different lengths run in ONE
+// persistent launch per stage.  Same four-step decomposition (M = M1 * M2, column DFTs of
+// length M1, twiddle w_M^{k1 j2}, row DFTs of length M2), same row layout of the
+// intermediate (slot k1 M2 + k2 holds frequency k1 + M1 k2) and the same scale
+// conventions, so every mode of the row stage (messenger filter of Sec. 2.1, chi^2 of
+// Eq. 3 per Fourier mode, PCG operator, spectra) is available for these chunks too.
+//
+// Even n: complex FFT of M = n/2 points over z_j = x_2j + i x_2j+1 with the real-to-complex
+// split in the row stage (rows k1 and M1 - k1 of one chunk in one CTA).  Odd n: complex FFT
+// of M = n points over z_j = x_j; every frequency is filtered on its own and the inverse
+// keeps the real part.
+//
+// Each Stockham pass of radix R over a length-L sequence (Ns = product of the radices of
+// the earlier passes) maps butterfly i, k = i mod Ns, to
+//   v_r = src[i + r L/R] * w_{Ns R}^{r k},  v = DFT_R(v),  dst[(i - k) R + k + r Ns] = v_r,
+// which leaves the result in natural order after the last pass.  The passes ping-pong
+// between two shared-memory tiles.
+#include "mm_colcommon.cuh"
+
+namespace mm {
+
+struct GenParams {
+  const ChunkDesc* __restrict__ desc;
+  const Group* __restrict__ groups;
+  const int* __restrict__ chunks;       // general chunk list
+  const int64_t* __restrict__ prefix;   // column tiles (A, C) or row jobs (B) per chunk
+  const int64_t* __restrict__ yoff;     // intermediate offset per chunk
+  int first, count;                     // the batch: general chunks [first, first + count)
+  int64_t base, n_items, base_y;
+  int nb;                               // columns per tile (A, C)
+  const int32_t* __restrict__ pix;      // caller's pointing, natural order
+  const void* cosw;
+  const void* sinw;
+  int half_w;
+  const void* map4;
+  const float* tod;
+  float2* ybuf;
+  double* acc;
+  float2* dtab;
+  const float* __restrict__ nbar;
+  const float* __restrict__ nyq;
+  RowArgs a;
+};
+
+// Chunk i (an index into the general list) whose item range holds global item g.
+__device__ __forceinline__ int gen_find(const GenParams& q, int64_t g) {
+  int lo = q.first, hi = q.first + q.count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(q.prefix + mid) <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ----------------------------------------------------------------- Stockham passes
+// Column tiles: element (j, c) of the tile's NB interleaved sequences at j * NB + c.
+template <int R, int DIR>
+__device__ __forceinline__ void gpass_cols(const float2* src, float2* dst, int L, int Ns, int NB,
+                                           int lnb, const float2* __restrict__ tw, int T) {
+  const int nb = L / R, mul = L / (Ns * R);
+  for (int b = threadIdx.x; b < nb * NB; b += T) {
+    const int c = b & (NB - 1), i = b >> lnb;
+    const int k = i % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(i + r * nb) * NB + c];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = __ldg(tw + r * k * mul);
+        v[r] = DIR < 0 ? cmul(v[r], w) : cmulc(v[r], w);
+      }
+    }
+    dftR<R, DIR>(v);
+    const int o = (i - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(o + r * Ns) * NB + c] = v[r];
+  }
+}
+
+// Row jobs: nseq (1 or 2) contiguous sequences of length L at 0 and L.
+template <int R, int DIR>
+__device__ __forceinline__ void gpass_rows(const float2* src, float2* dst, int L, int Ns, int nseq,
+                                           const float2* __restrict__ tw, int T) {
+  const int nb = L / R, mul = L / (Ns * R);
+  for (int b = threadIdx.x; b < nb * nseq; b += T) {
+    const int sq = b >= nb, i = b - sq * nb;
+    const int base = sq * L;
+    const int k = i % Ns;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[base + i + r * nb];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = __ldg(tw + r * k * mul);
+        v[r] = DIR < 0 ? cmul(v[r], w) : cmulc(v[r], w);
+      }
+    }
+    dftR<R, DIR>(v);
+    const int o = base + (i - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[o + r * Ns] = v[r];
+  }
+}
+
+// All passes of one DFT; returns the tile holding the result (a or b).
+template <bool COLS, int DIR>
+__device__ float2* gen_dft(float2* a, float2* b, int L, int nr, const int8_t* rad,
+                           const float2* tw, int NB, int lnb, int nseq, int T) {
+  int Ns = 1;
+  for (int p = 0; p < nr; ++p) {
+    const int R = rad[p];
+    if constexpr (COLS) {
+      switch (R) {
+        case 2: gpass_cols<2, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+        case 3: gpass_cols<3, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+        case 4: gpass_cols<4, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+        case 5: gpass_cols<5, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+        default: gpass_cols<8, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+      }
+    } else {
+      switch (R) {
+        case 2: gpass_rows<2, DIR>(a, b, L, Ns, nseq, tw, T); break;
+        case 3: gpass_rows<3, DIR>(a, b, L, Ns, nseq, tw, T); break;
+        case 4: gpass_rows<4, DIR>(a, b, L, Ns, nseq, tw, T); break;
+        case 5: gpass_rows<5, DIR>(a, b, L, Ns, nseq, tw, T); break;
+        default: gpass_rows<8, DIR>(a, b, L, Ns, nseq, tw, T); break;
+      }
+    }
+    __syncthreads();
+    float2* t = a; a = b; b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+__device__ __forceinline__ float2 gen_tw_big(const Group& g, int e) {
+  return cmul(__ldg(&g.tw_hi[e >> g.log_lo]), __ldg(&g.tw_lo[e & ((1 << g.log_lo) - 1)]));
+}
+
+// (P m)_s for one sample (Eq. 1); weights from the caller's natural-order arrays.
+template <int NC>
+__device__ __forceinline__ float gen_pm(const GenParams& q, int64_t s) {
+  const int p = __ldg(q.pix + s);
+  if (p < 0) return 0.f;
+  if constexpr (NC == 1) {
+    return __ldg(reinterpret_cast<const float*>(q.map4) + p);
+  } else {
+    float cw, sw;
+    if (q.half_w) {
+      cw = __half2float(static_cast<const __half*>(q.cosw)[s]);
+      sw = __half2float(static_cast<const __half*>(q.sinw)[s]);
+    } else {
+      cw = __ldg(static_cast<const float*>(q.cosw) + s);
+      sw = __ldg(static_cast<const float*>(q.sinw) + s);
+    }
+    const float4 m = __ldg(reinterpret_cast<const float4*>(q.map4) + p);
+    return fmaf(sw, m.z, fmaf(cw, m.y, m.x));
+  }
+}
+
+// ------------------------------------------------------------ kernel A: columns forward
+template <int NC, int SRC>
+__global__ void __launch_bounds__(512) k_gen_col_forward(GenParams q) {
+  extern __shared__ float2 gsm[];
+  const int T = blockDim.x, NB = q.nb, lnb = NB == 16 ? 4 : 3;
+  for (int64_t t = blockIdx.x; t < q.n_items; t += gridDim.x) {
+    const int64_t g = q.base + t;
+    const int i = gen_find(q, g);
+    const ChunkDesc d = q.desc[__ldg(q.chunks + i)];
+    const Group& G = q.groups[d.grp];
+    const int M1 = d.M1, M2 = d.M2;
+    const int j2_0 = (int)(g - __ldg(q.prefix + i)) * NB;
+    const int width = min(NB, M2 - j2_0);
+    float2* a = gsm;
+    float2* b = gsm + M1 * NB;
+    for (int e = threadIdx.x; e < M1 * NB; e += T) {
+      const int j1 = e >> lnb, c = e & (NB - 1);
+      float2 z = make_float2(0.f, 0.f);
+      if (c < width) {
+        const int64_t j = (int64_t)j1 * M2 + j2_0 + c;
+        if (d.cplx) {
+          z.x = SRC == kSrcTod ? __ldg(q.tod + d.off + j) : gen_pm<NC>(q, d.off + j);
+        } else if constexpr (SRC == kSrcTod) {
+          z = make_float2(__ldg(q.tod + d.off + 2 * j), __ldg(q.tod + d.off + 2 * j + 1));
+        } else {
+          z = make_float2(gen_pm<NC>(q, d.off + 2 * j), gen_pm<NC>(q, d.off + 2 * j + 1));
+        }
+      }
+      a[e] = z;
+    }
+    __syncthreads();
+    const float2* r = gen_dft<true, -1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, 1, T);
+    float2* y = q.ybuf + (__ldg(q.yoff + i) - q.base_y);
+    for (int e = threadIdx.x; e < M1 * NB; e += T) {
+      const int k1 = e >> lnb, c = e & (NB - 1);
+      if (c < width) {
+        const int j2 = j2_0 + c;
+        y[(int64_t)k1 * M2 + j2] = cmul(r[e], gen_tw_big(G, k1 * j2));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------- kernel C: columns inverse + P^T
+// Warp-segmented binning: the lanes of a warp hold 32 consecutive samples of the tile (in
+// sample order); runs of lanes on the same pixel are summed by a segmented suffix scan and
+// the first lane of each run issues one FP64 add per component.
+template <int NC>
+__device__ __forceinline__ void gen_scatter(const GenParams& q, const ChunkDesc& d, int j2_0,
+                                            int width, const float* smf, int NB, int lnb, int T) {
+  const int rw = d.cplx ? NB : 2 * NB;          // samples per tile row
+  const int lrw = d.cplx ? lnb : lnb + 1;
+  const int valid_u = d.cplx ? width : 2 * width;
+  const int total = d.M1 * rw;
+  const int lane = threadIdx.x & 31;
+  for (int base = threadIdx.x - lane; base < total; base += T) {
+    const int e = base + lane;
+    int p = -1;
+    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+    if (e < total) {
+      const int j1 = e >> lrw, u = e & (rw - 1);
+      if (u < valid_u) {
+        const int64_t s = d.off + (d.cplx ? (int64_t)j1 * d.M2 + j2_0 + u
+                                          : 2 * ((int64_t)j1 * d.M2 + j2_0) + u);
+        p = __ldg(q.pix + s);
+        const float t = d.cplx ? smf[2 * e] : smf[e];
+        v0 = t;
+        if constexpr (NC == 3) {
+          float cw, sw;
+          if (q.half_w) {
+            cw = __half2float(static_cast<const __half*>(q.cosw)[s]);
+            sw = __half2float(static_cast<const __half*>(q.sinw)[s]);
+          } else {
+            cw = __ldg(static_cast<const float*>(q.cosw) + s);
+            sw = __ldg(static_cast<const float*>(q.sinw) + s);
+          }
+          v1 = t * cw;
+          v2 = t * sw;
+        }
+      }
+    }
+    const int pp = __shfl_up_sync(0xffffffffu, p, 1);
+    const bool head = lane == 0 || p != pp;
+    const unsigned hm = __ballot_sync(0xffffffffu, head);
+    const int seg = __popc(hm & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float a0 = __shfl_down_sync(0xffffffffu, v0, o);
+      const float a1 = __shfl_down_sync(0xffffffffu, v1, o);
+      const float a2 = __shfl_down_sync(0xffffffffu, v2, o);
+      const int so = __shfl_down_sync(0xffffffffu, seg, o);
+      if (lane + o < 32 && so == seg) { v0 += a0; v1 += a1; v2 += a2; }
+    }
+    if (head) emit_run<NC>(q.acc, p, v0, v1, v2);
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(512) k_gen_col_inverse(GenParams q) {
+  extern __shared__ float2 gsm[];
+  const int T = blockDim.x, NB = q.nb, lnb = NB == 16 ? 4 : 3;
+  for (int64_t t = blockIdx.x; t < q.n_items; t += gridDim.x) {
+    const int64_t g = q.base + t;
+    const int i = gen_find(q, g);
+    const ChunkDesc d = q.desc[__ldg(q.chunks + i)];
+    const Group& G = q.groups[d.grp];
+    const int M1 = d.M1, M2 = d.M2;
+    const int j2_0 = (int)(g - __ldg(q.prefix + i)) * NB;
+    const int width = min(NB, M2 - j2_0);
+    float2* a = gsm;
+    float2* b = gsm + M1 * NB;
+    const float2* y = q.ybuf + (__ldg(q.yoff + i) - q.base_y);
+    for (int e = threadIdx.x; e < M1 * NB; e += T) {
+      const int k1 = e >> lnb, c = e & (NB - 1);
+      a[e] = c < width ? y[(int64_t)k1 * M2 + j2_0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const float2* r = gen_dft<true, +1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, 1, T);
+    gen_scatter<NC>(q, d, j2_0, width, reinterpret_cast<const float*>(r), NB, lnb, T);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------- kernel B: rows, filter, inverse rows
+__global__ void __launch_bounds__(512) k_gen_row(GenParams q) {
+  extern __shared__ float2 gsm[];
+  __shared__ double red[32];
+  const int T = blockDim.x;
+  const int mode = q.a.mode;
+  const bool fwd = mode != kRowPcgRhs;
+  const bool inv = mode == kRowMessenger || mode == kRowPcgApply || mode == kRowPcgRhs;
+  const bool spec_out = mode == kRowSpectrum || mode == kRowNatural;
+  const bool load_d = !spec_out && mode != kRowPcgApply;
+  double lambda = q.a.lambda;
+  double* chi2 = q.a.chi2;
+  if (q.a.lam_table) {          // graph mode: schedule and chi^2 slot from device memory
+    const int it = *q.a.iter;
+    lambda = q.a.lam_table[it];
+    chi2 = q.a.chi2_base[0] ? q.a.chi2_base[0] + it : nullptr;
+  }
+  const bool want_x2 = chi2 != nullptr &&
+                       (mode == kRowMessenger || mode == kRowChi2 || mode == kRowPcgRhs);
+  for (int64_t job = blockIdx.x; job < q.n_items; job += gridDim.x) {
+    const int64_t g = q.base + job;
+    const int i = gen_find(q, g);
+    const int c = __ldg(q.chunks + i);
+    const ChunkDesc d = q.desc[c];
+    const Group& G = q.groups[d.grp];
+    const int M1 = d.M1, M2 = d.M2, M = d.M;
+    const int rA = (int)(g - __ldg(q.prefix + i));
+    const int rB = rA == 0 ? 0 : M1 - rA;
+    const bool self = rA == rB;
+    const int nseq = self ? 1 : 2;
+    float2* y = q.ybuf + (__ldg(q.yoff + i) - q.base_y);
+    float2* a = gsm;
+    float2* b = gsm + 2 * M2;
+    float2* z = a;
+    if (fwd) {
+      for (int e = threadIdx.x; e < nseq * M2; e += T)
+        a[e] = y[(int64_t)(e < M2 ? rA : rB) * M2 + (e < M2 ? e : e - M2)];
+      __syncthreads();
+      z = gen_dft<false, -1>(a, b, M2, G.nr2, G.rad2, G.tw_row, 0, 0, nseq, T);
+    }
+    float2* other = z == a ? b : a;
+
+    const float tau = (float)d.tau;
+    const float inv_n = 1.0f / (float)d.n;
+    float lt = 0.f;
+    bool lam_inf = false;
+    if (mode == kRowMessenger) {
+      lam_inf = isinf(lambda);
+      lt = lam_inf ? 0.f : (float)(lambda * d.tau);
+    }
+    const float cn = mode == kRowChi2 ? (float)(lambda * d.tau) : tau;
+    const float sc = mode == kRowMessenger ? inv_n / tau : inv_n;
+    const float2* dt = q.dtab + d.spec;
+    const float* nb = q.nbar + d.spec;
+    auto filt = [&](float2 X, float2 D, float nbv) -> float2 {
+      if (mode == kRowMessenger) {
+        if (lam_inf) return cscale(D, sc);
+        const float r = __fdividef(sc, lt + nbv);
+        return make_float2((lt * D.x + nbv * X.x) * r, (lt * D.y + nbv * X.y) * r);
+      }
+      if (mode == kRowPcgApply) return cscale(X, __fdividef(sc, nbv + tau));
+      return cscale(D, __fdividef(sc, nbv + tau));  // kRowPcgRhs
+    };
+    float x2 = 0.f;
+
+    if (d.cplx) {
+      // every frequency on its own: k = r + M1 p for element p of row r
+      for (int e = threadIdx.x; e < nseq * M2; e += T) {
+        const int r = e < M2 ? rA : rB, p = e < M2 ? e : e - M2;
+        const int slot = r * M2 + p;
+        const int k = r + M1 * p;
+        const float2 X = fwd ? z[e] : make_float2(0.f, 0.f);
+        if (mode == kRowSpectrum) { q.dtab[d.spec + slot] = X; continue; }
+        if (mode == kRowNatural) {
+          if (2 * k <= d.n) q.a.natural[d.nat + k] = X;
+          continue;
+        }
+        const float2 D = load_d ? __ldcs(dt + slot) : make_float2(0.f, 0.f);
+        const float nbv = __ldcs(nb + slot);
+        if (want_x2) {
+          const float2 er = csub(D, X);
+          x2 += __fdividef(er.x * er.x + er.y * er.y, nbv + cn);
+        }
+        if (inv) z[e] = filt(X, D, nbv);
+      }
+    } else {
+      // pairs (k, M - k): element p of row rA with partner qi of row rB (or of row rA)
+      const float2 wa = __ldg(&G.tw_pack_a[rA]);
+      for (int p = threadIdx.x; p < M2; p += T) {
+        int qs = 1, qi = M2 - 1 - p;
+        if (self) {
+          qs = 0;
+          qi = rA == 0 ? (p == 0 ? 0 : M2 - p) : M2 - 1 - p;
+          if (p > qi) continue;
+        }
+        const int sk = rA * M2 + p, sp = (qs ? rB : rA) * M2 + qi;
+        const int ek = p, ep = qs * M2 + qi;             // positions in the tile
+        const float2 Zk = fwd ? z[ek] : make_float2(0.f, 0.f);
+        const float2 Zp = fwd ? z[ep] : make_float2(0.f, 0.f);
+        if (rA == 0 && p == 0) {
+          const float X0 = Zk.x + Zk.y, XM = Zk.x - Zk.y;
+          if (mode == kRowSpectrum) { q.dtab[d.spec] = make_float2(X0, XM); continue; }
+          if (mode == kRowNatural) {
+            q.a.natural[d.nat] = make_float2(X0, 0.f);
+            q.a.natural[d.nat + M] = make_float2(XM, 0.f);
+            continue;
+          }
+          const float2 D = load_d ? dt[0] : make_float2(0.f, 0.f);
+          const float n0 = nb[0], nM = __ldg(q.nyq + c);
+          if (want_x2) {
+            const float e0 = D.x - X0, eM = D.y - XM;
+            x2 += __fdividef(e0 * e0, n0 + cn) + __fdividef(eM * eM, nM + cn);
+          }
+          if (!inv) continue;
+          const float Y0 = filt(make_float2(X0, 0.f), make_float2(D.x, 0.f), n0).x;
+          const float YM = filt(make_float2(XM, 0.f), make_float2(D.y, 0.f), nM).x;
+          z[0] = make_float2(Y0 + YM, Y0 - YM);
+          continue;
+        }
+        const float2 w = cmul(wa, __ldg(&G.tw_pack_b[p]));   // w_{2M}^k, k = rA + M1 p
+        const float2 E = cscale(cadd(Zk, cconj(Zp)), 0.5f);
+        const float2 O = cscale(mul_i<-1>(csub(Zk, cconj(Zp))), 0.5f);
+        const float2 wO = cmul(w, O);
+        const float2 Xk = cadd(E, wO);
+        const float2 Xp = cconj(csub(E, wO));
+        const bool same = qs == 0 && qi == p;           // k == M - k
+        if (mode == kRowSpectrum) {
+          q.dtab[d.spec + sk] = Xk;
+          if (!same) q.dtab[d.spec + sp] = Xp;
+          continue;
+        }
+        if (mode == kRowNatural) {
+          const int k = rA + M1 * p;
+          q.a.natural[d.nat + k] = Xk;
+          q.a.natural[d.nat + M - k] = Xp;
+          continue;
+        }
+        const float2 Dk = load_d ? __ldcs(dt + sk) : make_float2(0.f, 0.f);
+        const float2 Dp = load_d ? __ldcs(dt + sp) : make_float2(0.f, 0.f);
+        const float nk = __ldcs(nb + sk), np = __ldcs(nb + sp);
+        if (want_x2) {
+          const float2 e1 = csub(Dk, Xk), e2 = csub(Dp, Xp);
+          float tt = __fdividef(e1.x * e1.x + e1.y * e1.y, nk + cn);
+          if (!same) tt += __fdividef(e2.x * e2.x + e2.y * e2.y, np + cn);
+          x2 += 2.f * tt;
+        }
+        if (!inv) continue;
+        const float2 Yk = filt(Xk, Dk, nk);
+        const float2 Yp = filt(Xp, Dp, np);
+        // Z'_k = (Y_k + conj Y_p) + i conj(w) (Y_k - conj Y_p)
+        // Z'_p = (Y_p + conj Y_k) - i w (Y_p - conj Y_k)
+        const float2 Zk2 = cadd(cadd(Yk, cconj(Yp)), mul_i<+1>(cmulc(csub(Yk, cconj(Yp)), w)));
+        z[ek] = Zk2;
+        if (!same) {
+          const float2 Zp2 = csub(cadd(Yp, cconj(Yk)), mul_i<+1>(cmul(w, csub(Yp, cconj(Yk)))));
+          z[ep] = Zp2;
+        }
+      }
+    }
+    if (want_x2) {
+      // block reduction: FP32 within warps, FP64 across warps and CTAs
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x2 += __shfl_down_sync(0xffffffffu, x2, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x2;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < T / 32; ++w) s += red[w];
+        atomicAdd(chi2, s / (double)d.n);
+      }
+    }
+    if (inv) {
+      __syncthreads();
+      const float2* r = gen_dft<false, +1>(z, other, M2, G.nr2, G.rad2, G.tw_row, 0, 0, nseq, T);
+      for (int e = threadIdx.x; e < nseq * M2; e += T) {
+        const int row = e < M2 ? rA : rB, p = e < M2 ? e : e - M2;
+        y[(int64_t)row * M2 + p] = cmulc(r[e], gen_tw_big(G, row * p));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------ launchers
+static GenParams gen_params(const mm_plan_s* p, const Batch& b, const int64_t* d_prefix,
+                            const int64_t* h_prefix) {
+  GenParams q{};
+  q.desc = p->d_desc;
+  q.groups = p->d_groups;
+  q.chunks = p->gen_chunks;
+  q.prefix = d_prefix;
+  q.yoff = p->gen_yoff;
+  q.first = b.first;
+  q.count = b.count;
+  q.base = h_prefix[b.first];
+  q.n_items = h_prefix[b.first + b.count] - q.base;
+  q.base_y = p->h_gen_yoff[b.first];
+  q.pix = p->pix;
+  q.cosw = p->cosw;
+  q.sinw = p->sinw;
+  q.half_w = p->wdtype == MM_W_F16;
+  q.map4 = p->map4;
+  q.ybuf = p->ybuf;
+  q.acc = p->acc;
+  q.dtab = p->dtab;
+  q.nbar = p->nbar;
+  q.nyq = p->nyq;
+  return q;
+}
+
+// Largest M1 / M2 among the batch's chunks (shared-memory size of the launch).
+static void gen_extent(const mm_plan_s* p, const Batch& b, int* m1, int* m2) {
+  *m1 = 1; *m2 = 1;
+  for (int i = b.first; i < b.first + b.count; ++i) {
+    const ChunkDesc& d = p->h_desc[p->h_gen_chunks[i]];
+    if (d.M1 > *m1) *m1 = d.M1;
+    if (d.M2 > *m2) *m2 = d.M2;
+  }
+}
+
+template <typename K>
+static cudaError_t gen_launch(K kernel, int threads, size_t smem, int64_t items,
+                              const GenParams& q, cudaStream_t st) {
+  if (items <= 0) return cudaSuccess;
+  int grid = 0;
+  const int work = items > (1 << 30) ? (1 << 30) : (int)items;
+  cudaError_t e = persistent_grid(kernel, threads, smem, work, &grid);
+  if (e != cudaSuccess) return e;
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  kernel<<<grid, threads, smem, st>>>(q);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_col_forward(const mm_plan_s* p, const Batch& b, int src, const float* tod,
+                                   cudaStream_t st) {
+  GenParams q = gen_params(p, b, p->gen_ctile, p->h_gen_ctile);
+  q.nb = p->gen_tune.col_nb;
+  q.tod = tod;
+  int m1, m2;
+  gen_extent(p, b, &m1, &m2);
+  const size_t smem = 2 * sizeof(float2) * (size_t)m1 * q.nb;
+  const int T = p->gen_tune.col_threads;
+  if (src == kSrcTod) return gen_launch(k_gen_col_forward<1, kSrcTod>, T, smem, q.n_items, q, st);
+  if (p->ncomp == 3) return gen_launch(k_gen_col_forward<3, kSrcGather>, T, smem, q.n_items, q, st);
+  return gen_launch(k_gen_col_forward<1, kSrcGather>, T, smem, q.n_items, q, st);
+}
+
+cudaError_t launch_gen_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st) {
+  GenParams q = gen_params(p, b, p->gen_ctile, p->h_gen_ctile);
+  q.nb = p->gen_tune.col_nb;
+  int m1, m2;
+  gen_extent(p, b, &m1, &m2);
+  const size_t smem = 2 * sizeof(float2) * (size_t)m1 * q.nb;
+  const int T = p->gen_tune.col_threads;
+  if (p->ncomp == 3) return gen_launch(k_gen_col_inverse<3>, T, smem, q.n_items, q, st);
+  return gen_launch(k_gen_col_inverse<1>, T, smem, q.n_items, q, st);
+}
+
+cudaError_t launch_gen_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
+  GenParams q = gen_params(p, b, p->gen_rjob, p->h_gen_rjob);
+  q.a = a;
+  int m1, m2;
+  gen_extent(p, b, &m1, &m2);
+  const size_t smem = 4 * sizeof(float2) * (size_t)m2;
+  return gen_launch(k_gen_row, p->gen_tune.row_threads, smem, q.n_items, q, st);
+}
+
+}  // namespace mm

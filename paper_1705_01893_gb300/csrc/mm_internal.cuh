@@ -17,36 +17,60 @@ namespace mm {
 // length M = M1 * M2 over z_j = x_{2j} + i x_{2j+1}, done as a four-step transform:
 // column FFTs of length M1 (kernel A / C), twiddles w_M^{k1 j2}, row FFTs of length M2
 // (kernel B).  Spectra live in "row layout": slot k1*M2 + k2 holds frequency k1 + M1*k2.
+// A chunk of odd length n ("complex" chunk, general path only) is transformed as a complex
+// FFT of M = n points over z_j = x_j + 0i; its row layout then holds all n frequencies.
 struct ChunkDesc {
   int64_t off;       // first sample of the chunk
   int64_t spec;      // first slot of the chunk in the spectrum-sized buffers (M per chunk)
+  int64_t nat;       // first bin of the chunk in natural-order rfft arrays (n/2 + 1 per chunk)
   int n, M, M1, M2;
+  int grp;           // FFT group
+  int cplx;          // 1: odd n, complex transform of M = n points
   double tau;        // messenger variance tau_c (Sec. 4.2)
 };
 
 // Chunks of the same length share FFT shapes and twiddle tables and run in one launch.
+// Power-of-two lengths use the compile-time kernels; other 5-smooth lengths ("general")
+// use runtime mixed-radix Stockham passes with the radix sequences below.
+constexpr int kMaxRadices = 16;
 struct Group {
   int M, M1, M2, log_lo;   // w_M^e = tw_hi[e >> log_lo] * tw_lo[e & (2^log_lo - 1)]
   int n_chunks;
   int batch;               // chunks per batch
+  int general, cplx;       // general path; odd length (complex transform)
+  int nr1, nr2;            // general: radix sequences of the M1 and M2 DFTs
+  int8_t rad1[kMaxRadices], rad2[kMaxRadices];
   int* chunks;             // device: chunk indices of this group
-  float2* tw_col;          // per-pass twiddles of the length-M1 DFT (see tw_offset)
-  float2* tw_row;          // per-pass twiddles of the length-M2 DFT
+  float2* tw_col;          // per-pass twiddles of the length-M1 DFT (see tw_offset);
+                           // general: [M1] exp(-2 pi i m / M1)
+  float2* tw_row;          // per-pass twiddles of the length-M2 DFT; general: [M2]
   float2* tw_lo;           // [2^log_lo]          exp(-2 pi i m / M)
-  float2* tw_hi;           // [M >> log_lo]        exp(-2 pi i m 2^log_lo / M)
+  float2* tw_hi;           // [M >> log_lo (+1)]   exp(-2 pi i m 2^log_lo / M)
   float2* tw_pack_a;       // [M1]  exp(-2 pi i m / (2M))     (real-pack twiddle, k1 part)
   float2* tw_pack_b;       // [M2]  exp(-2 pi i m M1 / (2M))  (real-pack twiddle, k2 part)
 };
 
-constexpr int kMaxGroups = 16;
+constexpr int kMaxGroups = 128;
+
+// Column / row limits of the general path (shared memory of one CTA: two ping-pong tiles).
+constexpr int kGenMaxM1 = 512;
+constexpr int kGenMaxM2 = 4096;
 
 // A batch: `count` consecutive chunks of one group whose four-step intermediates share the
 // ybuf slot.  Batches are sized so the slot (default 32 MB) stays resident in L2 between
 // the column and row passes; they run one after another on the caller's stream.
 struct Batch {
-  int group;
-  int first;          // index into the group's chunk list
+  int group;          // -1: a batch of the general path (chunks of any general length)
+  int first;          // index into the group's chunk list (general: into the general list)
   int count;
+};
+
+// Schedule of the general path's persistent kernels: tile width, threads (picked per plan
+// by measurement, see mm_autotune).
+struct GenTune {
+  int col_nb;         // columns per column tile: 8 or 16
+  int col_threads;    // 256 or 512
+  int row_threads;    // 256 or 512
 };
 
 }  // namespace mm
@@ -94,6 +118,19 @@ struct mm_plan_s {
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;
+  // general path: chunk list in plan order and per-chunk prefix sums over it (column tiles,
+  // row jobs, intermediate elements), device and host copies; device copy of the groups
+  int n_gen;
+  int* gen_chunks;
+  int64_t* gen_ctile;
+  int64_t* gen_rjob;
+  int64_t* gen_yoff;
+  int64_t* h_gen_ctile;
+  int64_t* h_gen_rjob;
+  int64_t* h_gen_yoff;
+  int* h_gen_chunks;
+  mm::Group* d_groups;
+  mm::GenTune gen_tune;
   int32_t* tpix;    // pointing copied into column-tile order (see k_tile_pointing)
   void* tcos;
   void* tsin;
@@ -204,10 +241,44 @@ __device__ __forceinline__ void dft16(float2* v) {
     for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = t[k2 + 4 * k1];
 }
 
+// DFT of 3 points: y_{1,2} = v0 - (v1 + v2)/2 +- DIR i (sqrt 3 / 2)(v1 - v2).
+template <int DIR>
+__device__ __forceinline__ void dft3(float2* v) {
+  constexpr float h3 = 0.86602540378443864676f;   // sin(2 pi / 3)
+  const float2 t1 = cadd(v[1], v[2]);
+  const float2 t2 = cscale(mul_i<DIR>(csub(v[1], v[2])), h3);
+  const float2 m = make_float2(v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y);
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(m, t2);
+  v[2] = csub(m, t2);
+}
+
+// DFT of 5 points from the sums and differences of the symmetric pairs (1, 4) and (2, 3):
+// y_{1,4} = v0 + c1 a + c2 b +- DIR i (s1 p + s2 q), y_{2,3} = v0 + c2 a + c1 b +- DIR i (s2 p - s1 q)
+// with a = v1 + v4, b = v2 + v3, p = v1 - v4, q = v2 - v3, c_j = cos(2 pi j / 5), s_j = sin(2 pi j / 5).
+template <int DIR>
+__device__ __forceinline__ void dft5(float2* v) {
+  constexpr float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;
+  constexpr float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;
+  const float2 a = cadd(v[1], v[4]), b = cadd(v[2], v[3]);
+  const float2 p = csub(v[1], v[4]), q = csub(v[2], v[3]);
+  const float2 r1 = make_float2(v[0].x + c1 * a.x + c2 * b.x, v[0].y + c1 * a.y + c2 * b.y);
+  const float2 r2 = make_float2(v[0].x + c2 * a.x + c1 * b.x, v[0].y + c2 * a.y + c1 * b.y);
+  const float2 i1 = mul_i<DIR>(make_float2(s1 * p.x + s2 * q.x, s1 * p.y + s2 * q.y));
+  const float2 i2 = mul_i<DIR>(make_float2(s2 * p.x - s1 * q.x, s2 * p.y - s1 * q.y));
+  v[0] = cadd(v[0], cadd(a, b));
+  v[1] = cadd(r1, i1);
+  v[4] = csub(r1, i1);
+  v[2] = cadd(r2, i2);
+  v[3] = csub(r2, i2);
+}
+
 template <int R, int DIR>
 __device__ __forceinline__ void dftR(float2* v) {
   if constexpr (R == 2) dft2<DIR>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<DIR>(v);
   else if constexpr (R == 4) dft4<DIR>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 5) dft5<DIR>(v);
   else if constexpr (R == 8) dft8<DIR>(v);
   else dft16<DIR>(v);
 }
@@ -404,6 +475,12 @@ cudaError_t launch_col_forward(const mm_plan_s* p, const Batch& b, int src, cons
 cudaError_t launch_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
 cudaError_t launch_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st);
 cudaError_t launch_tile_pointing(const mm_plan_s* p, cudaStream_t st);
+// General path (mm_gen.cu): the same three stages for a batch of general-length chunks,
+// one persistent launch each, with the same intermediate layout and scale conventions.
+cudaError_t launch_gen_col_forward(const mm_plan_s* p, const Batch& b, int src, const float* tod,
+                                   cudaStream_t st);
+cudaError_t launch_gen_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
+cudaError_t launch_gen_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st);
 // Forward column pass gathering from `map4` into `ybuf` (either NULL = the plan's own).
 cudaError_t launch_col_forward_ex(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                   const void* map4, float2* ybuf, cudaStream_t st);

@@ -259,8 +259,8 @@ static size_t plain_up(size_t x) { return (x + 255) & ~size_t(255); }
 
 extern "C" mm_status mm_plain_work_bytes(mm_plan p, size_t* bytes) {
   if (!p || !bytes) { mm_set_error("mm_plain_work_bytes: NULL argument"); return MM_ERR_ARG; }
-  if (p->n_groups != 1) {
-    mm_set_error("the plain FP64 step needs all chunks of one length");
+  if (p->n_groups != 1 || p->groups[0].general) {
+    mm_set_error("the plain FP64 step needs all chunks of one power-of-two length");
     return MM_ERR_UNSUPPORTED;
   }
   const int M = p->groups[0].M;

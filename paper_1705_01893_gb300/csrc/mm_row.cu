@@ -152,7 +152,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
         const float X0 = Zk.x + Zk.y, XM = Zk.x - Zk.y;
         if (mode == kRowSpectrum) { q.dtab[d.spec] = make_float2(X0, XM); continue; }
         if (mode == kRowNatural) {
-          float2* o = q.a.natural + d.spec + c;
+          float2* o = q.a.natural + d.nat;
           o[0] = make_float2(X0, 0.f);
           o[M] = make_float2(XM, 0.f);
           continue;
@@ -183,7 +183,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
         continue;
       }
       if (mode == kRowNatural) {
-        float2* o = q.a.natural + d.spec + c;
+        float2* o = q.a.natural + d.nat;
         const int k = rA + M1 * p;
         o[k] = Xk;
         o[M - k] = Xp;
@@ -287,6 +287,7 @@ static cudaError_t row_m2(const mm_plan_s* p, const Batch& b, const RowArgs& a,
 }
 
 cudaError_t launch_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
+  if (b.group < 0) return launch_gen_row(p, b, a, st);
   switch (p->groups[b.group].M2) {
     case 16: return row_m2<16>(p, b, a, st);
     case 32: return row_m2<32>(p, b, a, st);

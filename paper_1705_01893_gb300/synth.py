@@ -13,6 +13,10 @@ cross-linked rasters, polarised detectors at several angles, N(f) = s^2 (1 + (fk
 * ``config_iqu(...)``         W x W IQU map, D detectors of n samples each at 200 Hz,
   alternating horizontal / vertical sweeps (4 samples per pixel), detector angles
   0, 180/D, ... degrees plus a 0.5 Hz half-wave-plate rotation.
+* ``config_uneven(...)``      chunks of uneven 2-3-5-smooth lengths, each with its own
+  noise spectrum and raster angle, on one IQU map (1024^2, 64 chunks of 2^16..2^20).
+* ``config_crosslinked(...)`` 2048^2 IQU, 32 detectors x 2^24 samples on rasters at four
+  angles, FP16 weights.
 
 Noise draws use a circulant covariance per chunk: n = irfft(sqrt(N_k) * rfft(w)),
 w ~ N(0, 1), whose covariance is exactly F^-1 diag(N_k) F.
@@ -79,13 +83,51 @@ def raster_alternating(width: int, spp: int, n: int, phase: int) -> np.ndarray:
     """Sweeps of width*spp samples alternating horizontal / vertical, advancing one
     row / column every two sweeps, starting ``phase`` rows/columns in."""
     per = width * spp
-    nsweep = n // per
+    nsweep = -(-n // per)
     j = np.arange(per) // spp
     out = np.empty(nsweep * per, dtype=np.int64)
     for s in range(nsweep):
         line = (s // 2 + phase) % width
         out[s * per:(s + 1) * per] = line * width + j if s % 2 == 0 else j * width + line
     return out[:n].astype(np.int32)
+
+
+def raster_angled(width: int, spp: int, n: int, angle_rad: float, phase: int) -> np.ndarray:
+    """Back-and-forth sweeps across the map along direction (cos a, sin a) through its
+    centre, each sweep one pixel further along the cross direction (wrapping after the
+    map's extent, width (|cos a| + |sin a|), in that direction), spp samples per pixel of
+    path; coordinates in float64, nearest pixel floor(x) + width floor(y), samples outside
+    the map get -1."""
+    ca, sa = np.cos(angle_rad), np.sin(angle_rad)
+    span = int(np.ceil(width * (abs(ca) + abs(sa)) - 1e-9))
+    per = span * spp
+    s = np.arange(n) // per
+    j = np.arange(n) % per
+    xi = -0.5 * span + (j + 0.5) / spp
+    xi = np.where(s % 2 == 0, xi, -xi)
+    eta = -0.5 * span + ((s // 2 + phase) % span) + 0.5
+    x = 0.5 * width + xi * ca - eta * sa
+    y = 0.5 * width + xi * sa + eta * ca
+    inside = (x >= 0) & (x < width) & (y >= 0) & (y < width)
+    pix = np.floor(x).astype(np.int64) + width * np.floor(y).astype(np.int64)
+    return np.where(inside, pix, -1).astype(np.int32)
+
+
+def smooth235_lengths(lo: int, hi: int) -> np.ndarray:
+    """All n in [lo, hi] whose prime factors are 2, 3 and 5."""
+    out = []
+    a = 1
+    while a <= hi:
+        b = a
+        while b <= hi:
+            c = b
+            while c <= hi:
+                if c >= lo:
+                    out.append(c)
+                c *= 5
+            b *= 3
+        a *= 2
+    return np.array(sorted(out), dtype=np.int64)
 
 
 def _project(m: np.ndarray, pix: np.ndarray, c: np.ndarray | None, s: np.ndarray | None) -> np.ndarray:
@@ -169,3 +211,37 @@ def config_iqu_512(seed: int = SEED_BASE + 1):
 def config_iqu_256(seed: int = SEED_BASE + 3):
     """256x256 IQU map, 4 detectors x 2^20 samples at 200 Hz."""
     return config_iqu(256, 4, 1 << 20, seed)
+
+
+def config_uneven(width: int = 1024, n_chunks: int = 64, lo: int = 1 << 16, hi: int = 1 << 20,
+                  seed: int = SEED_BASE + 2, fs: float = 200.0, spp: int = 2):
+    """Batched uneven chunks: lengths drawn uniformly from the 2-3-5-smooth integers in
+    [lo, hi], each chunk its own 1/f spectrum (f_knee ~ U(0.05, 3) Hz, alpha ~ U(1, 3),
+    sigma ~ U(0.5, 2)), its own raster angle ~ U(0, pi) and detector angle ~ U(0, 180) deg
+    plus a 0.5 Hz half-wave plate, all scanning one width x width IQU map."""
+    rng = _rng(seed, 11)
+    cand = smooth235_lengths(lo, hi)
+    lens = rng.choice(cand, size=n_chunks)
+    fknees = rng.uniform(0.05, 3.0, size=n_chunks)
+    alphas = rng.uniform(1.0, 3.0, size=n_chunks)
+    sigmas = rng.uniform(0.5, 2.0, size=n_chunks)
+    raster = rng.uniform(0.0, np.pi, size=n_chunks)
+    angles = rng.uniform(0.0, 180.0, size=n_chunks)
+    phases = rng.integers(0, 1 << 20, size=n_chunks)
+    chunks = [raster_angled(width, spp, int(lens[c]), raster[c], int(phases[c]))
+              for c in range(n_chunks)]
+    return make_problem(width, 3, chunks, fs, sigmas, fknees, alphas, angles, 0.5, seed)
+
+
+def config_crosslinked(width: int = 2048, n_det: int = 32, n_per_det: int = 1 << 24,
+                       seed: int = SEED_BASE + 4, fs: float = 200.0, spp: int = 2,
+                       weight_dtype=np.float16):
+    """Large single-GPU run: n_det detectors on cross-linked rasters at 0, 45, 90 and 135
+    degrees (detector d at 45 (d mod 4) degrees), detector angles d * 180 / n_det plus a
+    0.5 Hz half-wave plate, 1/f noise f_knee 0.5 Hz, alpha 2, sigma 1, FP16 weights."""
+    step = max(1, width // max(1, n_det // 4))
+    chunks = [raster_angled(width, spp, n_per_det, np.deg2rad(45.0 * (d % 4)), (d // 4) * step)
+              for d in range(n_det)]
+    angles = [180.0 * d / n_det for d in range(n_det)]
+    return make_problem(width, 3, chunks, fs, [1.0] * n_det, [0.5] * n_det, [2.0] * n_det,
+                        angles, 0.5, seed, weight_dtype=weight_dtype)

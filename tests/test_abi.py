@@ -48,12 +48,19 @@ def test_workspace_size_host_checks(lib):
     assert lib.mm_plan_workspace_size(2, offp, 100, 3, 7, ctypes.byref(n)) == binding.MM_ERR_ARG
     assert lib.mm_plan_workspace_size(2, offp, 0, 3, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
     assert b"n_pix" in lib.mm_last_error()
-    # unsupported lengths: odd, not 2 x power of two, too short
-    for bad in ([0, 4095], [0, 3000], [0, 256]):
+    # unsupported lengths: a prime factor other than 2, 3, 5; too long; too short; empty
+    for bad in ([0, 4095], [0, 7 * 64], [0, 1 << 25], [0, 3], [0, 0]):
         o = np.array(bad, dtype=np.int64)
         r = lib.mm_plan_workspace_size(1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 10, 1,
                                        0, ctypes.byref(n))
-        assert r == binding.MM_ERR_UNSUPPORTED, bad
+        assert r in (binding.MM_ERR_UNSUPPORTED, binding.MM_ERR_ARG), bad
+        assert r == (binding.MM_ERR_ARG if bad[1] == 0 else binding.MM_ERR_UNSUPPORTED), bad
+    # 2-3-5-smooth lengths (even, odd, small powers of two) and unaligned starts are planned
+    for good in ([0, 3000], [0, 3125], [0, 256], [0, 6000, 10096], [2, 4098]):
+        o = np.array(good, dtype=np.int64)
+        r = lib.mm_plan_workspace_size(len(good) - 1, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       10, 3, 0, ctypes.byref(n))
+        assert r == binding.MM_OK, good
 
 
 def test_null_arguments_rejected_on_host(lib):

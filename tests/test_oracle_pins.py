@@ -283,3 +283,23 @@ def test_chi2_modes_sum_and_unit_mean():
     assert abs(tot - O.chi2(prob, m)) <= 1e-10 * tot
     allm = np.concatenate([md[1:-1] for md in modes])
     assert abs(allm.mean() - 1.0) < 0.05
+
+
+def test_synth_uneven_and_angled_rasters():
+    """Inputs of the uneven-chunk workload: lengths 2-3-5-smooth in range, pixel indices in
+    range or -1, an axis-aligned raster reproduces the horizontal sweep pixel by pixel."""
+    n = synth.smooth235_lengths(2 ** 16, 2 ** 20)
+    assert len(n) == 228 and n[0] == 2 ** 16 and n[-1] == 2 ** 20
+    for v in n[:40]:
+        x = int(v)
+        for f in (2, 3, 5):
+            while x % f == 0:
+                x //= f
+        assert x == 1
+    s = synth.config_uneven(32, 5, 2000, 12000, seed=3)
+    lens = np.diff(s["offsets"])
+    assert np.all((lens >= 2000) & (lens <= 12000))
+    assert s["pix"].min() >= -1 and s["pix"].max() < 32 * 32
+    p = synth.raster_angled(8, 2, 32, 0.0, 4)
+    assert np.array_equal(p[:16], 8 * 4 + np.arange(16) // 2)        # row 4, left to right
+    assert np.array_equal(p[16:32], 8 * 4 + 7 - np.arange(16) // 2)  # back, right to left
