@@ -2,13 +2,18 @@
 
 One step = one cooled messenger iteration (Sec. 2.1) over the whole workload: pointing
 gather + column FFTs, row FFTs with the Fourier-diagonal filter and chi^2, inverse FFTs +
-FP64 binning, and the per-pixel 3x3 map solve.  Workload: 512x512 IQU map, 8 detectors x
-2^22 samples at 200 Hz (33.5 M samples), FP32 cos/sin weights, per-detector 1/f noise,
-lambda cycling through a 10 x 10 cooling schedule.  Inputs per step (pointing 403 MB,
-data spectrum 134 MB, noise table 67 MB) exceed the 129 MB L2, so no flush is needed.
+FP64 binning, and the per-pixel 3x3 map solve.  Default workload: 512x512 IQU map, 8
+detectors x 2^22 samples at 200 Hz (33.5 M samples), FP32 cos/sin weights, per-detector
+1/f noise, lambda cycling through a 10 x 10 cooling schedule.  Inputs per step (pointing
+403 MB, data spectrum 134 MB, noise table 67 MB) exceed the 129 MB L2, so no flush is
+needed.  The default line also carries the uneven-chunk workload (64 chunks of 2-3-5-smooth
+lengths in [2^16, 2^20], 1024^2 IQU map) under "uneven_chunks".  ``--workload`` selects
+another headline workload: ``uneven64_1024`` or ``crosslinked2048_32det_2^24`` (2048^2 IQU,
+32 x 2^24 samples, FP16 weights; 200 cooled messenger iterations against 200 PCG
+iterations with chi^2 per iteration).
 
 ``--impl reference`` times the FP64 CPU oracle on the same workload instead (a bounded
-sample: one of the eight detector chunks per step, scaled by eight).
+sample: one detector chunk per step, scaled by the number of chunks).
 
 With ``--gpus N`` under torchrun each rank runs an independent replica on its own GPU
 (the solver is single-GPU); value = total iterations of all ranks / max rank time.
@@ -33,31 +38,58 @@ sys.path.insert(0, ROOT)
 METRIC = "messenger iters/s"
 UNIT = "iter/s"
 WORKLOAD = "iqu512_8det_2^22"
+WORKLOADS = ("iqu512_8det_2^22", "uneven64_1024", "crosslinked2048_32det_2^24")
 
 
-def workload_config(s):
+def load_workload(name):
+    from paper_1705_01893_gb300 import synth
+    if name == "iqu512_8det_2^22":
+        return synth.config_iqu_512()
+    if name == "uneven64_1024":
+        return synth.config_uneven()
+    if name == "crosslinked2048_32det_2^24":
+        return synth.config_crosslinked()
+    raise ValueError(name)
+
+
+def workload_config(name, s):
     n = int(s["offsets"][-1])
-    return {"workload": WORKLOAD, "map": "512x512 IQU", "detectors": len(s["offsets"]) - 1,
-            "samples_per_detector": int(s["offsets"][1] - s["offsets"][0]), "n_samples": n,
-            "weights": "fp32 cos2psi/sin2psi", "schedule": "10 levels x 10 iterations, cycled",
-            "l2": "inputs larger than L2 (>600 MB read per step), no flush",
-            "parallelism": "replicas"}
+    lens = np.diff(s["offsets"])
+    half = s["cos"] is not None and s["cos"].dtype == np.float16
+    cfg = {"workload": name, "map": "%dx%d %s" % (s["width"], s["width"],
+                                                  "IQU" if s["ncomp"] == 3 else "T"),
+           "chunks": int(len(lens)), "n_samples": n,
+           "weights": ("fp16" if half else "fp32") + " cos2psi/sin2psi",
+           "schedule": "10 levels x 10 iterations, cycled",
+           "l2": "inputs larger than L2 (>%d MB read per step), no flush" % (n * 12 // 2 ** 20),
+           "parallelism": "replicas"}
+    if len(set(lens.tolist())) == 1:
+        cfg["samples_per_chunk"] = int(lens[0])
+    else:
+        cfg["chunk_lengths"] = "2-3-5-smooth in [%d, %d], %d odd" % (lens.min(), lens.max(),
+                                                                    int(np.sum(lens % 2)))
+    return cfg
 
 
-def bytes_per_stage(n, npix, ncomp, wbytes):
-    """Algorithmic HBM bytes of each kernel per launch (see the design notes)."""
-    blk = 6 if ncomp == 3 else 1
-    mapb = 16 if ncomp == 3 else 4
-    return {
-        "gather_fft": n * (4 + wbytes) + 4 * n + mapb * npix,
-        "filter": 14 * n,
-        "ifft_bin": 4 * n + n * (4 + wbytes) + 8 * ncomp * npix,
-        "map": npix * (16 * ncomp + 8 * blk + mapb),
+def bytes_model(s):
+    """Algorithmic HBM bytes of each kernel for one whole iteration (see the design notes):
+    Y = bytes of the four-step intermediate (4 per sample for even chunks, packed as complex
+    pairs; 8 for odd ones, complex transforms), w = weight bytes per sample."""
+    lens = np.diff(s["offsets"]).astype(np.int64)
+    n = int(lens.sum())
+    nc, npix = s["ncomp"], s["npix"]
+    w = 0 if nc == 1 else (4 if s["cos"].dtype == np.float16 else 8)
+    Y = int(np.sum(np.where(lens % 2 == 1, 8 * lens, 4 * lens)))
+    blk = 6 if nc == 3 else 1
+    mapb = 16 if nc == 3 else 4
+    stages = {
+        "gather_fft": n * (4 + w) + Y + mapb * npix,
+        "filter": 2 * Y + Y + Y // 2,
+        "ifft_bin": Y + n * (4 + w) + 8 * nc * npix,
+        "map": npix * (16 * nc + 8 * blk + mapb),
     }
-
-
-def b_strict(n, npix, ncomp, wbytes):
-    return n * (2 * (4 + wbytes) + 4) + npix * (104 if ncomp == 3 else 24)
+    strict = 2 * n * (4 + w) + Y + npix * (104 if nc == 3 else 24)
+    return stages, strict, sum(stages.values())
 
 
 class ClockSampler:
@@ -145,7 +177,7 @@ def job_rate(ms_per_step_local, world, dev):
 # ----------------------------------------------------------------------- CPU oracle
 def time_oracle(s, steps, warmup, one_chunk=True):
     """Time the FP64 oracle's messenger step on the host (chunk 0 only when one_chunk,
-    scaled by the chunk count)."""
+    scaled by total samples / chunk-0 samples)."""
     import oracle.messenger as O
     sub = s
     scale = 1.0
@@ -159,6 +191,8 @@ def time_oracle(s, steps, warmup, one_chunk=True):
         sub["offsets"] = np.array([0, b - a], dtype=np.int64)
         sub["params"] = s["params"][c:c + 1]
         scale = float(len(s["offsets"]) - 1)
+    if one_chunk:
+        scale = float(s["offsets"][-1]) / float(len(sub["pix"]))
     prob = O.problem_from_synth(sub)
     lam = O.cooling_schedule(O.lambda_max(prob), 10, 10)
     m = np.zeros((sub["npix"], sub["ncomp"]))
@@ -175,14 +209,15 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from paper_1705_01893_gb300 import synth
-    s = synth.config_iqu_512()
+    s = load_workload(args.workload)
+    nch = len(s["offsets"]) - 1
     v, dt = time_oracle(s, args.steps, args.warmup, one_chunk=True)
-    sample = "chunk 0 of 8 (2^22 samples) per step, time x8; numpy FP64, 1 thread"
+    sample = "chunk 0 of %d (%d samples) per step, time x%d; numpy FP64, 1 thread" % (
+        nch, int(s["offsets"][1] - s["offsets"][0]), nch)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(s),
+            "data": "synthetic", "config": workload_config(args.workload, s),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -190,6 +225,109 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------- GPU arm
+def stage_loop(plan, sched, first, steps, dev, stream, chi):
+    """`steps` iterations launched stage by stage with events around every kernel on the
+    launching stream; returns per-launch times of each stage and the total."""
+    import torch
+    from paper_1705_01893_gb300 import binding as B
+    nb = plan.n_batches()
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nb + 1)]
+          for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        i = first + k
+        lam = float(sched[i % len(sched)])
+        e = ev[k]
+        for b in range(nb):
+            e[b][0].record(stream)
+            plan.stage(B.MM_STAGE_GATHER_FFT, b)
+            e[b][1].record(stream)
+            plan.stage(B.MM_STAGE_FILTER, b, lam, chi2_slot=chi[i % len(chi):i % len(chi) + 1])
+            e[b][2].record(stream)
+            plan.stage(B.MM_STAGE_IFFT_BIN, b)
+            e[b][3].record(stream)
+        e[nb][0].record(stream)
+        plan.stage(B.MM_STAGE_MAP)
+        e[nb][1].record(stream)
+    t1.record(stream)
+    fence(dev)
+    names = ["gather_fft", "filter", "ifft_bin"]
+    st = {nm: [ev[k][b][j].elapsed_time(ev[k][b][j + 1]) for k in range(steps) for b in range(nb)]
+          for j, nm in enumerate(names)}
+    st["map"] = [ev[k][nb][0].elapsed_time(ev[k][nb][1]) for k in range(steps)]
+    return st, t0.elapsed_time(t1)
+
+
+def graph_ms(plan, m, lams, dev, stream):
+    """Device time per iteration of `lams` replayed as one captured CUDA graph each."""
+    import torch
+    plan.messenger_graph(m, lams[:2])
+    fence(dev)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    plan.messenger_graph(m, lams)
+    g1.record(stream)
+    fence(dev)
+    return g0.elapsed_time(g1) / len(lams)
+
+
+def hbm_peak():
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    return float(peaks.get("hbm_gbs", 6800.0)), ("measured" if "hbm_gbs" in peaks else "fallback")
+
+
+def summarise(s, nb, stage_ms, ms_iter, hbm):
+    """Per-kernel averages, the dominant kernel and the iteration's HBM fractions."""
+    stages, strict, bpass = bytes_model(s)
+    avg = {k: sum(v) / len(v) for k, v in stage_ms.items()}
+    # the three FFT kernels run once per batch; batches split the samples
+    per_launch = {k: (v / nb if k != "map" else v) for k, v in stages.items()}
+    dom = max(avg, key=lambda k: avg[k])
+    return {
+        "avg": avg, "dom": dom, "per_launch": per_launch,
+        "achieved": per_launch[dom] / (avg[dom] * 1e-3) / 1e9,
+        "iteration_hbm": {"bytes_pass": bpass, "bytes_strict": strict,
+                          "frac_pass": bpass / (ms_iter * 1e-3) / 1e9 / hbm,
+                          "frac_strict": strict / (ms_iter * 1e-3) / 1e9 / hbm},
+    }
+
+
+def measure_secondary(name, args, dev, stream):
+    """Graph-replayed iteration time, per-kernel times and HBM fractions of another workload
+    (a compact record beside the headline line)."""
+    import torch
+    from paper_1705_01893_gb300 import binding
+    s = load_workload(name)
+    plan = binding.plan_from_synth(s, dev)
+    plan.autotune()
+    sched = binding.cooling_schedule(plan.lambda_max(), 10, 10)
+    m = torch.zeros(s["npix"], s["ncomp"], dtype=torch.float64, device=dev)
+    chi = torch.zeros(len(sched), dtype=torch.float64, device=dev)
+    plan.stage(binding.MM_STAGE_LOAD, map_inout=m)
+    steps = 20
+    stage_loop(plan, sched, 0, 3, dev, stream, chi)
+    st, _ = stage_loop(plan, sched, 3, steps, dev, stream, chi)
+    lam = np.array([float(sched[k % len(sched)]) for k in range(steps)])
+    ms = graph_ms(plan, m.clone(), lam, dev, stream)
+    hbm, src = hbm_peak()
+    sm = summarise(s, plan.n_batches(), st, ms, hbm)
+    n = int(s["offsets"][-1])
+    out = {"config": workload_config(name, s), "ms_per_iter": ms, "iters_per_s": 1e3 / ms,
+           "schedule": dict(zip(("col_nb", "col_threads", "row_threads", "radix_order"), plan.tune)),
+           "tod_gsamples_per_s": n / ms / 1e6, "batches": plan.n_batches(),
+           "stage_ms_per_launch": {k: round(v, 5) for k, v in sm["avg"].items()},
+           "dominant": {"kernel": sm["dom"], "achieved_gbs": sm["achieved"],
+                        "frac": sm["achieved"] / hbm, "bytes_per_launch": sm["per_launch"][sm["dom"]]},
+           "iteration_hbm": dict(sm["iteration_hbm"], peak_gbs=hbm, peak=src)}
+    del plan
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -198,87 +336,45 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_1705_01893_gb300 import binding, build, synth
+    from paper_1705_01893_gb300 import binding, build
     if local == 0:
         build.build()
     if world > 1:
         torch.distributed.barrier()
     binding.load()
 
-    s = synth.config_iqu_512()
+    name = args.workload
+    s = load_workload(name)
     n, npix, nc = int(s["offsets"][-1]), s["npix"], s["ncomp"]
+    lens = np.diff(s["offsets"])
     plan = binding.plan_from_synth(s, dev)
+    plan.autotune()          # schedules of the general-length kernels (no-op otherwise)
     sched = binding.cooling_schedule(plan.lambda_max(), 10, 10)
     m = torch.zeros(npix, nc, dtype=torch.float64, device=dev)
     chi = torch.zeros(max(args.steps, 1) + args.warmup, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    B = binding
-
     nb = plan.n_batches()
 
-    def step(i, ev=None):
-        """One messenger iteration; ev[b][0..3] bracket batch b's three kernels, ev[nb][0..1]
-        the map step, all on the launching stream."""
-        lam = float(sched[i % len(sched)])
-        for b in range(nb):
-            if ev is not None:
-                ev[b][0].record(stream)
-            plan.stage(B.MM_STAGE_GATHER_FFT, b)
-            if ev is not None:
-                ev[b][1].record(stream)
-            plan.stage(B.MM_STAGE_FILTER, b, lam, chi2_slot=chi[i:i + 1])
-            if ev is not None:
-                ev[b][2].record(stream)
-            plan.stage(B.MM_STAGE_IFFT_BIN, b)
-            if ev is not None:
-                ev[b][3].record(stream)
-        if ev is not None:
-            ev[nb][0].record(stream)
-        plan.stage(B.MM_STAGE_MAP)
-        if ev is not None:
-            ev[nb][1].record(stream)
-
-    plan.stage(B.MM_STAGE_LOAD, map_inout=m)
-    for i in range(args.warmup):
-        step(i)
-    fence(dev)
+    plan.stage(binding.MM_STAGE_LOAD, map_inout=m)
+    stage_loop(plan, sched, 0, args.warmup, dev, stream, chi)
 
     uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", local))
     sampler = ClockSampler(("GPU-" + uuid) if "-" in uuid and not uuid.startswith("GPU") else uuid)
     time.sleep(0.3)
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nb + 1)]
-           for _ in range(args.steps)]
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    t_start.record(stream)
-    for k in range(args.steps):
-        step(args.warmup + k, evs[k])
-    t_end.record(stream)
-    fence(dev)
-    total_ms = t_start.elapsed_time(t_end)
-    stage_names = ["gather_fft", "filter", "ifft_bin"]
-    # per-launch durations of each kernel kind (one launch per batch per iteration)
-    stage_ms = {nm: [evs[k][b][j].elapsed_time(evs[k][b][j + 1]) for k in range(args.steps)
-                     for b in range(nb)] for j, nm in enumerate(stage_names)}
-    stage_ms["map"] = [evs[k][nb][0].elapsed_time(evs[k][nb][1]) for k in range(args.steps)]
+    stage_ms, total_ms = stage_loop(plan, sched, args.warmup, args.steps, dev, stream, chi)
     _, stage_ms_step = job_rate(total_ms / args.steps, world, dev)
 
-    # the same iterations replayed as one captured CUDA graph per iteration
-    mg = m.clone()
+    # the same iterations replayed as one captured CUDA graph per iteration (the value)
     lam_g = np.array([float(sched[(args.warmup + k) % len(sched)]) for k in range(args.steps)])
-    plan.messenger_graph(mg, lam_g[:2])
-    fence(dev)
-    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    plan.messenger_graph(mg, lam_g)
-    g1.record(stream)
-    fence(dev)
+    ms_local = graph_ms(plan, m.clone(), lam_g, dev, stream)
     clocks = sampler.stop()
-    value, ms_step = job_rate(g0.elapsed_time(g1) / args.steps, world, dev)
+    value, ms_step = job_rate(ms_local, world, dev)
 
-    # the plain FP64 single-launch-per-iteration step on the same GPU (comparison bar)
+    # the plain FP64 single-launch-per-iteration step on the same GPU (comparison bar; one
+    # power-of-two chunk length only)
     plain_ms = None
-    if not args.no_plain:
+    if not args.no_plain and plan.n_batches() >= 1 and len(set(lens.tolist())) == 1 \
+            and name == WORKLOAD:
         mp = m.clone()
         lam_p = np.array([float(sched[k % len(sched)]) for k in range(5)])
         plan.messenger_plain_fp64(mp, lam_p[:1])
@@ -293,8 +389,8 @@ def run_gpu(args):
     # cuFFT (through torch.fft, a library call timed only as a comparison) against this
     # library's rfft of the same chunks (column + row kernels, natural-order output)
     fft_cmp = None
-    if not args.no_plain:
-        tod_dev = plan.tod.view(len(s["offsets"]) - 1, -1)
+    if not args.no_plain and len(set(lens.tolist())) == 1:
+        tod_dev = plan.tod.view(len(lens), -1)
         spec = torch.empty(tod_dev.shape[0] * (tod_dev.shape[1] // 2 + 1), 2, dtype=torch.float32,
                            device=dev)
         for _ in range(3):
@@ -311,7 +407,8 @@ def run_gpu(args):
         f2.record(stream)
         torch.cuda.synchronize(dev)
         fft_cmp = {"cufft_rfft_ms": f0.elapsed_time(f1) / reps, "mm_rfft_ms": f1.elapsed_time(f2) / reps,
-                   "what": "rfft of 8 x 2^22 float32 samples, complex64 out"}
+                   "what": "rfft of %d x %d float32 samples, complex64 out" % (len(lens), lens[0])}
+        del spec
 
     # end to end through the public call, host buffers: map in (pinned), one iteration,
     # map and chi^2 out, synchronised every step
@@ -342,39 +439,36 @@ def run_gpu(args):
     e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 8 * npix * nc,
            "d2h_bytes_per_step": 8 * npix * nc + 8}
 
-    tol = time_to_tolerance(plan, s, dev, stream, args) if not args.no_tolerance else None
+    tol = None
+    if not args.no_tolerance:
+        if name == "crosslinked2048_32det_2^24":
+            tol = time_to_tolerance(plan, s, dev, stream, args, schedules=(("20x10", (20, 10)),),
+                                    total=200, chi2_every=10)
+        else:
+            tol = time_to_tolerance(plan, s, dev, stream, args)
+
+    secondary = None
+    if name == WORKLOAD and not args.no_secondary:
+        del plan
+        torch.cuda.empty_cache()
+        secondary = measure_secondary("uneven64_1024", args, dev, stream)
 
     if rank != 0:
         return
-    wbytes = 8 if s["cos"] is not None and s["cos"].dtype == np.float32 else (4 if nc == 3 else 0)
-    # algorithmic bytes of one launch: the three FFT kernels process one batch
-    per_batch = bytes_per_stage(n // nb, npix, nc, wbytes)
-    full = bytes_per_stage(n, npix, nc, wbytes)
-    bps = {k: (per_batch[k] if k != "map" else full[k]) for k in full}
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    avg = {k: sum(v) / len(v) for k, v in stage_ms.items()}
-    dom = max(avg, key=lambda k: avg[k])
-    achieved = bps[dom] / (avg[dom] * 1e-3) / 1e9
-    iter_bytes = sum(full.values())
+    hbm, peak_src = hbm_peak()
+    sm = summarise(s, nb, stage_ms, ms_step, hbm)
+    dom = sm["dom"]
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
+    if os.path.exists(prof) and name == WORKLOAD:
         traffic = json.load(open(prof)).get(dom)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": workload_config(s),
+        "config": workload_config(name, s),
         "tod_gsamples_per_s": n * value / 1e9,
-        "iteration_hbm": {"bytes_pass": iter_bytes, "bytes_strict": b_strict(n, npix, nc, wbytes),
-                          "frac_pass": iter_bytes / (ms_step * 1e-3) / 1e9 / hbm,
-                          "frac_strict": b_strict(n, npix, nc, wbytes) / (ms_step * 1e-3) / 1e9 / hbm,
-                          "peak_gbs": hbm, "peak": peak_src},
+        "iteration_hbm": dict(sm["iteration_hbm"], peak_gbs=hbm, peak=peak_src),
         "batches": nb,
         "timing": "value/ms_per_step: K iterations replayed as one CUDA graph each (events on "
                   "the launching stream); roofline/stage_ms_per_launch: K iterations launched "
@@ -383,35 +477,43 @@ def run_gpu(args):
         "fp64_plain_ms_per_step": plain_ms,
         "fft_vs_cufft": fft_cmp,
         "speedup_vs_fp64_plain": None if plain_ms is None else plain_ms / ms_step,
-        "stage_ms_per_launch": {k: round(v, 5) for k, v in avg.items()},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm,
-                     "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                     "bytes_per_launch": bps[dom], "peak_source": peak_src},
+        "stage_ms_per_launch": {k: round(v, 5) for k, v in sm["avg"].items()},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": sm["achieved"], "peak": hbm,
+                     "unit": "GB/s", "frac": sm["achieved"] / hbm, "traffic": traffic,
+                     "bytes_per_launch": sm["per_launch"][dom], "peak_source": peak_src},
         "e2e": e2e,
         "gpu_launches": args.steps * (3 * nb + 1),   # per timed region
         "time_to_chi2_tol": tol,
+        "uneven_chunks": secondary,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, dt = time_oracle(s, 1, 0, one_chunk=False)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "1 full iteration of the 8 x 2^22 workload, numpy FP64, 1 thread"}
+        one = name != WORKLOAD
+        v, dt = time_oracle(s, 1, 0, one_chunk=one)
+        line["cpu_baseline"] = {
+            "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("1 full iteration of the workload" if not one else
+                       "1 iteration of chunk 0, scaled by total / chunk-0 samples") +
+                      ", numpy FP64, 1 thread"}
     print(json.dumps(line), flush=True)
 
 
-def time_to_tolerance(plan, s, dev, stream, args):
-    """Iterations and device time for the cooled messenger (10 levels x 10, then lambda = 1)
-    and for PCG (the paper's comparison solver, on the same kernels) to bring chi^2 within
-    1e-3 and 1e-4 (relative) of chi2_*, the lowest chi^2 either reaches in a long run."""
+def time_to_tolerance(plan, s, dev, stream, args, schedules=(("10x10", (10, 10)), ("8x5", (8, 5))),
+                      total=None, chi2_every=None):
+    """Iterations and device time for the cooled messenger (levels x iterations, then
+    lambda = 1) and for PCG (the paper's comparison solver, on the same kernels) to bring
+    chi^2 within 1e-3 and 1e-4 (relative) of chi2_*, the lowest chi^2 either reaches in a
+    long run.  chi2_every: also report chi^2 every that many iterations."""
     import torch
     from paper_1705_01893_gb300 import binding
     npix, nc = s["npix"], s["ncomp"]
     lam_max = plan.lambda_max()
-    total = 1 + 100 + args.tol_iters
+    if total is None:
+        total = 1 + 100 + args.tol_iters
     runs = {}
-    for label, (lv, it) in (("10x10", (10, 10)), ("8x5", (8, 5))):
+    for label, (lv, it) in schedules:
         cool = binding.cooling_schedule(lam_max, lv, it)
-        lam_m = np.concatenate([cool, np.ones(total - len(cool))])
+        lam_m = np.concatenate([cool, np.ones(max(0, total - len(cool)))])[:total]
         m = torch.zeros(npix, nc, dtype=torch.float64, device=dev)
         chi = torch.zeros(len(lam_m), dtype=torch.float64, device=dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -420,7 +522,6 @@ def time_to_tolerance(plan, s, dev, stream, args):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         runs[label] = (chi.cpu().numpy(), e0.elapsed_time(e1) / len(lam_m))
-    ms_m = runs["10x10"][1]
     n_pcg = total
     x = torch.zeros(npix, nc, dtype=torch.float64, device=dev)
     chi_p = torch.zeros(n_pcg, dtype=torch.float64, device=dev)
@@ -451,12 +552,9 @@ def time_to_tolerance(plan, s, dev, stream, args):
             it = reach(ch, t)
             out[name]["iters_%g" % t] = it
             out[name]["ms_%g" % t] = None if it is None else it * ms
+        if chi2_every:
+            out[name]["chi2_every_%d" % chi2_every] = [float(x) for x in ch[::chi2_every]]
     return out
-
-
-def plan_groups(s):
-    lens = np.diff(s["offsets"])
-    return sorted(set(int(x) for x in lens))
 
 
 def main():
@@ -470,6 +568,9 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--tol-iters", type=int, default=400,
                     help="lambda = 1 iterations after the cooling schedule (and PCG length)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS)
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the uneven-chunk record in the default line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -202,6 +202,23 @@ mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev,
 mm_status mm_chi2_modes(mm_plan p, const double* map, double lambda, double* chi2_dev,
                         double* modes, void* stream);
 
+/* Schedule of the general path (chunk lengths that are not powers of two, run by runtime
+ * mixed-radix kernels; no counterpart in the paper, which gives no implementation).
+ * mm_autotune measures, on this plan's own chunks and on `stream`, the column-tile width
+ * (8 or 16 columns), threads per CTA of the column (256, 512) and row (256, 512, 1024)
+ * kernels and the radix order (0: radix 8 first, then 4/2, 5, 3; 1: radix 4 in place of 8;
+ * 2: radices 3 and 5 first) and keeps the fastest.  It launches the column passes and the
+ * row pass in PCG-operator mode only, which leave no state behind (the accumulators are
+ * cleared), needs mm_set_noise_psd first, synchronises `stream`, and drops a captured
+ * iteration graph (recaptured on the next mm_messenger_graph).  mm_set_tune sets a schedule
+ * explicitly (MM_ERR_ARG for values outside those sets); mm_get_tune reads it (NULL
+ * outputs are skipped).  Results do not depend on the schedule beyond FP32 rounding.
+ * Plans with only power-of-two chunks ignore all three. */
+mm_status mm_autotune(mm_plan p, void* stream);
+mm_status mm_set_tune(mm_plan p, int col_nb, int col_threads, int row_threads, int radix_order,
+                      void* stream);
+mm_status mm_get_tune(mm_plan p, int* col_nb, int* col_threads, int* row_threads, int* radix_order);
+
 /* Operators, for testing and for callers composing their own solvers.
  * mm_apply_pointing:   tod_out[s] = (P m)_s in FP32 (Eq. 1), cut pixels contribute 0.
  * mm_apply_pointing_T: acc_out[p][c] = sum_s P_sp,c tod[s] in FP64 over every sample with

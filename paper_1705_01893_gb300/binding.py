@@ -26,6 +26,7 @@ _vp = ctypes.c_void_p
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _dp = ctypes.POINTER(ctypes.c_double)
 _szp = ctypes.POINTER(ctypes.c_size_t)
+_ip = ctypes.POINTER(ctypes.c_int)
 
 # name -> (restype, argtypes); mirrors include/mm.h
 SIGNATURES = {
@@ -51,6 +52,9 @@ SIGNATURES = {
     "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
     "mm_chi2_modes": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
+    "mm_autotune": (ctypes.c_int, [_vp, _vp]),
+    "mm_set_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
+    "mm_get_tune": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
     "mm_apply_pointing": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mm_apply_pointing_T": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "mm_rfft": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -266,6 +270,22 @@ class Plan:
         _check("mm_chi2_modes", load().mm_chi2_modes(self._h, _ptr(map_in), float(lam), _ptr(total),
                                                      _ptr(modes), _stream(stream)))
         return total, modes
+
+    def autotune(self, stream=None):
+        """Measure and keep the fastest schedule of the general-length kernels."""
+        _check("mm_autotune", load().mm_autotune(self._h, _stream(stream)))
+
+    @property
+    def tune(self):
+        """(col_nb, col_threads, row_threads, radix_order) of the general-length kernels."""
+        v = [ctypes.c_int() for _ in range(4)]
+        _check("mm_get_tune", load().mm_get_tune(self._h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def set_tune(self, col_nb, col_threads, row_threads, radix_order, stream=None):
+        _check("mm_set_tune", load().mm_set_tune(self._h, int(col_nb), int(col_threads),
+                                                 int(row_threads), int(radix_order),
+                                                 _stream(stream)))
 
     # -------------------------------------------------------------------- operators
     def apply_pointing(self, map_in, tod_out, stream=None):

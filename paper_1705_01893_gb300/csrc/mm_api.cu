@@ -133,15 +133,22 @@ static bool gen_shape(int64_t n, int* M, int* M1, int* M2, int* cplx) {
   return true;
 }
 
-// Radix sequence of a general DFT length: radix 8 while 8 divides, then 4 or 2, then 5s,
-// then 3s (any order is a valid Stockham schedule; larger radices mean fewer passes).
-static int radix_plan(int L, int8_t* rad) {
+// Radix sequence of a general DFT length (any order is a valid Stockham schedule; larger
+// radices mean fewer passes).  order 0: radix 8 while 8 divides, then 4 or 2, then 5s, then
+// 3s; order 1: radix 4 in place of 8; order 2: the 3s and 5s first, then 8, 4, 2.
+static int radix_plan(int L, int8_t* rad, int order = 0) {
   int n = 0;
-  while (L % 8 == 0 && n < kMaxRadices) { rad[n++] = 8; L /= 8; }
-  if (L % 4 == 0 && n < kMaxRadices) { rad[n++] = 4; L /= 4; }
-  if (L % 2 == 0 && n < kMaxRadices) { rad[n++] = 2; L /= 2; }
-  while (L % 5 == 0 && n < kMaxRadices) { rad[n++] = 5; L /= 5; }
-  while (L % 3 == 0 && n < kMaxRadices) { rad[n++] = 3; L /= 3; }
+  auto twos = [&]() {
+    if (order != 1)
+      while (L % 8 == 0 && n < kMaxRadices) { rad[n++] = 8; L /= 8; }
+    while (L % 4 == 0 && n < kMaxRadices) { rad[n++] = 4; L /= 4; }
+    if (L % 2 == 0 && n < kMaxRadices) { rad[n++] = 2; L /= 2; }
+  };
+  auto odds = [&]() {
+    while (L % 5 == 0 && n < kMaxRadices) { rad[n++] = 5; L /= 5; }
+    while (L % 3 == 0 && n < kMaxRadices) { rad[n++] = 3; L /= 3; }
+  };
+  if (order == 2) { odds(); twos(); } else { twos(); odds(); }
   return L == 1 ? n : -1;
 }
 
@@ -163,7 +170,9 @@ static size_t tw_count(int M, int M1, int M2, bool general) {
 // -------------------------------------------------------------------- workspace layout
 struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
-      ybuf, scal, tpix, tcos, tsin, lam, iter, map64, groups, gen, total, ybytes;
+      ybuf, scal, tpix, tcos, tsin, lam, iter, map64, groups, gen, gen_rec, gen_ctab, gen_rtab,
+      total, ybytes;
+  int64_t gen_ccap, gen_rcap;
   int lam_cap;
   int n_groups;
   int gM[kMaxGroups], gM1[kMaxGroups], gM2[kMaxGroups], gcount[kMaxGroups], gbatch[kMaxGroups];
@@ -295,9 +304,21 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->lam = take(sizeof(double) * L->lam_cap);
   L->iter = take(128);
   L->map64 = take(sizeof(double) * ncomp * np);
-  // general path: device groups, chunk list and three prefix arrays
+  // general path: device groups, chunk list, three prefix arrays, per-chunk records and the
+  // work-item tables (column tiles sized for the narrowest tile width)
+  int64_t ctiles = 0, rjobs = 0;
+  for (int c : L->gen_list) {
+    const int g = L->chunk_group[c];
+    ctiles += (L->gM2[g] + 7) / 8;
+    rjobs += L->gM1[g] / 2 + 1;
+  }
+  L->gen_ccap = ctiles;
+  L->gen_rcap = rjobs;
   L->groups = take(sizeof(Group) * L->n_groups);
   L->gen = take(sizeof(int) * (ngen + 1) + 3 * sizeof(int64_t) * (ngen + 1) + 64);
+  L->gen_rec = take(sizeof(GenChunk) * ngen);
+  L->gen_ctab = take(sizeof(int2) * ctiles);
+  L->gen_rtab = take(sizeof(int2) * rjobs);
   L->total = o;
   return MM_OK;
 }
@@ -819,29 +840,52 @@ __global__ void k_pcg_dir(int64_t n_pix, const double* __restrict__ z, double* _
 // ------------------------------------------------------------------------- plan API
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
-// Prefix sums of the general chunk list for the current column-tile width, uploaded with
-// the list itself (synchronous with respect to the host arrays: the copy is staged).
-static cudaError_t gen_set_tiles(mm_plan_s* p, cudaStream_t s) {
+// Tables of the general path for the current schedule (p->gen_tune): prefix sums over the
+// general chunk list, one record per general chunk (descriptor, twiddle tables, radix
+// sequences of the chosen order) and the work-item tables (chunk, tile / row) of the column
+// and row kernels; uploaded and synchronised.
+static cudaError_t gen_upload(mm_plan_s* p, cudaStream_t s) {
   const int ng = p->n_gen, nb = p->gen_tune.col_nb;
-  int64_t ct = 0, rj = 0, yo = 0;
+  std::vector<GenChunk> rec(ng);
+  std::vector<int2> ct, rt;
+  int64_t ct_n = 0, rj = 0, yo = 0;
   for (int i = 0; i < ng; ++i) {
-    const ChunkDesc& d = p->h_desc[p->h_gen_chunks[i]];
-    p->h_gen_ctile[i] = ct;
+    const int c = p->h_gen_chunks[i];
+    ChunkDesc& d = p->h_desc[c];
+    const Group& G = p->groups[d.grp];
+    p->h_gen_ctile[i] = ct_n;
     p->h_gen_rjob[i] = rj;
     p->h_gen_yoff[i] = yo;
-    ct += (d.M2 + nb - 1) / nb;
+    const int tiles = (d.M2 + nb - 1) / nb;
+    for (int t = 0; t < tiles; ++t) ct.push_back(make_int2(i, t * nb));
+    for (int r = 0; r <= d.M1 / 2; ++r) rt.push_back(make_int2(i, r));
+    GenChunk& R = rec[i];
+    memset(&R, 0, sizeof(R));
+    R.d = d;
+    R.c = c;
+    R.log_lo = G.log_lo;
+    R.yoff = yo;
+    R.tw_col = G.tw_col; R.tw_row = G.tw_row; R.tw_lo = G.tw_lo; R.tw_hi = G.tw_hi;
+    R.pack_a = G.tw_pack_a; R.pack_b = G.tw_pack_b;
+    R.nr1 = radix_plan(d.M1, R.rad1, p->gen_tune.radix_order);
+    R.nr2 = radix_plan(d.M2, R.rad2, p->gen_tune.radix_order);
+    ct_n += tiles;
     rj += d.M1 / 2 + 1;
     yo += d.M;
   }
-  p->h_gen_ctile[ng] = ct;
+  p->h_gen_ctile[ng] = ct_n;
   p->h_gen_rjob[ng] = rj;
   p->h_gen_yoff[ng] = yo;
+  if (ct_n > p->gen_ccap) return cudaErrorInvalidValue;
   cudaError_t e;
   const size_t b = sizeof(int64_t) * (ng + 1);
   if ((e = cudaMemcpyAsync(p->gen_ctile, p->h_gen_ctile, b, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(p->gen_rjob, p->h_gen_rjob, b, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(p->gen_yoff, p->h_gen_yoff, b, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(p->gen_chunks, p->h_gen_chunks, sizeof(int) * ng, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(p->gen_rec, rec.data(), sizeof(GenChunk) * ng, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(p->gen_ctab, ct.data(), sizeof(int2) * ct.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(p->gen_rtab, rt.data(), sizeof(int2) * rt.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
 }
 
@@ -916,9 +960,13 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
     p->gen_yoff = p->gen_rjob + ng1;
     p->gen_chunks = reinterpret_cast<int*>(p->gen_yoff + ng1);
   }
+  p->gen_rec = reinterpret_cast<GenChunk*>(ws + L.gen_rec);
+  p->gen_ctab = reinterpret_cast<int2*>(ws + L.gen_ctab);
+  p->gen_rtab = reinterpret_cast<int2*>(ws + L.gen_rtab);
+  p->gen_ccap = L.gen_ccap;
   p->h_gen_ctile = p->h_gen_rjob = p->h_gen_yoff = nullptr;
   p->h_gen_chunks = nullptr;
-  p->gen_tune = GenTune{8, 256, 256};
+  p->gen_tune = GenTune{8, 256, 256, 0};
 
   // host descriptors, grouped chunk lists
   p->h_desc = new (std::nothrow) ChunkDesc[n_chunks];
@@ -1026,7 +1074,7 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   if ((e = cudaMemcpyAsync(p->d_groups, p->groups, sizeof(Group) * L.n_groups,
                            cudaMemcpyHostToDevice, s)) != cudaSuccess) return fail("group upload", e);
   if (p->n_gen > 0) {
-    if ((e = gen_set_tiles(p, s)) != cudaSuccess) return fail("general chunk tables", e);
+    if ((e = gen_upload(p, s)) != cudaSuccess) return fail("general chunk tables", e);
   }
   if ((e = cudaMemsetAsync(p->hits, 0, sizeof(int32_t) * n_pix, s)) != cudaSuccess) return fail("memset", e);
   if ((e = cudaMemsetAsync(p->scal, 0, sizeof(double) * kScalCount, s)) != cudaSuccess) return fail("memset", e);
@@ -1119,6 +1167,7 @@ extern "C" mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const do
     p->h_desc[c].tau = taus[c];
   }
   MM_CUDA(cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(ChunkDesc) * C, cudaMemcpyHostToDevice, s));
+  if (p->n_gen > 0) MM_CUDA(gen_upload(p, s));     // the general records carry tau too
   const double* d_params = nullptr;
   if (params) {
     MM_CUDA(cudaMemcpyAsync(p->params, params, sizeof(double) * 4 * C, cudaMemcpyHostToDevice, s));
@@ -1488,6 +1537,130 @@ extern "C" mm_status mm_chi2_modes(mm_plan p, const double* map, double lambda, 
   k_chi2_modes<<<grid, 256, 0, s>>>(
       p->d_desc, p->n_chunks, n_bins, p->dtab, p->nbar, p->nyq, lambda, modes, chi2_dev);
   LAUNCHED("k_chi2_modes");
+  return MM_OK;
+}
+
+// ------------------------------------------------------------------- general-path schedule
+static mm_status apply_tune(mm_plan p, const GenTune& t, cudaStream_t s) {
+  p->gen_tune = t;
+  cudaError_t e = gen_upload(p, s);
+  if (e != cudaSuccess) {
+    mm_set_error("general schedule upload: %s", cudaGetErrorString(e));
+    return MM_ERR_CUDA;
+  }
+  if (p->graph_exec) {            // the captured iteration holds the old launch shapes
+    cudaGraphExecDestroy(p->graph_exec);
+    p->graph_exec = nullptr;
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_get_tune(mm_plan p, int* col_nb, int* col_threads, int* row_threads,
+                                 int* radix_order) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  if (col_nb) *col_nb = p->gen_tune.col_nb;
+  if (col_threads) *col_threads = p->gen_tune.col_threads;
+  if (row_threads) *row_threads = p->gen_tune.row_threads;
+  if (radix_order) *radix_order = p->gen_tune.radix_order;
+  return MM_OK;
+}
+
+extern "C" mm_status mm_set_tune(mm_plan p, int col_nb, int col_threads, int row_threads,
+                                 int radix_order, void* stream) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  MM_ARG(col_nb == 8 || col_nb == 16, "col_nb must be 8 or 16");
+  MM_ARG(col_threads == 256 || col_threads == 512, "col_threads must be 256 or 512");
+  MM_ARG(row_threads == 256 || row_threads == 512 || row_threads == 1024,
+         "row_threads must be 256, 512 or 1024");
+  MM_ARG(radix_order >= 0 && radix_order <= 2, "radix_order must be 0, 1 or 2");
+  if (p->n_gen == 0) return MM_OK;
+  return apply_tune(p, GenTune{col_nb, col_threads, row_threads, radix_order}, S(stream));
+}
+
+// Time `reps` runs of `fn` on stream s (after one untimed run); fastest run in ms.
+template <typename F>
+static cudaError_t time_min(cudaStream_t s, int reps, F fn, float* best) {
+  cudaEvent_t a, b;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&b)) != cudaSuccess) { cudaEventDestroy(a); return e; }
+  *best = 1e30f;
+  for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+    if ((e = cudaEventRecord(a, s)) != cudaSuccess) break;
+    if ((e = fn()) != cudaSuccess) break;
+    if ((e = cudaEventRecord(b, s)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+    float ms = 0.f;
+    if ((e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) break;
+    if (r > 0 && ms < *best) *best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return e;
+}
+
+extern "C" mm_status mm_autotune(mm_plan p, void* stream) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  if (p->n_gen == 0) return MM_OK;
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  cudaStream_t s = S(stream);
+  const GenTune keep = p->gen_tune;
+  // the candidates run the column passes (gather from the current map, bin into acc) and
+  // the row pass in PCG-operator mode, which touch only scratch (ybuf, acc), cleared below
+  auto cols = [&]() -> cudaError_t {
+    for (int b = 0; b < p->n_batches; ++b) {
+      const Batch& B = p->h_batches[b];
+      if (B.group >= 0) continue;
+      cudaError_t e = launch_gen_col_forward(p, B, kSrcGather, nullptr, s);
+      if (e == cudaSuccess) e = launch_gen_col_inverse(p, B, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  const RowArgs ra{kRowPcgApply, 1.0, nullptr, nullptr};
+  auto rows = [&]() -> cudaError_t {
+    for (int b = 0; b < p->n_batches; ++b) {
+      const Batch& B = p->h_batches[b];
+      if (B.group < 0) {
+        cudaError_t e = launch_gen_row(p, B, ra, s);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    return cudaSuccess;
+  };
+  const int nbs[2] = {8, 16}, cts[2] = {256, 512}, rts[3] = {256, 512, 1024};
+  GenTune best = keep;
+  float best_total = 1e30f;
+  for (int order = 0; order < 3; ++order) {
+    GenTune t = keep;
+    t.radix_order = order;
+    float bc = 1e30f, br = 1e30f;
+    GenTune tc = t;
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        t.col_nb = nbs[i];
+        t.col_threads = cts[j];
+        mm_status st = apply_tune(p, t, s);
+        if (st != MM_OK) return st;
+        float ms;
+        MM_CUDA(time_min(s, 3, cols, &ms));
+        if (ms < bc) { bc = ms; tc.col_nb = t.col_nb; tc.col_threads = t.col_threads; }
+      }
+    t = tc;
+    for (int k = 0; k < 3; ++k) {
+      t.row_threads = rts[k];
+      mm_status st = apply_tune(p, t, s);
+      if (st != MM_OK) return st;
+      float ms;
+      MM_CUDA(time_min(s, 3, rows, &ms));
+      if (ms < br) { br = ms; tc.row_threads = t.row_threads; }
+    }
+    if (bc + br < best_total) { best_total = bc + br; best = tc; }
+  }
+  mm_status st = apply_tune(p, best, s);
+  if (st != MM_OK) return st;
+  MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * p->ncomp * p->n_pix, s));
+  MM_CUDA(cudaStreamSynchronize(s));
   return MM_OK;
 }
 

@@ -22,13 +22,9 @@
 namespace mm {
 
 struct GenParams {
-  const ChunkDesc* __restrict__ desc;
-  const Group* __restrict__ groups;
-  const int* __restrict__ chunks;       // general chunk list
-  const int64_t* __restrict__ prefix;   // column tiles (A, C) or row jobs (B) per chunk
-  const int64_t* __restrict__ yoff;     // intermediate offset per chunk
-  int first, count;                     // the batch: general chunks [first, first + count)
-  int64_t base, n_items, base_y;
+  const GenChunk* __restrict__ rec;     // per general chunk
+  const int2* __restrict__ items;       // (general index, first column / row k1) per item
+  int64_t base, n_items, base_y;        // the batch's items and intermediate offset
   int nb;                               // columns per tile (A, C)
   const int32_t* __restrict__ pix;      // caller's pointing, natural order
   const void* cosw;
@@ -44,15 +40,20 @@ struct GenParams {
   RowArgs a;
 };
 
-// Chunk i (an index into the general list) whose item range holds global item g.
-__device__ __forceinline__ int gen_find(const GenParams& q, int64_t g) {
-  int lo = q.first, hi = q.first + q.count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (__ldg(q.prefix + mid) <= g) lo = mid; else hi = mid - 1;
+// k mod d for 0 <= k < 2^22 with d uniform: float reciprocal, then one correction step
+// each way (the float quotient is within one of the true one).
+struct FastDiv {
+  int d;
+  float inv;
+  __device__ __forceinline__ explicit FastDiv(int dd) : d(dd), inv(1.0f / (float)dd) {}
+  __device__ __forceinline__ int mod(int k) const {
+    const int q = __float2int_rz((float)k * inv);
+    int r = k - q * d;
+    if (r < 0) r += d;
+    if (r >= d) r -= d;
+    return r;
   }
-  return lo;
-}
+};
 
 // ----------------------------------------------------------------- Stockham passes
 // Column tiles: element (j, c) of the tile's NB interleaved sequences at j * NB + c.
@@ -60,9 +61,10 @@ template <int R, int DIR>
 __device__ __forceinline__ void gpass_cols(const float2* src, float2* dst, int L, int Ns, int NB,
                                            int lnb, const float2* __restrict__ tw, int T) {
   const int nb = L / R, mul = L / (Ns * R);
+  const FastDiv fd(Ns);
   for (int b = threadIdx.x; b < nb * NB; b += T) {
     const int c = b & (NB - 1), i = b >> lnb;
-    const int k = i % Ns;
+    const int k = fd.mod(i);
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(i + r * nb) * NB + c];
@@ -85,10 +87,11 @@ template <int R, int DIR>
 __device__ __forceinline__ void gpass_rows(const float2* src, float2* dst, int L, int Ns, int nseq,
                                            const float2* __restrict__ tw, int T) {
   const int nb = L / R, mul = L / (Ns * R);
+  const FastDiv fd(Ns);
   for (int b = threadIdx.x; b < nb * nseq; b += T) {
     const int sq = b >= nb, i = b - sq * nb;
     const int base = sq * L;
-    const int k = i % Ns;
+    const int k = fd.mod(i);
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[base + i + r * nb];
@@ -137,7 +140,7 @@ __device__ float2* gen_dft(float2* a, float2* b, int L, int nr, const int8_t* ra
   return a;
 }
 
-__device__ __forceinline__ float2 gen_tw_big(const Group& g, int e) {
+__device__ __forceinline__ float2 gen_tw_big(const GenChunk& g, int e) {
   return cmul(__ldg(&g.tw_hi[e >> g.log_lo]), __ldg(&g.tw_lo[e & ((1 << g.log_lo) - 1)]));
 }
 
@@ -168,12 +171,11 @@ __global__ void __launch_bounds__(512) k_gen_col_forward(GenParams q) {
   extern __shared__ float2 gsm[];
   const int T = blockDim.x, NB = q.nb, lnb = NB == 16 ? 4 : 3;
   for (int64_t t = blockIdx.x; t < q.n_items; t += gridDim.x) {
-    const int64_t g = q.base + t;
-    const int i = gen_find(q, g);
-    const ChunkDesc d = q.desc[__ldg(q.chunks + i)];
-    const Group& G = q.groups[d.grp];
+    const int2 it = __ldg(q.items + q.base + t);
+    const GenChunk& G = q.rec[it.x];
+    const ChunkDesc d = G.d;
     const int M1 = d.M1, M2 = d.M2;
-    const int j2_0 = (int)(g - __ldg(q.prefix + i)) * NB;
+    const int j2_0 = it.y;
     const int width = min(NB, M2 - j2_0);
     float2* a = gsm;
     float2* b = gsm + M1 * NB;
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(512) k_gen_col_forward(GenParams q) {
     }
     __syncthreads();
     const float2* r = gen_dft<true, -1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, 1, T);
-    float2* y = q.ybuf + (__ldg(q.yoff + i) - q.base_y);
+    float2* y = q.ybuf + (G.yoff - q.base_y);
     for (int e = threadIdx.x; e < M1 * NB; e += T) {
       const int k1 = e >> lnb, c = e & (NB - 1);
       if (c < width) {
@@ -265,16 +267,15 @@ __global__ void __launch_bounds__(512) k_gen_col_inverse(GenParams q) {
   extern __shared__ float2 gsm[];
   const int T = blockDim.x, NB = q.nb, lnb = NB == 16 ? 4 : 3;
   for (int64_t t = blockIdx.x; t < q.n_items; t += gridDim.x) {
-    const int64_t g = q.base + t;
-    const int i = gen_find(q, g);
-    const ChunkDesc d = q.desc[__ldg(q.chunks + i)];
-    const Group& G = q.groups[d.grp];
+    const int2 it = __ldg(q.items + q.base + t);
+    const GenChunk& G = q.rec[it.x];
+    const ChunkDesc d = G.d;
     const int M1 = d.M1, M2 = d.M2;
-    const int j2_0 = (int)(g - __ldg(q.prefix + i)) * NB;
+    const int j2_0 = it.y;
     const int width = min(NB, M2 - j2_0);
     float2* a = gsm;
     float2* b = gsm + M1 * NB;
-    const float2* y = q.ybuf + (__ldg(q.yoff + i) - q.base_y);
+    const float2* y = q.ybuf + (G.yoff - q.base_y);
     for (int e = threadIdx.x; e < M1 * NB; e += T) {
       const int k1 = e >> lnb, c = e & (NB - 1);
       a[e] = c < width ? y[(int64_t)k1 * M2 + j2_0 + c] : make_float2(0.f, 0.f);
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(512) k_gen_col_inverse(GenParams q) {
 }
 
 // ---------------------------------------------------- kernel B: rows, filter, inverse rows
-__global__ void __launch_bounds__(512) k_gen_row(GenParams q) {
+__global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   extern __shared__ float2 gsm[];
   __shared__ double red[32];
   const int T = blockDim.x;
@@ -306,17 +307,16 @@ __global__ void __launch_bounds__(512) k_gen_row(GenParams q) {
   const bool want_x2 = chi2 != nullptr &&
                        (mode == kRowMessenger || mode == kRowChi2 || mode == kRowPcgRhs);
   for (int64_t job = blockIdx.x; job < q.n_items; job += gridDim.x) {
-    const int64_t g = q.base + job;
-    const int i = gen_find(q, g);
-    const int c = __ldg(q.chunks + i);
-    const ChunkDesc d = q.desc[c];
-    const Group& G = q.groups[d.grp];
+    const int2 it = __ldg(q.items + q.base + job);
+    const GenChunk& G = q.rec[it.x];
+    const ChunkDesc d = G.d;
+    const int c = G.c;
     const int M1 = d.M1, M2 = d.M2, M = d.M;
-    const int rA = (int)(g - __ldg(q.prefix + i));
+    const int rA = it.y;
     const int rB = rA == 0 ? 0 : M1 - rA;
     const bool self = rA == rB;
     const int nseq = self ? 1 : 2;
-    float2* y = q.ybuf + (__ldg(q.yoff + i) - q.base_y);
+    float2* y = q.ybuf + (G.yoff - q.base_y);
     float2* a = gsm;
     float2* b = gsm + 2 * M2;
     float2* z = a;
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(512) k_gen_row(GenParams q) {
       }
     } else {
       // pairs (k, M - k): element p of row rA with partner qi of row rB (or of row rA)
-      const float2 wa = __ldg(&G.tw_pack_a[rA]);
+      const float2 wa = __ldg(&G.pack_a[rA]);
       for (int p = threadIdx.x; p < M2; p += T) {
         int qs = 1, qi = M2 - 1 - p;
         if (self) {
@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(512) k_gen_row(GenParams q) {
           z[0] = make_float2(Y0 + YM, Y0 - YM);
           continue;
         }
-        const float2 w = cmul(wa, __ldg(&G.tw_pack_b[p]));   // w_{2M}^k, k = rA + M1 p
+        const float2 w = cmul(wa, __ldg(&G.pack_b[p]));   // w_{2M}^k, k = rA + M1 p
         const float2 E = cscale(cadd(Zk, cconj(Zp)), 0.5f);
         const float2 O = cscale(mul_i<-1>(csub(Zk, cconj(Zp))), 0.5f);
         const float2 wO = cmul(w, O);
@@ -470,16 +470,11 @@ __global__ void __launch_bounds__(512) k_gen_row(GenParams q) {
 }
 
 // ------------------------------------------------------------------------ launchers
-static GenParams gen_params(const mm_plan_s* p, const Batch& b, const int64_t* d_prefix,
+static GenParams gen_params(const mm_plan_s* p, const Batch& b, const int2* items,
                             const int64_t* h_prefix) {
   GenParams q{};
-  q.desc = p->d_desc;
-  q.groups = p->d_groups;
-  q.chunks = p->gen_chunks;
-  q.prefix = d_prefix;
-  q.yoff = p->gen_yoff;
-  q.first = b.first;
-  q.count = b.count;
+  q.rec = p->gen_rec;
+  q.items = items;
   q.base = h_prefix[b.first];
   q.n_items = h_prefix[b.first + b.count] - q.base;
   q.base_y = p->h_gen_yoff[b.first];
@@ -521,7 +516,7 @@ static cudaError_t gen_launch(K kernel, int threads, size_t smem, int64_t items,
 
 cudaError_t launch_gen_col_forward(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                    cudaStream_t st) {
-  GenParams q = gen_params(p, b, p->gen_ctile, p->h_gen_ctile);
+  GenParams q = gen_params(p, b, p->gen_ctab, p->h_gen_ctile);
   q.nb = p->gen_tune.col_nb;
   q.tod = tod;
   int m1, m2;
@@ -534,7 +529,7 @@ cudaError_t launch_gen_col_forward(const mm_plan_s* p, const Batch& b, int src, 
 }
 
 cudaError_t launch_gen_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st) {
-  GenParams q = gen_params(p, b, p->gen_ctile, p->h_gen_ctile);
+  GenParams q = gen_params(p, b, p->gen_ctab, p->h_gen_ctile);
   q.nb = p->gen_tune.col_nb;
   int m1, m2;
   gen_extent(p, b, &m1, &m2);
@@ -545,7 +540,7 @@ cudaError_t launch_gen_col_inverse(const mm_plan_s* p, const Batch& b, cudaStrea
 }
 
 cudaError_t launch_gen_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
-  GenParams q = gen_params(p, b, p->gen_rjob, p->h_gen_rjob);
+  GenParams q = gen_params(p, b, p->gen_rtab, p->h_gen_rjob);
   q.a = a;
   int m1, m2;
   gen_extent(p, b, &m1, &m2);

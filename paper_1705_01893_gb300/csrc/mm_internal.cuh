@@ -65,12 +65,29 @@ struct Batch {
   int count;
 };
 
-// Schedule of the general path's persistent kernels: tile width, threads (picked per plan
-// by measurement, see mm_autotune).
+// Schedule of the general path's persistent kernels: tile width, threads and radix order
+// (picked per plan by measurement, see mm_autotune).
 struct GenTune {
   int col_nb;         // columns per column tile: 8 or 16
   int col_threads;    // 256 or 512
-  int row_threads;    // 256 or 512
+  int row_threads;    // 256, 512 or 1024
+  int radix_order;    // 0: radix 8 first, then 4/2, 5, 3; 1: radix 4 instead of 8; 2: 3s and 5s first
+};
+
+// Everything a general-path kernel needs about one chunk, in one record (one dependent load
+// per work item instead of chunk list -> descriptor -> group).
+struct GenChunk {
+  ChunkDesc d;
+  int c;                   // chunk index in the plan
+  int log_lo, nr1, nr2;
+  int64_t yoff;            // intermediate offset in the general list
+  const float2* tw_col;    // [M1] exp(-2 pi i m / M1)
+  const float2* tw_row;    // [M2] exp(-2 pi i m / M2)
+  const float2* tw_lo;
+  const float2* tw_hi;
+  const float2* pack_a;
+  const float2* pack_b;
+  int8_t rad1[kMaxRadices], rad2[kMaxRadices];
 };
 
 }  // namespace mm
@@ -129,6 +146,10 @@ struct mm_plan_s {
   int64_t* h_gen_rjob;
   int64_t* h_gen_yoff;
   int* h_gen_chunks;
+  mm::GenChunk* gen_rec;   // [n_gen] device records
+  int2* gen_ctab;          // column tiles: (general index, first column), capacity gen_ccap
+  int2* gen_rtab;          // row jobs: (general index, row k1)
+  int64_t gen_ccap;
   mm::Group* d_groups;
   mm::GenTune gen_tune;
   int32_t* tpix;    // pointing copied into column-tile order (see k_tile_pointing)

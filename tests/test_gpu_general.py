@@ -232,3 +232,35 @@ def test_uneven_full_size_one_step():
         torch.cuda.synchronize()
         assert rel(m.cpu().numpy(), m_ref) <= tol, (lam, tol)
         assert abs(chi.item() - chi_ref) <= 1e-5 * chi_ref
+
+
+def test_every_schedule_gives_the_same_iterate(uneven):
+    """Each tile width, thread count and radix order of the general kernels (and the one the
+    autotuner picks) reproduces the oracle's step; schedules differ only by FP32 rounding."""
+    s = uneven
+    prob = O.problem_from_synth(s)
+    lam = [math.inf, O.lambda_max(prob) ** 0.5, 1.0]
+    m_ref, chi_ref = O.run_messenger(prob, lam)
+    plan = binding.plan_from_synth(s, DEV)
+    outs = []
+    for tune in [(8, 256, 256, 0), (16, 512, 1024, 1), (8, 512, 512, 2), (16, 256, 256, 2), None]:
+        if tune is None:
+            plan.autotune()
+            assert plan.tune[0] in (8, 16) and plan.tune[3] in (0, 1, 2)
+        else:
+            plan.set_tune(*tune)
+            assert plan.tune == tune
+        m = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+        chi = torch.zeros(len(lam), dtype=torch.float64, device=DEV)
+        plan.messenger(m, lam, chi)
+        g = torch.zeros_like(m)
+        plan.messenger_graph(g, lam)
+        torch.cuda.synchronize()
+        assert rel(m.cpu().numpy(), m_ref) <= 1e-5, tune
+        assert np.max(np.abs(chi.cpu().numpy() - chi_ref) / chi_ref) <= 1e-5
+        assert rel(g.cpu().numpy(), m.cpu().numpy()) <= 1e-12
+        outs.append(m.cpu().numpy())
+    for o in outs[1:]:
+        assert rel(o, outs[0]) <= 1e-5
+    with pytest.raises(binding.MMError):
+        plan.set_tune(12, 256, 256, 0)
