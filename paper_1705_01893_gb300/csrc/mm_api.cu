@@ -318,7 +318,7 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->gen = take(sizeof(int) * (ngen + 1) + 3 * sizeof(int64_t) * (ngen + 1) + 64);
   L->gen_rec = take(sizeof(GenChunk) * ngen);
   L->gen_ctab = take(sizeof(int2) * ctiles);
-  L->gen_rtab = take(sizeof(int2) * rjobs);
+  L->gen_rtab = take(sizeof(int4) * rjobs);
   L->total = o;
   return MM_OK;
 }
@@ -847,7 +847,8 @@ static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 static cudaError_t gen_upload(mm_plan_s* p, cudaStream_t s) {
   const int ng = p->n_gen, nb = p->gen_tune.col_nb;
   std::vector<GenChunk> rec(ng);
-  std::vector<int2> ct, rt;
+  std::vector<int2> ct;
+  std::vector<int4> rt;
   int64_t ct_n = 0, rj = 0, yo = 0;
   for (int i = 0; i < ng; ++i) {
     const int c = p->h_gen_chunks[i];
@@ -858,7 +859,13 @@ static cudaError_t gen_upload(mm_plan_s* p, cudaStream_t s) {
     p->h_gen_yoff[i] = yo;
     const int tiles = (d.M2 + nb - 1) / nb;
     for (int t = 0; t < tiles; ++t) ct.push_back(make_int2(i, t * nb));
-    for (int r = 0; r <= d.M1 / 2; ++r) rt.push_back(make_int2(i, r));
+    // row jobs: row 0 alone, pairs (k1, M1 - k1) in groups, row M1/2 alone for even M1
+    const size_t r0 = rt.size();
+    rt.push_back(make_int4(i, 0, 0, 0));
+    const int h = (d.M1 - 1) / 2, np = gen_row_pairs(d.M1, d.M2);
+    for (int f = 1; f <= h; f += np) rt.push_back(make_int4(i, f, h - f + 1 < np ? h - f + 1 : np, 0));
+    if (d.M1 % 2 == 0 && d.M1 >= 2) rt.push_back(make_int4(i, d.M1 / 2, 0, 0));
+    const int jobs = (int)(rt.size() - r0);
     GenChunk& R = rec[i];
     memset(&R, 0, sizeof(R));
     R.d = d;
@@ -870,7 +877,7 @@ static cudaError_t gen_upload(mm_plan_s* p, cudaStream_t s) {
     R.nr1 = radix_plan(d.M1, R.rad1, p->gen_tune.radix_order);
     R.nr2 = radix_plan(d.M2, R.rad2, p->gen_tune.radix_order);
     ct_n += tiles;
-    rj += d.M1 / 2 + 1;
+    rj += jobs;
     yo += d.M;
   }
   p->h_gen_ctile[ng] = ct_n;
@@ -885,7 +892,7 @@ static cudaError_t gen_upload(mm_plan_s* p, cudaStream_t s) {
   if ((e = cudaMemcpyAsync(p->gen_chunks, p->h_gen_chunks, sizeof(int) * ng, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(p->gen_rec, rec.data(), sizeof(GenChunk) * ng, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(p->gen_ctab, ct.data(), sizeof(int2) * ct.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(p->gen_rtab, rt.data(), sizeof(int2) * rt.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(p->gen_rtab, rt.data(), sizeof(int4) * rt.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
 }
 
@@ -962,7 +969,7 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   }
   p->gen_rec = reinterpret_cast<GenChunk*>(ws + L.gen_rec);
   p->gen_ctab = reinterpret_cast<int2*>(ws + L.gen_ctab);
-  p->gen_rtab = reinterpret_cast<int2*>(ws + L.gen_rtab);
+  p->gen_rtab = reinterpret_cast<int4*>(ws + L.gen_rtab);
   p->gen_ccap = L.gen_ccap;
   p->h_gen_ctile = p->h_gen_rjob = p->h_gen_yoff = nullptr;
   p->h_gen_chunks = nullptr;

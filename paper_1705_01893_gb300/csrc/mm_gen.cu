@@ -23,7 +23,9 @@ namespace mm {
 
 struct GenParams {
   const GenChunk* __restrict__ rec;     // per general chunk
-  const int2* __restrict__ items;       // (general index, first column / row k1) per item
+  const int2* __restrict__ items;       // column tiles: (general index, first column)
+  const int4* __restrict__ jobs;        // row jobs: (general index, first row, pairs or 0, -)
+  int tile;                             // row tile capacity (elements, padded layout)
   int64_t base, n_items, base_y;        // the batch's items and intermediate offset
   int nb;                               // columns per tile (A, C)
   const int32_t* __restrict__ pix;      // caller's pointing, natural order
@@ -53,7 +55,20 @@ struct FastDiv {
     if (r >= d) r -= d;
     return r;
   }
+  __device__ __forceinline__ int div(int k) const {
+    int q = __float2int_rz((float)k * inv);
+    const int r = k - q * d;
+    if (r < 0) --q;
+    if (r >= d) ++q;
+    return q;
+  }
 };
+
+// Row tiles hold nseq sequences of length L (sequence s at s L) in one of two layouts:
+// plain, or padded with one spare slot per 16 elements.  Each pass writes the layout that
+// suits it (padded after an even radix, whose stride-R stores would otherwise hit the same
+// banks), and the next pass reads that layout.
+__device__ __forceinline__ int lay(int e, bool pad) { return pad ? e + (e >> 4) : e; }
 
 // ----------------------------------------------------------------- Stockham passes
 // Column tiles: element (j, c) of the tile's NB interleaved sequences at j * NB + c.
@@ -82,19 +97,19 @@ __device__ __forceinline__ void gpass_cols(const float2* src, float2* dst, int L
   }
 }
 
-// Row jobs: nseq (1 or 2) contiguous sequences of length L at 0 and L.
+// Row jobs: nseq contiguous sequences of length L.
 template <int R, int DIR>
-__device__ __forceinline__ void gpass_rows(const float2* src, float2* dst, int L, int Ns, int nseq,
-                                           const float2* __restrict__ tw, int T) {
+__device__ __forceinline__ void gpass_rows(const float2* src, bool ps, float2* dst, bool pd, int L,
+                                           int Ns, int nseq, const float2* __restrict__ tw, int T) {
   const int nb = L / R, mul = L / (Ns * R);
-  const FastDiv fd(Ns);
+  const FastDiv fd(Ns), fs(nb);
   for (int b = threadIdx.x; b < nb * nseq; b += T) {
-    const int sq = b >= nb, i = b - sq * nb;
+    const int sq = fs.div(b), i = b - sq * nb;
     const int base = sq * L;
     const int k = fd.mod(i);
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[base + i + r * nb];
+    for (int r = 0; r < R; ++r) v[r] = src[lay(base + i + r * nb, ps)];
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -105,33 +120,47 @@ __device__ __forceinline__ void gpass_rows(const float2* src, float2* dst, int L
     dftR<R, DIR>(v);
     const int o = base + (i - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[o + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) dst[lay(o + r * Ns, pd)] = v[r];
   }
 }
 
-// All passes of one DFT; returns the tile holding the result (a or b).
-template <bool COLS, int DIR>
-__device__ float2* gen_dft(float2* a, float2* b, int L, int nr, const int8_t* rad,
-                           const float2* tw, int NB, int lnb, int nseq, int T) {
+// All passes of the row DFTs of a job, starting from layout `pad` in tile a; returns the
+// tile holding the result and sets `pad` to its layout.
+template <int DIR>
+__device__ float2* gen_dft_rows(float2* a, float2* b, bool& pad, int L, int nr, const int8_t* rad,
+                                const float2* tw, int nseq, int T) {
   int Ns = 1;
   for (int p = 0; p < nr; ++p) {
     const int R = rad[p];
-    if constexpr (COLS) {
-      switch (R) {
-        case 2: gpass_cols<2, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
-        case 3: gpass_cols<3, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
-        case 4: gpass_cols<4, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
-        case 5: gpass_cols<5, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
-        default: gpass_cols<8, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
-      }
-    } else {
-      switch (R) {
-        case 2: gpass_rows<2, DIR>(a, b, L, Ns, nseq, tw, T); break;
-        case 3: gpass_rows<3, DIR>(a, b, L, Ns, nseq, tw, T); break;
-        case 4: gpass_rows<4, DIR>(a, b, L, Ns, nseq, tw, T); break;
-        case 5: gpass_rows<5, DIR>(a, b, L, Ns, nseq, tw, T); break;
-        default: gpass_rows<8, DIR>(a, b, L, Ns, nseq, tw, T); break;
-      }
+    const bool pd = (R & 1) == 0;
+    switch (R) {
+      case 2: gpass_rows<2, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
+      case 3: gpass_rows<3, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
+      case 4: gpass_rows<4, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
+      case 5: gpass_rows<5, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
+      default: gpass_rows<8, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
+    }
+    __syncthreads();
+    float2* t = a; a = b; b = t;
+    pad = pd;
+    Ns *= R;
+  }
+  return a;
+}
+
+// All passes of the column DFTs of a tile; returns the tile holding the result (a or b).
+template <int DIR>
+__device__ float2* gen_dft_cols(float2* a, float2* b, int L, int nr, const int8_t* rad,
+                                const float2* tw, int NB, int lnb, int T) {
+  int Ns = 1;
+  for (int p = 0; p < nr; ++p) {
+    const int R = rad[p];
+    switch (R) {
+      case 2: gpass_cols<2, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+      case 3: gpass_cols<3, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+      case 4: gpass_cols<4, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+      case 5: gpass_cols<5, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
+      default: gpass_cols<8, DIR>(a, b, L, Ns, NB, lnb, tw, T); break;
     }
     __syncthreads();
     float2* t = a; a = b; b = t;
@@ -195,7 +224,7 @@ __global__ void __launch_bounds__(512) k_gen_col_forward(GenParams q) {
       a[e] = z;
     }
     __syncthreads();
-    const float2* r = gen_dft<true, -1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, 1, T);
+    const float2* r = gen_dft_cols<-1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, T);
     float2* y = q.ybuf + (G.yoff - q.base_y);
     for (int e = threadIdx.x; e < M1 * NB; e += T) {
       const int k1 = e >> lnb, c = e & (NB - 1);
@@ -281,13 +310,16 @@ __global__ void __launch_bounds__(512) k_gen_col_inverse(GenParams q) {
       a[e] = c < width ? y[(int64_t)k1 * M2 + j2_0 + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const float2* r = gen_dft<true, +1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, 1, T);
+    const float2* r = gen_dft_cols<+1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, T);
     gen_scatter<NC>(q, d, j2_0, width, reinterpret_cast<const float*>(r), NB, lnb, T);
     __syncthreads();
   }
 }
 
 // ---------------------------------------------------- kernel B: rows, filter, inverse rows
+// A job is either one row that pairs with itself (k1 = 0, or k1 = M1/2 for even M1) or
+// `count` consecutive pairs of rows (k1, M1 - k1), k1 = first .. first + count - 1; tile
+// sequence 2j holds row first + j and sequence 2j + 1 its partner.
 __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   extern __shared__ float2 gsm[];
   __shared__ double red[32];
@@ -295,8 +327,7 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   const int mode = q.a.mode;
   const bool fwd = mode != kRowPcgRhs;
   const bool inv = mode == kRowMessenger || mode == kRowPcgApply || mode == kRowPcgRhs;
-  const bool spec_out = mode == kRowSpectrum || mode == kRowNatural;
-  const bool load_d = !spec_out && mode != kRowPcgApply;
+  const bool load_d = mode != kRowSpectrum && mode != kRowNatural && mode != kRowPcgApply;
   double lambda = q.a.lambda;
   double* chi2 = q.a.chi2;
   if (q.a.lam_table) {          // graph mode: schedule and chi^2 slot from device memory
@@ -307,24 +338,28 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   const bool want_x2 = chi2 != nullptr &&
                        (mode == kRowMessenger || mode == kRowChi2 || mode == kRowPcgRhs);
   for (int64_t job = blockIdx.x; job < q.n_items; job += gridDim.x) {
-    const int2 it = __ldg(q.items + q.base + job);
+    const int4 it = __ldg(q.jobs + q.base + job);
     const GenChunk& G = q.rec[it.x];
     const ChunkDesc d = G.d;
     const int c = G.c;
     const int M1 = d.M1, M2 = d.M2, M = d.M;
-    const int rA = it.y;
-    const int rB = rA == 0 ? 0 : M1 - rA;
-    const bool self = rA == rB;
-    const int nseq = self ? 1 : 2;
+    const bool self = it.z == 0;
+    const int first = it.y, count = self ? 1 : it.z;
+    const int nseq = self ? 1 : 2 * count;
+    const FastDiv fm2(M2);
+    auto row_of = [&](int sq) { return self ? first : ((sq & 1) ? M1 - first - (sq >> 1) : first + (sq >> 1)); };
     float2* y = q.ybuf + (G.yoff - q.base_y);
     float2* a = gsm;
-    float2* b = gsm + 2 * M2;
+    float2* b = gsm + q.tile;
+    bool pz = false;
     float2* z = a;
     if (fwd) {
-      for (int e = threadIdx.x; e < nseq * M2; e += T)
-        a[e] = y[(int64_t)(e < M2 ? rA : rB) * M2 + (e < M2 ? e : e - M2)];
+      for (int e = threadIdx.x; e < nseq * M2; e += T) {
+        const int sq = fm2.div(e), p = e - sq * M2;
+        a[e] = y[(int64_t)row_of(sq) * M2 + p];
+      }
       __syncthreads();
-      z = gen_dft<false, -1>(a, b, M2, G.nr2, G.rad2, G.tw_row, 0, 0, nseq, T);
+      z = gen_dft_rows<-1>(a, b, pz, M2, G.nr2, G.rad2, G.tw_row, nseq, T);
     }
     float2* other = z == a ? b : a;
 
@@ -354,10 +389,12 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
     if (d.cplx) {
       // every frequency on its own: k = r + M1 p for element p of row r
       for (int e = threadIdx.x; e < nseq * M2; e += T) {
-        const int r = e < M2 ? rA : rB, p = e < M2 ? e : e - M2;
+        const int sq = fm2.div(e), p = e - sq * M2;
+        const int r = row_of(sq);
         const int slot = r * M2 + p;
         const int k = r + M1 * p;
-        const float2 X = fwd ? z[e] : make_float2(0.f, 0.f);
+        const int ze = lay(e, pz);
+        const float2 X = fwd ? z[ze] : make_float2(0.f, 0.f);
         if (mode == kRowSpectrum) { q.dtab[d.spec + slot] = X; continue; }
         if (mode == kRowNatural) {
           if (2 * k <= d.n) q.a.natural[d.nat + k] = X;
@@ -369,20 +406,30 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
           const float2 er = csub(D, X);
           x2 += __fdividef(er.x * er.x + er.y * er.y, nbv + cn);
         }
-        if (inv) z[e] = filt(X, D, nbv);
+        if (inv) z[ze] = filt(X, D, nbv);
       }
     } else {
-      // pairs (k, M - k): element p of row rA with partner qi of row rB (or of row rA)
-      const float2 wa = __ldg(&G.pack_a[rA]);
-      for (int p = threadIdx.x; p < M2; p += T) {
-        int qs = 1, qi = M2 - 1 - p;
+      // pairs (k, M - k): element p of a row with its partner qi in the partner row (or in
+      // the same row for a self-paired row)
+      const int npair = self ? M2 : count * M2;
+      for (int e = threadIdx.x; e < npair; e += T) {
+        int j = 0, p = e, qi, rA, rB, sA, sB;
         if (self) {
-          qs = 0;
+          rA = rB = first;
+          sA = sB = 0;
           qi = rA == 0 ? (p == 0 ? 0 : M2 - p) : M2 - 1 - p;
           if (p > qi) continue;
+        } else {
+          j = fm2.div(e);
+          p = e - j * M2;
+          rA = first + j;
+          rB = M1 - rA;
+          sA = 2 * j;
+          sB = 2 * j + 1;
+          qi = M2 - 1 - p;
         }
-        const int sk = rA * M2 + p, sp = (qs ? rB : rA) * M2 + qi;
-        const int ek = p, ep = qs * M2 + qi;             // positions in the tile
+        const int sk = rA * M2 + p, sp = rB * M2 + qi;                 // spectrum slots
+        const int ek = lay(sA * M2 + p, pz), ep = lay(sB * M2 + qi, pz);   // tile positions
         const float2 Zk = fwd ? z[ek] : make_float2(0.f, 0.f);
         const float2 Zp = fwd ? z[ep] : make_float2(0.f, 0.f);
         if (rA == 0 && p == 0) {
@@ -402,16 +449,16 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
           if (!inv) continue;
           const float Y0 = filt(make_float2(X0, 0.f), make_float2(D.x, 0.f), n0).x;
           const float YM = filt(make_float2(XM, 0.f), make_float2(D.y, 0.f), nM).x;
-          z[0] = make_float2(Y0 + YM, Y0 - YM);
+          z[ek] = make_float2(Y0 + YM, Y0 - YM);
           continue;
         }
-        const float2 w = cmul(wa, __ldg(&G.pack_b[p]));   // w_{2M}^k, k = rA + M1 p
+        const float2 w = cmul(__ldg(&G.pack_a[rA]), __ldg(&G.pack_b[p]));   // w_{2M}^k
         const float2 E = cscale(cadd(Zk, cconj(Zp)), 0.5f);
         const float2 O = cscale(mul_i<-1>(csub(Zk, cconj(Zp))), 0.5f);
         const float2 wO = cmul(w, O);
         const float2 Xk = cadd(E, wO);
         const float2 Xp = cconj(csub(E, wO));
-        const bool same = qs == 0 && qi == p;           // k == M - k
+        const bool same = self && qi == p;                 // k == M - k
         if (mode == kRowSpectrum) {
           q.dtab[d.spec + sk] = Xk;
           if (!same) q.dtab[d.spec + sp] = Xp;
@@ -437,12 +484,8 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
         const float2 Yp = filt(Xp, Dp, np);
         // Z'_k = (Y_k + conj Y_p) + i conj(w) (Y_k - conj Y_p)
         // Z'_p = (Y_p + conj Y_k) - i w (Y_p - conj Y_k)
-        const float2 Zk2 = cadd(cadd(Yk, cconj(Yp)), mul_i<+1>(cmulc(csub(Yk, cconj(Yp)), w)));
-        z[ek] = Zk2;
-        if (!same) {
-          const float2 Zp2 = csub(cadd(Yp, cconj(Yk)), mul_i<+1>(cmul(w, csub(Yp, cconj(Yk)))));
-          z[ep] = Zp2;
-        }
+        z[ek] = cadd(cadd(Yk, cconj(Yp)), mul_i<+1>(cmulc(csub(Yk, cconj(Yp)), w)));
+        if (!same) z[ep] = csub(cadd(Yp, cconj(Yk)), mul_i<+1>(cmul(w, csub(Yp, cconj(Yk)))));
       }
     }
     if (want_x2) {
@@ -452,17 +495,18 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
       if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x2;
       __syncthreads();
       if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int w = 0; w < T / 32; ++w) s += red[w];
-        atomicAdd(chi2, s / (double)d.n);
+        double sum = 0.0;
+        for (int w = 0; w < T / 32; ++w) sum += red[w];
+        atomicAdd(chi2, sum / (double)d.n);
       }
     }
     if (inv) {
       __syncthreads();
-      const float2* r = gen_dft<false, +1>(z, other, M2, G.nr2, G.rad2, G.tw_row, 0, 0, nseq, T);
+      const float2* r = gen_dft_rows<+1>(z, other, pz, M2, G.nr2, G.rad2, G.tw_row, nseq, T);
       for (int e = threadIdx.x; e < nseq * M2; e += T) {
-        const int row = e < M2 ? rA : rB, p = e < M2 ? e : e - M2;
-        y[(int64_t)row * M2 + p] = cmulc(r[e], gen_tw_big(G, row * p));
+        const int sq = fm2.div(e), p = e - sq * M2;
+        const int row = row_of(sq);
+        y[(int64_t)row * M2 + p] = cmulc(r[lay(e, pz)], gen_tw_big(G, row * p));
       }
     }
     __syncthreads();
@@ -540,11 +584,19 @@ cudaError_t launch_gen_col_inverse(const mm_plan_s* p, const Batch& b, cudaStrea
 }
 
 cudaError_t launch_gen_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
-  GenParams q = gen_params(p, b, p->gen_rtab, p->h_gen_rjob);
+  GenParams q = gen_params(p, b, nullptr, p->h_gen_rjob);
+  q.jobs = p->gen_rtab;
   q.a = a;
-  int m1, m2;
-  gen_extent(p, b, &m1, &m2);
-  const size_t smem = 4 * sizeof(float2) * (size_t)m2;
+  // the largest job of the batch (sequences x row length), in the padded layout
+  int emax = 1;
+  for (int i = b.first; i < b.first + b.count; ++i) {
+    const ChunkDesc& d = p->h_desc[p->h_gen_chunks[i]];
+    const int e = gen_row_pairs(d.M1, d.M2) * 2 * d.M2;
+    if (e > emax) emax = e;
+    if (d.M2 > emax) emax = d.M2;
+  }
+  q.tile = emax + (emax >> 4) + 1;
+  const size_t smem = 2 * sizeof(float2) * (size_t)q.tile;
   return gen_launch(k_gen_row, p->gen_tune.row_threads, smem, q.n_items, q, st);
 }
 

@@ -55,6 +55,15 @@ constexpr int kMaxGroups = 128;
 // Column / row limits of the general path (shared memory of one CTA: two ping-pong tiles).
 constexpr int kGenMaxM1 = 512;
 constexpr int kGenMaxM2 = 4096;
+// Row jobs of the general path gather pairs of rows (k1, M1 - k1) up to about this many
+// elements, so that each Stockham pass has several butterflies per thread.
+constexpr int kGenRowElems = 4096;
+__host__ __device__ inline int gen_row_pairs(int M1, int M2) {
+  const int h = (M1 - 1) / 2;                 // rows 1 .. h pair with M1 - 1 .. M1 - h
+  int n = kGenRowElems / (2 * M2);
+  if (n < 1) n = 1;
+  return h < n ? h : n;
+}
 
 // A batch: `count` consecutive chunks of one group whose four-step intermediates share the
 // ybuf slot.  Batches are sized so the slot (default 32 MB) stays resident in L2 between
@@ -148,7 +157,7 @@ struct mm_plan_s {
   int* h_gen_chunks;
   mm::GenChunk* gen_rec;   // [n_gen] device records
   int2* gen_ctab;          // column tiles: (general index, first column), capacity gen_ccap
-  int2* gen_rtab;          // row jobs: (general index, row k1)
+  int4* gen_rtab;          // row jobs: (general index, first row, pairs or 0 for a self-paired row)
   int64_t gen_ccap;
   mm::Group* d_groups;
   mm::GenTune gen_tune;
