@@ -193,6 +193,26 @@ mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, void* state, 
 mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev,
                   void* stream);
 
+/* Plateau-driven cooling (Sec. 3.1: at each lambda chi^2 falls to a plateau, then lambda is
+ * lowered), run entirely on the device as ONE CUDA graph launch: a conditional WHILE node
+ * whose body is one messenger iteration plus a one-thread controller.  The run starts with
+ * one lambda = inf step from map_inout, then walks levels[0..n_levels) (finite, >= 1, not
+ * increasing; the last is normally 1).  chi^2 of the map entering iteration j is known once
+ * iteration j runs, so after iteration i the newest measured decrease is that of iteration
+ * i-2, r = (chi2[i-2] - chi2[i-1]) / chi2[i-1]; the level advances when at least
+ * min_per_level (>= 2) of its iterations have run, iteration i-2 ran at this level and
+ * r < rel_tol, or when max_per_level of its iterations have run (not applied to the last
+ * level).  The loop ends when the last level would advance or after max_iter iterations.
+ * Outputs (device): chi2_out[max_iter] (chi^2 at lambda = 1 of each iteration's input map,
+ * zero beyond the run), lambda_out[max_iter] (lambda of each iteration, zero beyond),
+ * *n_done (int, iterations run), map_inout (the final map).  Asynchronous on `stream`;
+ * read *n_done after synchronising.  The graph is built on first use (and again after
+ * mm_set_tune / mm_autotune). */
+mm_status mm_messenger_adaptive(mm_plan p, const double* levels, int n_levels, double rel_tol,
+                                int min_per_level, int max_per_level, int max_iter,
+                                double* map_inout, double* chi2_out, double* lambda_out,
+                                int* n_done, void* stream);
+
 /* chi^2 per Fourier mode (the online convergence diagnostic of Sec. 3.1 / Sec. 4.1):
  * modes[off_c + k] = |d~_k - (P m)~_k|^2 / (n_c N'_c(f_k)), k = 0..n_c/2 for every chunk c
  * (off_c = sum of (n_c'/2 + 1) over the chunks before c; device float64), with N' = N +

@@ -235,6 +235,47 @@ def run_messenger(prob, lambdas, m0=None):
     return m, np.array(chis)
 
 
+def run_messenger_adaptive(prob, levels, rel_tol, min_per_level, max_per_level, max_iter,
+                           m0=None):
+    """Cooling driven by the chi^2 plateaus of Sec. 3.1: one lambda = inf step, then the
+    levels in order, moving on once chi^2 has stopped falling at the current level.
+
+    Reading of "plateau" (the paper describes it without a rule): chi^2 of the map entering
+    iteration j is known once iteration j runs, so after iteration i the newest measured
+    decrease is that of iteration i - 2, (chi2_{i-2} - chi2_{i-1}) / chi2_{i-1}.  The level
+    advances when at least min_per_level of its iterations have run, iteration i - 2 ran at
+    this level and that relative decrease is below rel_tol, or when max_per_level of its
+    iterations have run (not applied to the last level, lambda = 1).  The run ends when the
+    last level would advance, or after max_iter iterations.  Returns (final map, chi^2 of
+    each iteration's input map, lambda of each iteration)."""
+    m = np.zeros((prob.npix, prob.ncomp)) if m0 is None else np.array(m0, dtype=np.float64)
+    chis, lams = [], []
+    lam = np.inf
+    level, start = -1, 0
+    while True:
+        m, x2 = messenger_step(prob, m, lam)
+        chis.append(x2)
+        lams.append(lam)
+        it = len(chis)                         # iterations done
+        if it >= max_iter:
+            break
+        if level < 0:
+            level, start = 0, it
+        else:
+            count = it - start
+            plateau = False
+            if it - 2 >= start:
+                rel = (chis[it - 2] - chis[it - 1]) / chis[it - 1]
+                plateau = rel < rel_tol
+            last = level == len(levels) - 1
+            if count >= min_per_level and plateau or (not last and count >= max_per_level):
+                if last:
+                    break
+                level, start = level + 1, it
+        lam = levels[level]
+    return m, np.array(chis), np.array(lams)
+
+
 # ------------------------------------------------------------------------------- PCG
 def apply_A(prob, m):
     """A m = P^T N^-1 P m with N^-1 applied per chunk as 1/N(f_k) on the Fourier modes."""

@@ -53,6 +53,8 @@ SIGNATURES = {
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
     "mm_chi2_modes": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "mm_autotune": (ctypes.c_int, [_vp, _vp]),
+    "mm_messenger_adaptive": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
     "mm_set_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
     "mm_get_tune": (ctypes.c_int, [_vp, _ip, _ip, _ip, _ip]),
     "mm_apply_pointing": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -270,6 +272,23 @@ class Plan:
         _check("mm_chi2_modes", load().mm_chi2_modes(self._h, _ptr(map_in), float(lam), _ptr(total),
                                                      _ptr(modes), _stream(stream)))
         return total, modes
+
+    def messenger_adaptive(self, map_inout, levels, rel_tol: float, min_per_level: int = 2,
+                           max_per_level: int = 20, max_iter: int = 400, stream=None):
+        """Plateau-driven cooling in one graph launch; returns (chi2 [n], lambda [n], n) with
+        n the iterations run (synchronises the stream to read n)."""
+        import torch
+        lv = np.ascontiguousarray(levels, dtype=np.float64)
+        chi = torch.zeros(max_iter, dtype=torch.float64, device=self.device)
+        lam = torch.zeros(max_iter, dtype=torch.float64, device=self.device)
+        nd = torch.zeros(1, dtype=torch.int32, device=self.device)
+        _check("mm_messenger_adaptive", load().mm_messenger_adaptive(
+            self._h, lv.ctypes.data_as(_dp), len(lv), float(rel_tol), int(min_per_level),
+            int(max_per_level), int(max_iter), _ptr(map_inout), _ptr(chi), _ptr(lam), _ptr(nd),
+            _stream(stream)))
+        torch.cuda.current_stream(self.device).synchronize() if stream is None else stream.synchronize()
+        n = int(nd.item())
+        return chi[:n], lam[:n], n
 
     def autotune(self, stream=None):
         """Measure and keep the fastest schedule of the general-length kernels."""

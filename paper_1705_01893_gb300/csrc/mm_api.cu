@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <map>
 #include <tuple>
 #include <mutex>
@@ -171,7 +172,7 @@ static size_t tw_count(int M, int M1, int M2, bool general) {
 struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
       ybuf, scal, tpix, tcos, tsin, lam, iter, map64, groups, gen, gen_rec, gen_ctab, gen_rtab,
-      total, ybytes;
+      adapt, total, ybytes;
   int64_t gen_ccap, gen_rcap;
   int lam_cap;
   int n_groups;
@@ -319,6 +320,7 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->gen_rec = take(sizeof(GenChunk) * ngen);
   L->gen_ctab = take(sizeof(int2) * ctiles);
   L->gen_rtab = take(sizeof(int4) * rjobs);
+  L->adapt = take(sizeof(AdaptState));
   L->total = o;
   return MM_OK;
 }
@@ -952,6 +954,8 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   p->iter = reinterpret_cast<int*>(ws + L.iter);
   p->chi2_base = reinterpret_cast<double**>(ws + L.iter + 64);
   p->map64 = reinterpret_cast<double*>(ws + L.map64);
+  p->adapt_exec = nullptr;
+  p->adapt_st = ws + L.adapt;
   p->scal = reinterpret_cast<double*>(ws + L.scal);
   p->params = reinterpret_cast<double*>(ws + L.params);
   p->tpix = reinterpret_cast<int32_t*>(ws + L.tpix);
@@ -1111,6 +1115,7 @@ extern "C" void mm_plan_destroy(mm_plan p) {
   delete[] p->h_chunk_group;
   delete[] p->h_batches;
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  if (p->adapt_exec) cudaGraphExecDestroy(p->adapt_exec);
   if (p->graph_stream) cudaStreamDestroy(p->graph_stream);
   delete p;
 }
@@ -1336,17 +1341,13 @@ extern "C" mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double 
 
 // Capture one messenger iteration (every batch's three kernels, then the map step) as a CUDA
 // graph whose cooling parameter and chi^2 slot come from device memory.
-static mm_status capture_iteration_graph(mm_plan p) {
-  if (p->graph_exec) return MM_OK;
-  if (!p->graph_stream)
-    MM_CUDA(cudaStreamCreateWithFlags(&p->graph_stream, cudaStreamNonBlocking));
-  cudaStream_t s = p->graph_stream;
+// The kernels of one graph-mode iteration (lambda and the chi^2 slot from device memory,
+// the iteration counter advanced by the map step) launched on s.
+static cudaError_t launch_iteration(mm_plan p, cudaStream_t s) {
   RowArgs a{kRowMessenger, 1.0, nullptr, nullptr};
   a.lam_table = p->lam_table;
   a.iter = p->iter;
   a.chi2_base = p->chi2_base;
-  // relaxed: the launchers may query occupancy / set kernel attributes on first use
-  MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < p->n_batches && e == cudaSuccess; ++b) {
     const Batch& B = p->h_batches[b];
@@ -1354,13 +1355,22 @@ static mm_status capture_iteration_graph(mm_plan p) {
     if ((e = launch_row(p, B, a, s)) != cudaSuccess) break;
     e = launch_col_inverse(p, B, s);
   }
-  if (e == cudaSuccess) {
-    if (p->ncomp == 3)
-      k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, p->map64, p->iter);
-    else
-      k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, p->map64, p->iter);
-    e = cudaGetLastError();
-  }
+  if (e != cudaSuccess) return e;
+  if (p->ncomp == 3)
+    k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, p->map64, p->iter);
+  else
+    k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, p->map64, p->iter);
+  return cudaGetLastError();
+}
+
+static mm_status capture_iteration_graph(mm_plan p) {
+  if (p->graph_exec) return MM_OK;
+  if (!p->graph_stream)
+    MM_CUDA(cudaStreamCreateWithFlags(&p->graph_stream, cudaStreamNonBlocking));
+  cudaStream_t s = p->graph_stream;
+  // relaxed: the launchers may query occupancy / set kernel attributes on first use
+  MM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+  cudaError_t e = launch_iteration(p, s);
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(s, &graph);
   if (e != cudaSuccess || ec != cudaSuccess) {
@@ -1375,6 +1385,138 @@ static mm_status capture_iteration_graph(mm_plan p) {
     mm_set_error("graph instantiate failed: %s", cudaGetErrorString(e));
     return MM_ERR_CUDA;
   }
+  return MM_OK;
+}
+
+// Plateau-driven cooling (Sec. 3.1), one thread after each iteration's map step: decides
+// the next iteration's lambda from the chi^2 of the maps entering the last two iterations
+// and ends the loop (condition 0) after the last level's plateau or max_iter iterations.
+__global__ void k_adapt(AdaptState* __restrict__ st, double* __restrict__ lam_table,
+                        const int* __restrict__ iter, cudaGraphConditionalHandle h) {
+  if (threadIdx.x != 0) return;
+  const int it = *iter;                    // iterations done
+  bool go = it < st->max_iter;
+  if (go) {
+    if (st->level < 0) {
+      st->level = 0;
+      st->start = it;
+    } else {
+      const int count = it - st->start;
+      bool plateau = false;
+      if (it - 2 >= st->start) {
+        const double rel = (st->chi2[it - 2] - st->chi2[it - 1]) / st->chi2[it - 1];
+        plateau = rel < st->rel_tol;
+      }
+      const bool last = st->level == st->n_levels - 1;
+      if ((count >= st->min_per && plateau) || (!last && count >= st->max_per)) {
+        if (last) {
+          go = false;
+        } else {
+          st->level += 1;
+          st->start = it;
+        }
+      }
+    }
+  }
+  if (go) {
+    const double lam = st->levels[st->level];
+    lam_table[it] = lam;
+    st->lambda_out[it] = lam;
+  } else {
+    st->n_done = it;
+  }
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
+// One graph: a WHILE conditional node whose body is one iteration plus the controller.
+static mm_status build_adaptive_graph(mm_plan p) {
+  if (p->adapt_exec) return MM_OK;
+  if (!p->graph_stream)
+    MM_CUDA(cudaStreamCreateWithFlags(&p->graph_stream, cudaStreamNonBlocking));
+  cudaStream_t s = p->graph_stream;
+  cudaGraph_t g = nullptr;
+  MM_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  // the parameter union has no default constructor: zero-filled storage stands in for it
+  alignas(cudaGraphNodeParams) unsigned char np_buf[sizeof(cudaGraphNodeParams)];
+  memset(np_buf, 0, sizeof(np_buf));
+  cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(np_buf);
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      cudaError_t el = launch_iteration(p, s);
+      if (el == cudaSuccess) {
+        k_adapt<<<1, 32, 0, s>>>(static_cast<AdaptState*>(p->adapt_st), p->lam_table, p->iter, h);
+        el = cudaGetLastError();
+      }
+      cudaGraph_t out = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(s, &out);
+      e = el != cudaSuccess ? el : ec;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&p->adapt_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    p->adapt_exec = nullptr;
+    mm_set_error("adaptive graph: %s", cudaGetErrorString(e));
+    return MM_ERR_CUDA;
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_messenger_adaptive(mm_plan p, const double* levels, int n_levels,
+                                           double rel_tol, int min_per_level, int max_per_level,
+                                           int max_iter, double* map_inout, double* chi2_out,
+                                           double* lambda_out, int* n_done, void* stream) {
+  MM_ARG(p != nullptr && levels != nullptr && map_inout != nullptr && chi2_out != nullptr &&
+         lambda_out != nullptr && n_done != nullptr, "NULL argument");
+  MM_ARG(n_levels >= 1 && n_levels <= kMaxLevels, "n_levels must be in [1, %d]", kMaxLevels);
+  MM_ARG(max_iter >= 1 && max_iter <= p->lam_cap, "max_iter must be in [1, %d]", p->lam_cap);
+  MM_ARG(min_per_level >= 2 && max_per_level >= min_per_level,
+         "need 2 <= min_per_level <= max_per_level");
+  MM_ARG(!isnan(rel_tol), "rel_tol is NaN");
+  for (int j = 0; j < n_levels; ++j) {
+    MM_ARG(isfinite(levels[j]) && levels[j] >= 1.0, "levels[%d] must be finite and >= 1", j);
+    MM_ARG(j == 0 || levels[j] <= levels[j - 1], "levels must not increase");
+  }
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  mm_status st = build_adaptive_graph(p);
+  if (st != MM_OK) return st;
+  cudaStream_t s = S(stream);
+  AdaptState h;
+  memset(&h, 0, sizeof(h));
+  h.level = -1;
+  h.n_levels = n_levels;
+  h.min_per = min_per_level;
+  h.max_per = max_per_level;
+  h.max_iter = max_iter;
+  h.rel_tol = rel_tol;
+  h.chi2 = chi2_out;
+  h.lambda_out = lambda_out;
+  for (int j = 0; j < n_levels; ++j) h.levels[j] = levels[j];
+  const double inf = INFINITY;
+  MM_CUDA(cudaMemcpyAsync(p->adapt_st, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemcpyAsync(p->lam_table, &inf, sizeof(double), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemsetAsync(p->iter, 0, sizeof(int), s));
+  MM_CUDA(cudaMemcpyAsync(p->chi2_base, &chi2_out, sizeof(double*), cudaMemcpyHostToDevice, s));
+  MM_CUDA(cudaMemsetAsync(chi2_out, 0, sizeof(double) * max_iter, s));
+  MM_CUDA(cudaMemsetAsync(lambda_out, 0, sizeof(double) * max_iter, s));
+  MM_CUDA(cudaMemcpyAsync(lambda_out, &inf, sizeof(double), cudaMemcpyHostToDevice, s));
+  st = load_map(p, map_inout, s);
+  if (st != MM_OK) return st;
+  MM_CUDA(cudaGraphLaunch(p->adapt_exec, s));
+  MM_CUDA(cudaMemcpyAsync(map_inout, p->map64, sizeof(double) * p->ncomp * p->n_pix,
+                          cudaMemcpyDeviceToDevice, s));
+  MM_CUDA(cudaMemcpyAsync(n_done, reinterpret_cast<char*>(p->adapt_st) + offsetof(AdaptState, n_done),
+                          sizeof(int), cudaMemcpyDeviceToDevice, s));
   return MM_OK;
 }
 
@@ -1558,6 +1700,10 @@ static mm_status apply_tune(mm_plan p, const GenTune& t, cudaStream_t s) {
   if (p->graph_exec) {            // the captured iteration holds the old launch shapes
     cudaGraphExecDestroy(p->graph_exec);
     p->graph_exec = nullptr;
+  }
+  if (p->adapt_exec) {
+    cudaGraphExecDestroy(p->adapt_exec);
+    p->adapt_exec = nullptr;
   }
   return MM_OK;
 }

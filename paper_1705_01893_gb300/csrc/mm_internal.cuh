@@ -74,6 +74,19 @@ struct Batch {
   int count;
 };
 
+// State of the plateau-driven cooling controller (device memory, one per plan).
+constexpr int kMaxLevels = 64;
+struct AdaptState {
+  int level;          // current level, -1 during the lambda = inf step
+  int start;          // iterations done when the current level began
+  int n_done;         // iterations run, set when the loop ends
+  int n_levels, min_per, max_per, max_iter;
+  double rel_tol;
+  double* chi2;       // [max_iter] chi^2 of each iteration's input map
+  double* lambda_out; // [max_iter] lambda of each iteration
+  double levels[kMaxLevels];
+};
+
 // Schedule of the general path's persistent kernels: tile width, threads and radix order
 // (picked per plan by measurement, see mm_autotune).
 struct GenTune {
@@ -141,6 +154,9 @@ struct mm_plan_s {
   int* iter;           // device iteration counter
   double** chi2_base;  // device pointer slot: chi^2 output array or NULL
   double* map64;       // device FP64 copy of the current map (graph mode)
+  // adaptive cooling: graph with a device-side loop (conditional WHILE node) and its state
+  cudaGraphExec_t adapt_exec;
+  void* adapt_st;      // device mm::AdaptState followed by the level table
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;

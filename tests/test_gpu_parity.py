@@ -365,3 +365,33 @@ def test_chi2_per_mode():
         got = modes.cpu().numpy()
         assert rel(got, ref) <= 1e-5
         assert abs(tot.item() - O.chi2(prob, m, lam)) <= 1e-5 * O.chi2(prob, m, lam)
+
+
+@pytest.mark.parametrize("cfg", ["iqu32", "uneven"])
+def test_adaptive_cooling_matches_oracle(cfg):
+    """Plateau-driven cooling as one graph launch (device-side WHILE loop and controller)
+    against the oracle's rule.  The test first checks that no plateau decision of the oracle
+    run lies within 1e-2 (relative) of the tolerance, so FP32 rounding of chi^2 cannot flip
+    one; then the lambda sequences must be identical, the maps within 1e-4 (rms) and chi^2
+    within 1e-5."""
+    s = synth.config_iqu(32, 4, 1 << 14, 36) if cfg == "iqu32" else \
+        synth.config_uneven(32, 5, 2000, 12000, seed=17050112)
+    prob = O.problem_from_synth(s)
+    lm = O.lambda_max(prob)
+    L = 8
+    levels = [lm ** ((L - 1 - j) / (L - 1)) for j in range(L)]
+    tol, mn, mx, cap = 2e-3, 2, 12, 150
+    m_ref, chi_ref, lam_ref = O.run_messenger_adaptive(prob, levels, tol, mn, mx, cap)
+    rel_dec = (chi_ref[:-1] - chi_ref[1:]) / chi_ref[1:]
+    assert np.all(np.abs(rel_dec - tol) > 1e-2 * tol), "borderline plateau decision"
+    plan = gpu_plan(s)
+    m = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    chi, lam, n = plan.messenger_adaptive(m, levels, tol, mn, mx, cap)
+    lam_g = lam.cpu().numpy()
+    assert n == len(lam_ref)
+    assert np.array_equal(np.isinf(lam_g), np.isinf(lam_ref))
+    assert np.allclose(lam_g[1:], lam_ref[1:], rtol=1e-15, atol=0)
+    mg = m.cpu().numpy()
+    rms = np.sqrt(np.mean((mg - m_ref) ** 2)) / np.sqrt(np.mean(m_ref ** 2))
+    assert rms <= 1e-4
+    assert np.max(np.abs(chi.cpu().numpy() - chi_ref) / chi_ref) <= 1e-5

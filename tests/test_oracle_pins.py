@@ -303,3 +303,32 @@ def test_synth_uneven_and_angled_rasters():
     p = synth.raster_angled(8, 2, 32, 0.0, 4)
     assert np.array_equal(p[:16], 8 * 4 + np.arange(16) // 2)        # row 4, left to right
     assert np.array_equal(p[16:32], 8 * 4 + 7 - np.arange(16) // 2)  # back, right to left
+
+
+def test_adaptive_cooling_bookkeeping_and_target():
+    """Plateau-driven cooling (Sec. 3.1).  With no plateau ever detected it is exactly the
+    fixed schedule (one lambda = inf step, max_per_level iterations per level, the last level
+    until max_iter); with every test a plateau each level runs min_per_level = 2 iterations;
+    with a small tolerance it ends within 1e-6 of the brute-force GLS chi^2 (Eq. 2)."""
+    prob = O.problem_from_synth(tiny(seed=31))
+    lm = O.lambda_max(prob)
+    L, k = 5, 3
+    levels = [lm ** ((L - 1 - j) / (L - 1)) for j in range(L)]
+    fixed = O.cooling_schedule(lm, L, k)
+    m_a, chi_a, lam_a = O.run_messenger_adaptive(prob, levels, -np.inf, 2, k, len(fixed))
+    m_f, chi_f = O.run_messenger(prob, fixed)
+    assert np.array_equal(lam_a, fixed)
+    assert np.array_equal(m_a, m_f) and np.array_equal(chi_a, chi_f)
+    _, _, lam_b = O.run_messenger_adaptive(prob, levels, np.inf, 2, 50, 1000)
+    assert np.array_equal(lam_b, [np.inf] + [l for l in levels for _ in range(2)])
+    m_c, chi_c, lam_c = O.run_messenger_adaptive(prob, levels, 1e-9, 2, 200, 4000)
+    assert lam_c[-1] == 1.0 and len(lam_c) < 4000
+    ref = O.dense_solve(prob)
+    c_ref = O.dense_chi2(prob, ref)
+    assert (O.chi2(prob, m_c) - c_ref) / c_ref < 1e-6
+    # every level change follows a measured decrease below the tolerance or the cap
+    starts = [i for i in range(2, len(lam_c)) if lam_c[i] != lam_c[i - 1]]
+    for s in starts:
+        run = s - max(j for j in range(1, s) if lam_c[j] != lam_c[j - 1] or j == 1)
+        rel = (chi_c[s - 2] - chi_c[s - 1]) / chi_c[s - 1]
+        assert rel < 1e-9 or run >= 200
