@@ -71,15 +71,21 @@ struct FastDiv {
 __device__ __forceinline__ int lay(int e, bool pad) { return pad ? e + (e >> 4) : e; }
 
 // ----------------------------------------------------------------- Stockham passes
-// Column tiles: element (j, c) of the tile's NB interleaved sequences at j * NB + c.
+// Column tiles: element (j, c) of the tile's NB interleaved sequences at j * NB + c.  A
+// thread keeps its column c and walks butterflies i = i0, i0 + T/NB, ...; k = i mod Ns is
+// advanced by the same step instead of being recomputed.
 template <int R, int DIR>
 __device__ __forceinline__ void gpass_cols(const float2* src, float2* dst, int L, int Ns, int NB,
                                            int lnb, const float2* __restrict__ tw, int T) {
   const int nb = L / R, mul = L / (Ns * R);
+  const int c = threadIdx.x & (NB - 1);
+  const int di = T >> lnb;
+  int i = threadIdx.x >> lnb;
+  if (i >= nb) return;
   const FastDiv fd(Ns);
-  for (int b = threadIdx.x; b < nb * NB; b += T) {
-    const int c = b & (NB - 1), i = b >> lnb;
-    const int k = fd.mod(i);
+  int k = fd.mod(i);
+  const int dk = fd.mod(di);
+  for (; i < nb; i += di) {
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(i + r * nb) * NB + c];
@@ -94,22 +100,31 @@ __device__ __forceinline__ void gpass_cols(const float2* src, float2* dst, int L
     const int o = (i - k) * R + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[(o + r * Ns) * NB + c] = v[r];
+    k += dk;
+    if (k >= Ns) k -= Ns;
   }
 }
 
-// Row jobs: nseq contiguous sequences of length L.
-template <int R, int DIR>
-__device__ __forceinline__ void gpass_rows(const float2* src, bool ps, float2* dst, bool pd, int L,
-                                           int Ns, int nseq, const float2* __restrict__ tw, int T) {
+// Row jobs: nseq contiguous sequences of length L; PS / PD: the source / destination tile is
+// in the padded layout.  Butterfly b = sq nb + i advances by T per step as (sq, i, k) with
+// carries (nb is a multiple of Ns, so wrapping i keeps k = i mod Ns).
+template <int R, int DIR, bool PS, bool PD>
+__device__ __forceinline__ void gpass_rows(const float2* src, float2* dst, int L, int Ns, int nseq,
+                                           const float2* __restrict__ tw, int T) {
   const int nb = L / R, mul = L / (Ns * R);
-  const FastDiv fd(Ns), fs(nb);
-  for (int b = threadIdx.x; b < nb * nseq; b += T) {
-    const int sq = fs.div(b), i = b - sq * nb;
+  const int total = nb * nseq;
+  int b = threadIdx.x;
+  if (b >= total) return;
+  const FastDiv fs(nb), fd(Ns);
+  int sq = fs.div(b);
+  int i = b - sq * nb;
+  int k = fd.mod(i);
+  const int dsq = fs.div(T), di = T - dsq * nb, dk = fd.mod(di);
+  for (; b < total; b += T) {
     const int base = sq * L;
-    const int k = fd.mod(i);
     float2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[lay(base + i + r * nb, ps)];
+    for (int r = 0; r < R; ++r) v[r] = src[lay(base + i + r * nb, PS)];
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
@@ -120,29 +135,43 @@ __device__ __forceinline__ void gpass_rows(const float2* src, bool ps, float2* d
     dftR<R, DIR>(v);
     const int o = base + (i - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[lay(o + r * Ns, pd)] = v[r];
+    for (int r = 0; r < R; ++r) dst[lay(o + r * Ns, PD)] = v[r];
+    i += di;
+    sq += dsq;
+    k += dk;
+    if (k >= Ns) k -= Ns;
+    if (i >= nb) { i -= nb; ++sq; }
   }
 }
 
 // All passes of the row DFTs of a job, starting from layout `pad` in tile a; returns the
-// tile holding the result and sets `pad` to its layout.
+// tile holding the result and sets `pad` to its layout (padded after an even radix).
 template <int DIR>
 __device__ float2* gen_dft_rows(float2* a, float2* b, bool& pad, int L, int nr, const int8_t* rad,
                                 const float2* tw, int nseq, int T) {
   int Ns = 1;
   for (int p = 0; p < nr; ++p) {
     const int R = rad[p];
-    const bool pd = (R & 1) == 0;
-    switch (R) {
-      case 2: gpass_rows<2, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
-      case 3: gpass_rows<3, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
-      case 4: gpass_rows<4, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
-      case 5: gpass_rows<5, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
-      default: gpass_rows<8, DIR>(a, pad, b, pd, L, Ns, nseq, tw, T); break;
+    if (pad) {
+      switch (R) {
+        case 2: gpass_rows<2, DIR, true, true>(a, b, L, Ns, nseq, tw, T); break;
+        case 3: gpass_rows<3, DIR, true, false>(a, b, L, Ns, nseq, tw, T); break;
+        case 4: gpass_rows<4, DIR, true, true>(a, b, L, Ns, nseq, tw, T); break;
+        case 5: gpass_rows<5, DIR, true, false>(a, b, L, Ns, nseq, tw, T); break;
+        default: gpass_rows<8, DIR, true, true>(a, b, L, Ns, nseq, tw, T); break;
+      }
+    } else {
+      switch (R) {
+        case 2: gpass_rows<2, DIR, false, true>(a, b, L, Ns, nseq, tw, T); break;
+        case 3: gpass_rows<3, DIR, false, false>(a, b, L, Ns, nseq, tw, T); break;
+        case 4: gpass_rows<4, DIR, false, true>(a, b, L, Ns, nseq, tw, T); break;
+        case 5: gpass_rows<5, DIR, false, false>(a, b, L, Ns, nseq, tw, T); break;
+        default: gpass_rows<8, DIR, false, true>(a, b, L, Ns, nseq, tw, T); break;
+      }
     }
     __syncthreads();
     float2* t = a; a = b; b = t;
-    pad = pd;
+    pad = (R & 1) == 0;
     Ns *= R;
   }
   return a;
