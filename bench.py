@@ -410,6 +410,29 @@ def run_gpu(args):
                    "what": "rfft of %d x %d float32 samples, complex64 out" % (len(lens), lens[0])}
         del spec
 
+    # the map-sized form m' = m_d(lambda) + F(lambda) m against the standard step, both
+    # launched stage by stage from the host: 10 and 60 iterations at one lambda separate the
+    # per-iteration cost from the one-off m_d pass of each distinct lambda
+    md_cmp = None
+    if not args.no_plain and name == WORKLOAD:
+        lam1 = float(sched[len(sched) // 2])
+        t = {}
+        for label, fn in (("standard", lambda mm, l: plan.messenger(mm, l)),
+                          ("map_sized", lambda mm, l: plan.messenger_md(mm, l))):
+            mm = m.clone()
+            fn(mm, [lam1] * 2)
+            for n_it in (10, 60):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn(mm, [lam1] * n_it)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                t[(label, n_it)] = e0.elapsed_time(e1)
+        md_cmp = {k: {"ms_per_iter": (t[(k, 60)] - t[(k, 10)]) / 50,
+                      "ms_10_iter": t[(k, 10)]} for k in ("standard", "map_sized")}
+        md_cmp["map_sized"]["ms_m_d_per_lambda"] = t[("map_sized", 10)] - \
+            10 * md_cmp["map_sized"]["ms_per_iter"]
+
     # end to end through the public call, host buffers: map in (pinned), one iteration,
     # map and chi^2 out, synchronised every step
     m_host = torch.zeros(npix, nc, dtype=torch.float64).pin_memory()
@@ -476,6 +499,7 @@ def run_gpu(args):
         "stage_loop_ms_per_step": stage_ms_step,
         "fp64_plain_ms_per_step": plain_ms,
         "fft_vs_cufft": fft_cmp,
+        "map_sized_form": md_cmp,
         "speedup_vs_fp64_plain": None if plain_ms is None else plain_ms / ms_step,
         "stage_ms_per_launch": {k: round(v, 5) for k, v in sm["avg"].items()},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": sm["achieved"], "peak": hbm,

@@ -193,6 +193,21 @@ mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, void* state, 
 mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev,
                   void* stream);
 
+/* Map-sized form of the messenger iteration (Sec. 2.1): m' = m_d(lambda) + F(lambda) m, with
+ * m_d(lambda) = W P^T T^-1 F^-1[lambda tau d~ / (lambda tau + Nbar)] formed once for every
+ * distinct lambda of the schedule (one row + column pass each, in order of first use) and
+ * F(lambda) m = W P^T T^-1 F^-1[Nbar (P m)~ / (lambda tau + Nbar)] applied each iteration, so
+ * the iterations no longer read d~.  Same result as mm_messenger_iterate up to FP32
+ * rounding.  chi2_out (device [n_iter] or NULL) receives chi^2 at lambda = 1 of each
+ * iteration's input map, assembled as d^T N^-1 d - 2 m . b + sum_k w_k |(P m)~_k|^2 /
+ * (n N_k) with b = P^T N^-1 d.  work: caller-owned device memory, 256-byte aligned, of at
+ * least mm_messenger_md_bytes(p, number of distinct lambdas) bytes (one float64
+ * [n_pix][ncomp] map per distinct lambda); MM_ERR_NOMEM if smaller.  Asynchronous on
+ * `stream`. */
+mm_status mm_messenger_md_bytes(mm_plan p, int n_levels, size_t* bytes);
+mm_status mm_messenger_iterate_md(mm_plan p, const double* lambdas, int n_iter, double* map_inout,
+                                  double* chi2_out, void* work, size_t work_bytes, void* stream);
+
 /* Plateau-driven cooling (Sec. 3.1: at each lambda chi^2 falls to a plateau, then lambda is
  * lowered), run entirely on the device as ONE CUDA graph launch: a conditional WHILE node
  * whose body is one messenger iteration plus a one-thread controller.  The run starts with

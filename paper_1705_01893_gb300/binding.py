@@ -53,6 +53,8 @@ SIGNATURES = {
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
     "mm_chi2_modes": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "mm_autotune": (ctypes.c_int, [_vp, _vp]),
+    "mm_messenger_md_bytes": (ctypes.c_int, [_vp, ctypes.c_int, _szp]),
+    "mm_messenger_iterate_md": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "mm_messenger_adaptive": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                              ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp]),
     "mm_set_tune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp]),
@@ -272,6 +274,21 @@ class Plan:
         _check("mm_chi2_modes", load().mm_chi2_modes(self._h, _ptr(map_in), float(lam), _ptr(total),
                                                      _ptr(modes), _stream(stream)))
         return total, modes
+
+    def messenger_md(self, map_inout, lambdas, chi2_out=None, stream=None):
+        """Map-sized form m' = m_d(lambda) + F(lambda) m over the schedule `lambdas` (m_d
+        formed once per distinct lambda in a work buffer allocated here)."""
+        import torch
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        n_lev = max(1, len(set(lam.tolist())))
+        nb = ctypes.c_size_t()
+        _check("mm_messenger_md_bytes", load().mm_messenger_md_bytes(self._h, n_lev, ctypes.byref(nb)))
+        work = torch.empty(int(nb.value) + 256, dtype=torch.uint8, device=self.device)
+        wp = (work.data_ptr() + 255) // 256 * 256
+        _check("mm_messenger_iterate_md", load().mm_messenger_iterate_md(
+            self._h, lam.ctypes.data_as(_dp), len(lam), _ptr(map_inout), _ptr(chi2_out), wp,
+            int(nb.value), _stream(stream)))
+        self._md_work = work   # keep alive until the stream has run the call
 
     def messenger_adaptive(self, map_inout, levels, rel_tol: float, min_per_level: int = 2,
                            max_per_level: int = 20, max_iter: int = 400, stream=None):

@@ -1292,6 +1292,143 @@ extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int 
   return MM_OK;
 }
 
+// ------------------------------------------------------- map-sized form of the iteration
+// Sec. 2.1 writes the step as m' = m_d(lambda) + F(lambda) m with
+//   m_d(lambda) = W P^T T^-1 F^-1[ lambda tau d~ / (lambda tau + Nbar) ]   (data only)
+//   F(lambda) m = W P^T T^-1 F^-1[ Nbar (P m)~ / (lambda tau + Nbar) ]     (map only).
+// m_d is formed once per distinct lambda, after which an iteration no longer reads d~.  Its
+// chi^2 (Eq. 3) is assembled without d~ as
+//   chi^2(m) = d^T N^-1 d - 2 m . b + sum_k w_k |(P m)~_k|^2 / (n N_k),  b = P^T N^-1 d,
+// the first two terms by the map step that produces m, the last by the row pass that reads
+// it.
+
+// out = m_d + W acc (m_d may be NULL); acc cleared; map4 (FP32 gather copy) and map_out
+// written when given; chi2_next (when given) receives d^T N^-1 d - 2 out . b.
+template <int NC>
+__global__ void k_bin_md(int64_t n_pix, double* __restrict__ acc, const double* __restrict__ W,
+                         const double* __restrict__ md, void* map4, double* __restrict__ map_out,
+                         const double* __restrict__ bvec, const double* __restrict__ cdd,
+                         double* __restrict__ chi2_next) {
+  __shared__ double red[32];
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double dot = 0.0;
+  if (p < n_pix) {
+    constexpr int B = NC == 3 ? 6 : 1;
+    double a[NC], w[B], m[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) { a[i] = acc[NC * p + i]; acc[NC * p + i] = 0.0; }
+#pragma unroll
+    for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
+    sym_apply<NC>(w, a, m);
+    if (md)
+#pragma unroll
+      for (int i = 0; i < NC; ++i) m[i] += md[NC * p + i];
+    if (map4) store_map4<NC>(map4, p, m);
+    if (map_out)
+#pragma unroll
+      for (int i = 0; i < NC; ++i) map_out[NC * p + i] = m[i];
+    if (chi2_next)
+#pragma unroll
+      for (int i = 0; i < NC; ++i) dot += m[i] * bvec[NC * p + i];
+  }
+  if (chi2_next == nullptr) return;
+  const double sum = block_sum(dot, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(chi2_next, -2.0 * sum);
+    if (blockIdx.x == 0) atomicAdd(chi2_next, *cdd);
+  }
+}
+
+// chi2 slot of the first iteration: d^T N^-1 d - 2 m . b for the caller's map (b is zero on
+// cut pixels).
+__global__ void k_chi2_md_start(int64_t len, const double* __restrict__ m,
+                                const double* __restrict__ bvec, const double* __restrict__ cdd,
+                                double* __restrict__ chi2) {
+  __shared__ double red[32];
+  double dot = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dot += m[i] * bvec[i];
+  const double sum = block_sum(dot, red);
+  if (threadIdx.x == 0) {
+    atomicAdd(chi2, -2.0 * sum);
+    if (blockIdx.x == 0) atomicAdd(chi2, *cdd);
+  }
+}
+
+extern "C" mm_status mm_messenger_md_bytes(mm_plan p, int n_levels, size_t* bytes) {
+  MM_ARG(p != nullptr && bytes != nullptr, "NULL argument");
+  MM_ARG(n_levels >= 1, "n_levels must be >= 1");
+  *bytes = sizeof(double) * (size_t)p->ncomp * (size_t)p->n_pix * (size_t)n_levels;
+  return MM_OK;
+}
+
+extern "C" mm_status mm_messenger_iterate_md(mm_plan p, const double* lambdas, int n_iter,
+                                             double* map_inout, double* chi2_out, void* work,
+                                             size_t work_bytes, void* stream) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  MM_ARG(n_iter >= 0, "n_iter must be >= 0");
+  MM_ARG(n_iter == 0 || lambdas != nullptr, "lambdas is NULL");
+  MM_ARG(map_inout != nullptr, "map_inout is NULL");
+  if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
+  for (int i = 0; i < n_iter; ++i)
+    MM_ARG(lambdas[i] >= 1.0 || isinf(lambdas[i]), "lambdas[%d] = %g must be >= 1 or inf", i, lambdas[i]);
+  if (n_iter == 0) return MM_OK;
+  // distinct lambdas in order of first use: one m_d map each
+  std::vector<double> lv;
+  std::vector<int> lev(n_iter);
+  for (int i = 0; i < n_iter; ++i) {
+    int j = 0;
+    while (j < (int)lv.size() && !(lv[j] == lambdas[i])) ++j;
+    if (j == (int)lv.size()) lv.push_back(lambdas[i]);
+    lev[i] = j;
+  }
+  const size_t per = sizeof(double) * (size_t)p->ncomp * (size_t)p->n_pix;
+  MM_ARG(work != nullptr && ((uintptr_t)work & 255) == 0, "work must be 256-byte aligned");
+  if (work_bytes < per * lv.size()) {
+    mm_set_error("work holds %zu m_d maps, the schedule has %zu distinct lambdas",
+                 work_bytes / per, lv.size());
+    return MM_ERR_NOMEM;
+  }
+  double* md = static_cast<double*>(work);
+  const int64_t len = p->ncomp * p->n_pix;
+  cudaStream_t s = S(stream);
+  const unsigned nbp = blocks_for(p->n_pix, 256);
+  MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * len, s));
+  for (size_t j = 0; j < lv.size(); ++j) {
+    RowArgs a{kRowMd, lv[j], nullptr, nullptr};
+    FOR_BATCHES(L_(launch_row(p, B, a, s)); L_(launch_col_inverse(p, B, s)));
+    double* out = md + (size_t)p->ncomp * p->n_pix * j;
+    if (p->ncomp == 3)
+      k_bin_md<3><<<nbp, 256, 0, s>>>(p->n_pix, p->acc, p->W, nullptr, nullptr, out, nullptr, nullptr, nullptr);
+    else
+      k_bin_md<1><<<nbp, 256, 0, s>>>(p->n_pix, p->acc, p->W, nullptr, nullptr, out, nullptr, nullptr, nullptr);
+    LAUNCHED("k_bin_md (m_d)");
+  }
+  mm_status st = load_map(p, map_inout, s);
+  if (st != MM_OK) return st;
+  if (chi2_out) {
+    MM_CUDA(cudaMemsetAsync(chi2_out, 0, sizeof(double) * n_iter, s));
+    k_chi2_md_start<<<blocks_for(len, 256) < 1024 ? blocks_for(len, 256) : 1024, 256, 0, s>>>(
+        len, map_inout, p->bvec, p->scal + kScalCdd, chi2_out);
+    LAUNCHED("k_chi2_md_start");
+  }
+  for (int it = 0; it < n_iter; ++it) {
+    RowArgs a{kRowMessengerF, lambdas[it], chi2_out ? chi2_out + it : nullptr, nullptr};
+    FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
+                L_(launch_col_inverse(p, B, s)));
+    const double* mdl = md + (size_t)p->ncomp * p->n_pix * lev[it];
+    double* mo = it == n_iter - 1 ? map_inout : nullptr;
+    double* cn = chi2_out && it + 1 < n_iter ? chi2_out + it + 1 : nullptr;
+    if (p->ncomp == 3)
+      k_bin_md<3><<<nbp, 256, 0, s>>>(p->n_pix, p->acc, p->W, mdl, p->map4, mo, p->bvec, p->scal + kScalCdd, cn);
+    else
+      k_bin_md<1><<<nbp, 256, 0, s>>>(p->n_pix, p->acc, p->W, mdl, p->map4, mo, p->bvec, p->scal + kScalCdd, cn);
+    LAUNCHED("k_bin_md");
+  }
+  return MM_OK;
+}
+
 extern "C" mm_status mm_plan_batches(mm_plan p, int* n_batches) {
   MM_ARG(p != nullptr && n_batches != nullptr, "NULL argument");
   *n_batches = p->n_batches;

@@ -354,9 +354,11 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   __shared__ double red[32];
   const int T = blockDim.x;
   const int mode = q.a.mode;
-  const bool fwd = mode != kRowPcgRhs;
-  const bool inv = mode == kRowMessenger || mode == kRowPcgApply || mode == kRowPcgRhs;
-  const bool load_d = mode != kRowSpectrum && mode != kRowNatural && mode != kRowPcgApply;
+  const bool fwd = mode != kRowPcgRhs && mode != kRowMd;
+  const bool mess = mode == kRowMessenger || mode == kRowMessengerF || mode == kRowMd;
+  const bool inv = mess || mode == kRowPcgApply || mode == kRowPcgRhs;
+  const bool load_d = mode != kRowSpectrum && mode != kRowNatural && mode != kRowPcgApply &&
+                      mode != kRowMessengerF;
   double lambda = q.a.lambda;
   double* chi2 = q.a.chi2;
   if (q.a.lam_table) {          // graph mode: schedule and chi^2 slot from device memory
@@ -365,7 +367,8 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
     chi2 = q.a.chi2_base[0] ? q.a.chi2_base[0] + it : nullptr;
   }
   const bool want_x2 = chi2 != nullptr &&
-                       (mode == kRowMessenger || mode == kRowChi2 || mode == kRowPcgRhs);
+                       (mode == kRowMessenger || mode == kRowMessengerF || mode == kRowChi2 ||
+                        mode == kRowPcgRhs);
   for (int64_t job = blockIdx.x; job < q.n_items; job += gridDim.x) {
     const int4 it = __ldg(q.jobs + q.base + job);
     const GenChunk& G = q.rec[it.x];
@@ -396,16 +399,16 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
     const float inv_n = 1.0f / (float)d.n;
     float lt = 0.f;
     bool lam_inf = false;
-    if (mode == kRowMessenger) {
+    if (mess) {
       lam_inf = isinf(lambda);
       lt = lam_inf ? 0.f : (float)(lambda * d.tau);
     }
     const float cn = mode == kRowChi2 ? (float)(lambda * d.tau) : tau;
-    const float sc = mode == kRowMessenger ? inv_n / tau : inv_n;
+    const float sc = mess ? inv_n / tau : inv_n;
     const float2* dt = q.dtab + d.spec;
     const float* nb = q.nbar + d.spec;
     auto filt = [&](float2 X, float2 D, float nbv) -> float2 {
-      if (mode == kRowMessenger) {
+      if (mess) {
         if (lam_inf) return cscale(D, sc);
         const float r = __fdividef(sc, lt + nbv);
         return make_float2((lt * D.x + nbv * X.x) * r, (lt * D.y + nbv * X.y) * r);

@@ -497,7 +497,11 @@ enum RowMode {
   kRowMessenger = 2,  // forward, messenger filter (+ chi^2 of the input), inverse
   kRowPcgApply = 3,   // forward, Y = X / N, inverse
   kRowPcgRhs = 4,     // no forward: Y = d~ / N (+ chi^2 of m = 0, i.e. d^T N^-1 d), inverse
-  kRowChi2 = 5        // forward, chi^2 only
+  kRowChi2 = 5,       // forward, chi^2 only
+  // map-sized form m' = m_d(lambda) + F(lambda) m of the messenger step (Sec. 2.1):
+  kRowMessengerF = 6, // forward, Y = Nbar X / (lambda tau + Nbar) (the F part, no d~), chi^2
+                      // partial sum_k w_k |X_k|^2 / N_k / n, inverse
+  kRowMd = 7          // no forward: Y = lambda tau d~ / (lambda tau + Nbar) (the m_d part), inverse
 };
 
 struct RowArgs {

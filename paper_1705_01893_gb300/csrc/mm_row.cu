@@ -49,7 +49,7 @@ struct DstRows {
   }
 };
 
-template <int M2, int T>
+template <int M2, int T, int MODE>
 __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, const float2* tws,
                                                 float* red, int ci, int rA_) {
   using Lay = RowLayout<M2>;
@@ -59,10 +59,11 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   const int rA = rA_;
   const int rB = (M1 - rA) & (M1 - 1);
   const bool self = rA == rB;
-  const int mode = q.a.mode;
+  const int mode = MODE >= 0 ? MODE : q.a.mode;   // compile-time for the hot mode
   float2* y = q.ybuf + (int64_t)ci * d.M;
-  const bool fwd = mode != kRowPcgRhs;
-  const bool inv = mode == kRowMessenger || mode == kRowPcgApply || mode == kRowPcgRhs;
+  const bool fwd = mode != kRowPcgRhs && mode != kRowMd;
+  const bool mess = mode == kRowMessenger || mode == kRowMessengerF || mode == kRowMd;
+  const bool inv = mess || mode == kRowPcgApply || mode == kRowPcgRhs;
 
   if (fwd) {
     const SrcRows src{y, rA * M2, rB * M2};
@@ -81,21 +82,21 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   }
   float lt = 0.f;               // lambda * tau
   bool lam_inf = false;
-  if (mode == kRowMessenger) {
+  if (mess) {
     lam_inf = isinf(lambda);
     lt = lam_inf ? 0.f : (float)(lambda * d.tau);
   }
   // N' = Nbar + cn for chi^2: tau (Eq. 3) or lambda tau (chi^2(m, lambda))
   const float cn = mode == kRowChi2 ? (float)(lambda * d.tau) : tau;
   // output scale: irfft normalisation 1/n, and T^-1 = 1/tau for the messenger map step
-  const float sc = mode == kRowMessenger ? inv_n / tau : inv_n;
+  const float sc = mess ? inv_n / tau : inv_n;
   const float2* dt = q.dtab + d.spec;
   const float* nb = q.nbar + d.spec;
   const float2 wa = __ldg(&q.g.tw_pack_a[rA]);
   float x2 = 0.f;
 
   auto filt = [&](float2 X, float2 D, float nbv) -> float2 {
-    if (mode == kRowMessenger) {
+    if (mess) {
       if (lam_inf) return cscale(D, sc);
       const float r = __fdividef(sc, lt + nbv);
       return make_float2((lt * D.x + nbv * X.x) * r, (lt * D.y + nbv * X.y) * r);
@@ -104,9 +105,10 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
     return cscale(D, __fdividef(sc, nbv + tau));  // kRowPcgRhs
   };
   const bool want_x2 = chi2 != nullptr &&
-                       (mode == kRowMessenger || mode == kRowChi2 || mode == kRowPcgRhs);
+                       (mode == kRowMessenger || mode == kRowMessengerF || mode == kRowChi2 ||
+                        mode == kRowPcgRhs);
   const bool spec_out = mode == kRowSpectrum || mode == kRowNatural;
-  const bool load_d = !spec_out && mode != kRowPcgApply;
+  const bool load_d = !spec_out && mode != kRowPcgApply && mode != kRowMessengerF;
 
   // Pairs (k, M - k): p in row rA with partner qi in row rB (or in row rA itself when the
   // row pairs with itself).  PB pairs per thread have their d~ / Nbar loads in flight at once.
@@ -157,7 +159,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
           o[M] = make_float2(XM, 0.f);
           continue;
         }
-        const float2 D = dt[0];
+        const float2 D = load_d ? dt[0] : make_float2(0.f, 0.f);
         const float n0 = nb[0], nM = __ldg(q.nyq + c);
         if (want_x2) {
           const float e0 = D.x - X0, eM = D.y - XM;
@@ -226,16 +228,16 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   smem_fft<M2, 2, Lay, T, +1>(sm, tws, SmemIO{}, DstRows{y, &q.g, rA, rB, self});
 }
 
-template <int M2, int T>
+template <int M2, int T, int MODE>
 __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_row(RowParams q) {
   extern __shared__ float2 sm[];
   using Lay = RowLayout<M2>;
   __shared__ float red[32];
   const int jobs_pc = q.g.M1 / 2 + 1;
   const int njobs = q.count * jobs_pc;
-  const int mode = q.a.mode;
+  const int mode = MODE >= 0 ? MODE : q.a.mode;
   const bool reads_d = mode == kRowMessenger || mode == kRowPcgRhs || mode == kRowChi2 ||
-                       mode == kRowPcgApply;
+                       mode == kRowPcgApply || mode == kRowMd;
   // per-pass twiddles of the row DFT, staged once per CTA after the 2 rows of data
   float2* tws = sm + 2 * M2;
   for (int i = threadIdx.x; i < tw_size(M2); i += T) tws[i] = q.g.tw_row[i];
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_row(RowParams q) {
         prefetch_l2(q.nbar + dn.spec + (int64_t)rb * M2, 4 * M2);
       }
     }
-    kernel_body_job<M2, T>(q, sm, tws, red, ci, job % jobs_pc);
+    kernel_body_job<M2, T, MODE>(q, sm, tws, red, ci, job % jobs_pc);
     __syncthreads();
   }
 }
@@ -278,7 +280,11 @@ static cudaError_t row_m2(const mm_plan_s* p, const Batch& b, const RowArgs& a,
   q.nyq = p->nyq;
   q.a = a;
   const size_t smem = sizeof(float2) * (2 * M2 + tw_size(M2));
-  auto k = k_row<M2, T>;
+  // the per-iteration modes (messenger step, its map-sized form) get their own instances
+  // with the mode folded in; the set-up, PCG and chi^2 modes share one
+  auto k = a.mode == kRowMessenger    ? k_row<M2, T, kRowMessenger>
+           : a.mode == kRowMessengerF ? k_row<M2, T, kRowMessengerF>
+                                      : k_row<M2, T, -1>;
   int grid = 0;
   cudaError_t e = persistent_grid(k, T, smem, (g.M1 / 2 + 1) * b.count, &grid);
   if (e != cudaSuccess) return e;
