@@ -92,12 +92,13 @@ def raster_alternating(width: int, spp: int, n: int, phase: int) -> np.ndarray:
     return out[:n].astype(np.int32)
 
 
-def raster_angled(width: int, spp: int, n: int, angle_rad: float, phase: int) -> np.ndarray:
+def raster_angled(width: int, spp: int, n: int, angle_rad: float, phase: int,
+                  cross_offset: float = 0.0) -> np.ndarray:
     """Back-and-forth sweeps across the map along direction (cos a, sin a) through its
     centre, each sweep one pixel further along the cross direction (wrapping after the
     map's extent, width (|cos a| + |sin a|), in that direction), spp samples per pixel of
     path; coordinates in float64, nearest pixel floor(x) + width floor(y), samples outside
-    the map get -1."""
+    the map get -1.  cross_offset shifts the beam across the scan direction (pixels)."""
     ca, sa = np.cos(angle_rad), np.sin(angle_rad)
     span = int(np.ceil(width * (abs(ca) + abs(sa)) - 1e-9))
     per = span * spp
@@ -105,7 +106,7 @@ def raster_angled(width: int, spp: int, n: int, angle_rad: float, phase: int) ->
     j = np.arange(n) % per
     xi = -0.5 * span + (j + 0.5) / spp
     xi = np.where(s % 2 == 0, xi, -xi)
-    eta = -0.5 * span + ((s // 2 + phase) % span) + 0.5
+    eta = -0.5 * span + ((s // 2 + phase) % span) + 0.5 + cross_offset
     x = 0.5 * width + xi * ca - eta * sa
     y = 0.5 * width + xi * sa + eta * ca
     inside = (x >= 0) & (x < width) & (y >= 0) & (y < width)
@@ -245,3 +246,34 @@ def config_crosslinked(width: int = 2048, n_det: int = 32, n_per_det: int = 1 <<
     angles = [180.0 * d / n_det for d in range(n_det)]
     return make_problem(width, 3, chunks, fs, [1.0] * n_det, [0.5] * n_det, [2.0] * n_det,
                         angles, 0.5, seed, weight_dtype=weight_dtype)
+
+
+def config_differential(width: int = 32, n_chunks: int = 9, n_per: int = 1 << 13,
+                        sep: float = 3.0, seed: int = SEED_BASE + 5, fs: float = 100.0,
+                        spp: int = 2, fknee: float = 1.0, alpha: float = 2.0,
+                        sigma: float = 1.0, noiseless: bool = False):
+    """Differencing instrument (App. B test): one T-only detector with two beams offset by
+    +-sep/2 pixels across the scan direction, data d = m(beam A) - m(beam B) + n, rasters at
+    n_chunks orientations k pi / n_chunks (one chunk each), 1/f noise.  Returns the fields
+    of make_problem plus pix_b, gain_a = 1, gain_b = -1."""
+    m_true = sky(width, 1, seed)
+    offsets = np.arange(n_chunks + 1, dtype=np.int64) * n_per
+    pa, pb, tod = [], [], []
+    rng = _rng(seed, 13)
+    phases = rng.integers(0, 1 << 20, size=n_chunks)
+    for c in range(n_chunks):
+        ang = np.pi * c / n_chunks
+        a = raster_angled(width, spp, n_per, ang, int(phases[c]), 0.5 * sep)
+        b = raster_angled(width, spp, n_per, ang, int(phases[c]), -0.5 * sep)
+        sig = np.where(a >= 0, m_true[np.maximum(a, 0), 0], 0.0) - \
+            np.where(b >= 0, m_true[np.maximum(b, 0), 0], 0.0)
+        if not noiseless:
+            sig = sig + draw_noise(n_per, noise_psd(n_per, fs, sigma, fknee, alpha), seed, 200 + c)
+        pa.append(a)
+        pb.append(b)
+        tod.append(sig)
+    params = np.tile([sigma, fknee, alpha, fs], (n_chunks, 1)).astype(np.float64)
+    return dict(width=width, npix=width * width, ncomp=1, pix=np.concatenate(pa).astype(np.int32),
+                pix_b=np.concatenate(pb).astype(np.int32), gain_a=1.0, gain_b=-1.0, cos=None,
+                sin=None, tod=np.concatenate(tod).astype(np.float32), offsets=offsets,
+                params=params, m_true=m_true)
