@@ -193,6 +193,30 @@ mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, void* state, 
 mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev,
                   void* stream);
 
+/* Composite pointing (App. B): every sample carries two pointing entries,
+ * P = gain_a P_a + gain_b P_b, each of the single-entry form of mm_plan_pointing (pixel
+ * index, -1 = none; IQU weights (1, cos 2psi, sin 2psi) when ncomp == 3), e.g. a
+ * differencing instrument with gain_a = 1, gain_b = -1.  The messenger covariance is split
+ * T_A = T_B = T/2, so the map step divides by D = P_a^T T_A^-1 P_a + P_b^T T_B^-1 P_b (gains
+ * squared, 3x3 blocks per pixel, cut by rcond as for one component), and
+ * mm_messenger_iterate runs App. B's compact update
+ *   m' = m + D^-1 P^T (Nbar / lambda + T)^-1 (d - P m)      (lambda = inf: T^-1)
+ * (the map is not reset at lambda = inf: F(inf) != 0 for two components).  Arguments as
+ * for mm_plan_pointing, plus the second component and the two gains (finite, not both 0);
+ * every chunk runs on the general-length kernels (lengths with prime factors 2, 3, 5 up to
+ * 2^21).  Available on a composite plan: mm_set_noise_psd, mm_lambda_max,
+ * mm_messenger_iterate, mm_chi2, mm_chi2_modes, mm_rfft, mm_plan_maps (weight = D^-1),
+ * mm_autotune / mm_set_tune / mm_get_tune; the other iteration forms and the operators
+ * return MM_ERR_UNSUPPORTED.  The workspace size comes from
+ * mm_plan_workspace_size_composite. */
+mm_status mm_plan_workspace_size_composite(int n_chunks, const int64_t* chunk_offsets, int64_t n_pix,
+                                           int ncomp, int weight_dtype, size_t* bytes);
+mm_status mm_plan_composite(mm_plan* out, int n_chunks, const int64_t* chunk_offsets,
+                            const int32_t* pix_a, const void* cos_a, const void* sin_a, float gain_a,
+                            const int32_t* pix_b, const void* cos_b, const void* sin_b, float gain_b,
+                            int weight_dtype, int64_t n_pix, int ncomp, double rcond_min,
+                            void* workspace, size_t workspace_bytes, void* stream);
+
 /* Map-sized form of the messenger iteration (Sec. 2.1): m' = m_d(lambda) + F(lambda) m, with
  * m_d(lambda) = W P^T T^-1 F^-1[lambda tau d~ / (lambda tau + Nbar)] formed once for every
  * distinct lambda of the schedule (one row + column pass each, in order of first use) and

@@ -52,6 +52,10 @@ class CompositeProblem:
         for c in range(self.nchunk):
             yield int(self.offsets[c]), int(self.offsets[c + 1])
 
+    def nbar(self, c):
+        """Nbar = N - T (T = T_A + T_B = tau_c) on the rfft bins of chunk c."""
+        return self.psd[c] - self.tau[c]
+
     def _plan(self):
         """Hit counts of both components and the blocks of D (T_A = T_B = tau/2)."""
         nc = self.ncomp

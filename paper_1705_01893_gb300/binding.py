@@ -53,6 +53,12 @@ SIGNATURES = {
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
     "mm_chi2_modes": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp, _vp]),
     "mm_autotune": (ctypes.c_int, [_vp, _vp]),
+    "mm_plan_workspace_size_composite": (ctypes.c_int, [ctypes.c_int, _i64p, ctypes.c_int64,
+                                                        ctypes.c_int, ctypes.c_int, _szp]),
+    "mm_plan_composite": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _i64p, _vp, _vp, _vp,
+                                         ctypes.c_float, _vp, _vp, _vp, ctypes.c_float,
+                                         ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                         ctypes.c_double, _vp, ctypes.c_size_t, _vp]),
     "mm_messenger_md_bytes": (ctypes.c_int, [_vp, ctypes.c_int, _szp]),
     "mm_messenger_iterate_md": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
     "mm_messenger_adaptive": (ctypes.c_int, [_vp, _dp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
@@ -126,7 +132,9 @@ class Plan:
     (the library keeps raw pointers to them for the plan's lifetime)."""
 
     def __init__(self, offsets: Sequence[int], pix, cos2psi, sin2psi, n_pix: int, ncomp: int,
-                 rcond_min: float = 1e-3, stream=None):
+                 rcond_min: float = 1e-3, stream=None, second=None):
+        """second: None, or (pix_b, cos_b, sin_b, gain_a, gain_b) for a composite plan
+        (App. B: P = gain_a P(pix, cos2psi, sin2psi) + gain_b P(pix_b, cos_b, sin_b))."""
         import torch
         lib = load()
         self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -143,18 +151,33 @@ class Plan:
         self.weight_dtype = wd
         nbytes = ctypes.c_size_t()
         offp = self.offsets.ctypes.data_as(_i64p)
-        _check("mm_plan_workspace_size", lib.mm_plan_workspace_size(
-            self.n_chunks, offp, self.n_pix, self.ncomp, wd, ctypes.byref(nbytes)))
+        self.second = None
+        if second is not None:
+            pb, cb, sb, ga, gb = second
+            self.second = (pb.contiguous(), None if cb is None else cb.contiguous(),
+                           None if sb is None else sb.contiguous(), float(ga), float(gb))
+            _check("mm_plan_workspace_size_composite", lib.mm_plan_workspace_size_composite(
+                self.n_chunks, offp, self.n_pix, self.ncomp, wd, ctypes.byref(nbytes)))
+        else:
+            _check("mm_plan_workspace_size", lib.mm_plan_workspace_size(
+                self.n_chunks, offp, self.n_pix, self.ncomp, wd, ctypes.byref(nbytes)))
         self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=pix.device)
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
         self._ws_bytes = int(nbytes.value)
         self.device = pix.device
         h = _vp()
-        _check("mm_plan_pointing", lib.mm_plan_pointing(
-            ctypes.byref(h), self.n_chunks, offp, _ptr(self.pix), _ptr(self.cos2psi),
-            _ptr(self.sin2psi), wd, self.n_pix, self.ncomp, float(rcond_min), self._ws_ptr,
-            self._ws_bytes, _stream(stream)))
+        if self.second is not None:
+            pb, cb, sb, ga, gb = self.second
+            _check("mm_plan_composite", lib.mm_plan_composite(
+                ctypes.byref(h), self.n_chunks, offp, _ptr(self.pix), _ptr(self.cos2psi),
+                _ptr(self.sin2psi), ga, _ptr(pb), _ptr(cb), _ptr(sb), gb, wd, self.n_pix,
+                self.ncomp, float(rcond_min), self._ws_ptr, self._ws_bytes, _stream(stream)))
+        else:
+            _check("mm_plan_pointing", lib.mm_plan_pointing(
+                ctypes.byref(h), self.n_chunks, offp, _ptr(self.pix), _ptr(self.cos2psi),
+                _ptr(self.sin2psi), wd, self.n_pix, self.ncomp, float(rcond_min), self._ws_ptr,
+                self._ws_bytes, _stream(stream)))
         self._h = h
         self._pcg_state = None
 
@@ -341,14 +364,23 @@ class Plan:
 
 
 def plan_from_synth(s: dict, device="cuda:0", rcond_min: float = 1e-3, tau=None, stream=None):
-    """Upload a synthetic-data dict (see ``synth``) and build a plan with its noise model."""
+    """Upload a synthetic-data dict (see ``synth``) and build a plan with its noise model
+    (a composite plan when the dict has a second pointing component, ``pix_b``)."""
     import torch
     dev = torch.device(device)
     pix = torch.from_numpy(s["pix"]).to(dev)
     cos = None if s["cos"] is None else torch.from_numpy(s["cos"]).to(dev)
     sin = None if s["sin"] is None else torch.from_numpy(s["sin"]).to(dev)
     tod = torch.from_numpy(s["tod"]).to(dev)
-    plan = Plan(s["offsets"], pix, cos, sin, s["npix"], s["ncomp"], rcond_min, stream=stream)
+    second = None
+    if s.get("pix_b") is not None:
+        cb, sb = s.get("cos_b"), s.get("sin_b")
+        second = (torch.from_numpy(s["pix_b"]).to(dev),
+                  None if cb is None else torch.from_numpy(cb).to(dev),
+                  None if sb is None else torch.from_numpy(sb).to(dev),
+                  s.get("gain_a", 1.0), s.get("gain_b", -1.0))
+    plan = Plan(s["offsets"], pix, cos, sin, s["npix"], s["ncomp"], rcond_min, stream=stream,
+                second=second)
     plan.set_noise(tod, params=s["params"], tau=tau, stream=stream)
     plan.tod = tod
     return plan

@@ -196,7 +196,7 @@ static size_t ybuf_budget() {
 }
 
 static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, int ncomp,
-                             int wdtype, Layout* L) {
+                             int wdtype, Layout* L, bool force_general = false) {
   MM_ARG(n_chunks >= 1, "n_chunks must be >= 1 (got %d)", n_chunks);
   MM_ARG(off != nullptr, "offsets is NULL");
   MM_ARG(n_pix >= 1 && n_pix < (int64_t(1) << 31), "n_pix out of range (%lld)", (long long)n_pix);
@@ -213,7 +213,7 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
     int M, M1, M2, cplx = 0;
     // power-of-two chunks on 16-byte boundaries take the compile-time kernels (vector loads)
     bool general = false;
-    if (!(fft_shape(n, &M, &M1, &M2) && off[c] % 4 == 0)) {
+    if (force_general || !(fft_shape(n, &M, &M1, &M2) && off[c] % 4 == 0)) {
       if (!gen_shape(n, &M, &M1, &M2, &cplx)) {
         mm_set_error("chunk %d: length %lld unsupported (need prime factors 2, 3, 5 only and "
                      "n <= 2^24; n/2 up to 2^21 for lengths that are not powers of two)",
@@ -332,6 +332,19 @@ extern "C" mm_status mm_plan_workspace_size(int n_chunks, const int64_t* offsets
          weight_dtype);
   Layout L;
   mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, weight_dtype, &L);
+  if (st != MM_OK) return st;
+  *bytes = L.total;
+  return MM_OK;
+}
+
+extern "C" mm_status mm_plan_workspace_size_composite(int n_chunks, const int64_t* offsets,
+                                                      int64_t n_pix, int ncomp, int weight_dtype,
+                                                      size_t* bytes) {
+  MM_ARG(bytes != nullptr, "bytes is NULL");
+  MM_ARG(weight_dtype == MM_W_F32 || weight_dtype == MM_W_F16, "bad weight_dtype %d",
+         weight_dtype);
+  Layout L;
+  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, weight_dtype, &L, true);
   if (st != MM_OK) return st;
   *bytes = L.total;
   return MM_OK;
@@ -468,12 +481,12 @@ __global__ void k_weights_accum(const ChunkDesc* __restrict__ desc, int c,
                                 const int32_t* __restrict__ pix, const void* cosw,
                                 const void* sinw, int half_w, int ncomp,
                                 const double* __restrict__ c0, int64_t n0, int64_t n,
-                                double* __restrict__ acc12) {
+                                double* __restrict__ acc12, double scale) {
   const int64_t s = n0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int p = pix[s];
   if (p < 0) return;
-  const double s1 = 1.0 / desc[c].tau, s2 = c0[c];
+  const double s1 = scale / desc[c].tau, s2 = c0[c];
   if (ncomp == 1) {
     atomicAdd(acc12 + 2 * (int64_t)p, s1);
     atomicAdd(acc12 + 2 * (int64_t)p + 1, s2);
@@ -597,6 +610,32 @@ __global__ void k_bin_apply(int64_t n_pix, double* __restrict__ acc, const doubl
   for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
   sym_apply<NC>(w, a, m);
   store_map4<NC>(map4, p, m);
+  if (map_out)
+#pragma unroll
+    for (int i = 0; i < NC; ++i) map_out[NC * p + i] = m[i];
+}
+
+// Composite map step (App. B, compact form): m += D^-1 acc with D^-1 in W; acc cleared; the
+// FP32 gather copy holds m on kept pixels and 0 on cut ones (whose entries drop out of P).
+template <int NC>
+__global__ void k_bin_resid(int64_t n_pix, double* __restrict__ acc, const double* __restrict__ W,
+                            const uint8_t* __restrict__ valid, double* __restrict__ m64,
+                            void* map4, double* __restrict__ map_out) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n_pix) return;
+  constexpr int B = NC == 3 ? 6 : 1;
+  double a[NC], w[B], u[NC], m[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) { a[i] = acc[NC * p + i]; acc[NC * p + i] = 0.0; }
+#pragma unroll
+  for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
+  sym_apply<NC>(w, a, u);
+#pragma unroll
+  for (int i = 0; i < NC; ++i) { m[i] = m64[NC * p + i] + u[i]; m64[NC * p + i] = m[i]; }
+  double g[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) g[i] = valid[p] ? m[i] : 0.0;
+  store_map4<NC>(map4, p, g);
   if (map_out)
 #pragma unroll
     for (int i = 0; i < NC; ++i) map_out[NC * p + i] = m[i];
@@ -898,18 +937,59 @@ static cudaError_t gen_upload(mm_plan_s* p, cudaStream_t s) {
   return cudaStreamSynchronize(s);
 }
 
+// Second pointing component of a composite plan (App. B).
+struct CompArgs {
+  const int32_t* pix_b;
+  const void* cos_b;
+  const void* sin_b;
+  float gain_a, gain_b;
+};
+
+static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
+                             const int32_t* pix, const void* cos2psi, const void* sin2psi,
+                             int weight_dtype, int64_t n_pix, int ncomp, double rcond_min,
+                             void* workspace, size_t workspace_bytes, void* stream,
+                             const CompArgs* cp);
+
 extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t* offsets,
                                       const int32_t* pix, const void* cos2psi,
                                       const void* sin2psi, int weight_dtype, int64_t n_pix,
                                       int ncomp, double rcond_min, void* workspace,
                                       size_t workspace_bytes, void* stream) {
+  return plan_create(out, n_chunks, offsets, pix, cos2psi, sin2psi, weight_dtype, n_pix, ncomp,
+                     rcond_min, workspace, workspace_bytes, stream, nullptr);
+}
+
+extern "C" mm_status mm_plan_composite(mm_plan* out, int n_chunks, const int64_t* offsets,
+                                       const int32_t* pix_a, const void* cos_a, const void* sin_a,
+                                       float gain_a, const int32_t* pix_b, const void* cos_b,
+                                       const void* sin_b, float gain_b, int weight_dtype,
+                                       int64_t n_pix, int ncomp, double rcond_min, void* workspace,
+                                       size_t workspace_bytes, void* stream) {
+  MM_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  MM_ARG(pix_b != nullptr, "pix_b is NULL");
+  MM_ARG((ncomp == 3) == (cos_b != nullptr && sin_b != nullptr),
+         "cos_b/sin_b must be given iff ncomp == 3");
+  MM_ARG(isfinite(gain_a) && isfinite(gain_b) && (gain_a != 0.f || gain_b != 0.f),
+         "gains must be finite and not both zero");
+  const CompArgs cp{pix_b, cos_b, sin_b, gain_a, gain_b};
+  return plan_create(out, n_chunks, offsets, pix_a, cos_a, sin_a, weight_dtype, n_pix, ncomp,
+                     rcond_min, workspace, workspace_bytes, stream, &cp);
+}
+
+static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
+                             const int32_t* pix, const void* cos2psi, const void* sin2psi,
+                             int weight_dtype, int64_t n_pix, int ncomp, double rcond_min,
+                             void* workspace, size_t workspace_bytes, void* stream,
+                             const CompArgs* cp) {
   MM_ARG(out != nullptr, "out is NULL");
   *out = nullptr;
   MM_ARG(pix != nullptr, "pix is NULL");
   MM_ARG(weight_dtype == MM_W_F32 || weight_dtype == MM_W_F16, "bad weight_dtype %d",
          weight_dtype);
   Layout L;
-  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, weight_dtype, &L);
+  mm_status st = make_layout(n_chunks, offsets, n_pix, ncomp, weight_dtype, &L, cp != nullptr);
   if (st != MM_OK) return st;
   MM_ARG((ncomp == 3) == (cos2psi != nullptr && sin2psi != nullptr),
          "cos2psi/sin2psi must be given iff ncomp == 3");
@@ -928,6 +1008,12 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   p->n_pix = n_pix; p->n_total = L.n_total; p->spec_total = L.spec_total;
   p->rcond_min = rcond_min; p->pix = pix; p->cosw = cos2psi; p->sinw = sin2psi;
   p->noise_set = false;
+  p->composite = cp != nullptr;
+  p->pix_b = cp ? cp->pix_b : nullptr;
+  p->cos_b = cp ? cp->cos_b : nullptr;
+  p->sin_b = cp ? cp->sin_b : nullptr;
+  p->gain_a = cp ? cp->gain_a : 1.f;
+  p->gain_b = cp ? cp->gain_b : 0.f;
   char* ws = static_cast<char*>(workspace);
   p->d_desc = reinterpret_cast<ChunkDesc*>(ws + L.desc);
   int* d_chunks = reinterpret_cast<int*>(ws + L.chunks);
@@ -1092,6 +1178,8 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
   if ((e = cudaMemsetAsync(p->acc, 0, sizeof(double) * ncomp * n_pix, s)) != cudaSuccess) return fail("memset", e);
   if (L.n_total > 0)
     k_hits<<<blocks_for(L.n_total, 256), 256, 0, s>>>(pix, L.n_total, n_pix, p->hits, p->scal + kScalTmp);
+  if (L.n_total > 0 && p->composite)
+    k_hits<<<blocks_for(L.n_total, 256), 256, 0, s>>>(p->pix_b, L.n_total, n_pix, p->hits, p->scal + kScalTmp);
   if ((e = launch_tile_pointing(p, s)) != cudaSuccess) return fail("pointing tile copy", e);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail("set-up kernels", e);
   double flag = 0.0;
@@ -1210,9 +1298,20 @@ extern "C" mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const do
   // one launch per chunk keeps the chunk's scales without a per-sample search
   for (int c = 0; c < C; ++c) {
     const ChunkDesc& d = p->h_desc[c];
-    k_weights_accum<<<blocks_for(d.n, 256), 256, 0, s>>>(
-        p->d_desc, c, p->pix, p->cosw, p->sinw, p->wdtype == MM_W_F16, p->ncomp, p->c0, d.off,
-        d.off + d.n, p->acc12);
+    if (!p->composite) {
+      k_weights_accum<<<blocks_for(d.n, 256), 256, 0, s>>>(
+          p->d_desc, c, p->pix, p->cosw, p->sinw, p->wdtype == MM_W_F16, p->ncomp, p->c0, d.off,
+          d.off + d.n, p->acc12, 1.0);
+    } else {
+      // D = P_A^T T_A^-1 P_A + P_B^T T_B^-1 P_B with T_A = T_B = tau / 2 (App. B); the gains
+      // enter squared
+      k_weights_accum<<<blocks_for(d.n, 256), 256, 0, s>>>(
+          p->d_desc, c, p->pix, p->cosw, p->sinw, p->wdtype == MM_W_F16, p->ncomp, p->c0, d.off,
+          d.off + d.n, p->acc12, 2.0 * (double)p->gain_a * p->gain_a);
+      k_weights_accum<<<blocks_for(d.n, 256), 256, 0, s>>>(
+          p->d_desc, c, p->pix_b, p->cos_b, p->sin_b, p->wdtype == MM_W_F16, p->ncomp, p->c0,
+          d.off, d.off + d.n, p->acc12, 2.0 * (double)p->gain_b * p->gain_b);
+    }
   }
   LAUNCHED("k_weights_accum");
   unsigned long long* d_nvalid = reinterpret_cast<unsigned long long*>(p->scal + kScalTmp + 1);
@@ -1280,6 +1379,23 @@ extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int 
   mm_status st = load_map(p, map_inout, s);
   if (st != MM_OK) return st;
   if (chi2_out) MM_CUDA(cudaMemsetAsync(chi2_out, 0, sizeof(double) * n_iter, s));
+  if (p->composite) {
+    // App. B: m' = m + D^-1 P^T (Nbar / lambda + T)^-1 (d - P m), the map kept in FP64
+    MM_CUDA(cudaMemcpyAsync(p->map64, map_inout, sizeof(double) * p->ncomp * p->n_pix,
+                            cudaMemcpyDeviceToDevice, s));
+    for (int it = 0; it < n_iter; ++it) {
+      RowArgs a{kRowResidual, lambdas[it], chi2_out ? chi2_out + it : nullptr, nullptr};
+      FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
+                  L_(launch_col_inverse(p, B, s)));
+      double* mo = it == n_iter - 1 ? map_inout : nullptr;
+      if (p->ncomp == 3)
+        k_bin_resid<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->valid, p->map64, p->map4, mo);
+      else
+        k_bin_resid<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->valid, p->map64, p->map4, mo);
+      LAUNCHED("k_bin_resid");
+    }
+    return MM_OK;
+  }
   for (int it = 0; it < n_iter; ++it) {
     RowArgs a{kRowMessenger, lambdas[it], chi2_out ? chi2_out + it : nullptr, nullptr};
     FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
@@ -1366,6 +1482,10 @@ extern "C" mm_status mm_messenger_md_bytes(mm_plan p, int n_levels, size_t* byte
 extern "C" mm_status mm_messenger_iterate_md(mm_plan p, const double* lambdas, int n_iter,
                                              double* map_inout, double* chi2_out, void* work,
                                              size_t work_bytes, void* stream) {
+  if (p && p->composite) {
+    mm_set_error("mm_messenger_iterate_md: not available for composite-pointing plans");
+    return MM_ERR_UNSUPPORTED;
+  }
   MM_ARG(p != nullptr, "plan is NULL");
   MM_ARG(n_iter >= 0, "n_iter must be >= 0");
   MM_ARG(n_iter == 0 || lambdas != nullptr, "lambdas is NULL");
@@ -1437,6 +1557,10 @@ extern "C" mm_status mm_plan_batches(mm_plan p, int* n_batches) {
 
 extern "C" mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double lambda,
                                         double* map_inout, double* chi2_slot, void* stream) {
+  if (p && p->composite) {
+    mm_set_error("mm_messenger_stage: not available for composite-pointing plans");
+    return MM_ERR_UNSUPPORTED;
+  }
   MM_ARG(p != nullptr, "plan is NULL");
   if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
   cudaStream_t s = S(stream);
@@ -1613,6 +1737,10 @@ extern "C" mm_status mm_messenger_adaptive(mm_plan p, const double* levels, int 
                                            double rel_tol, int min_per_level, int max_per_level,
                                            int max_iter, double* map_inout, double* chi2_out,
                                            double* lambda_out, int* n_done, void* stream) {
+  if (p && p->composite) {
+    mm_set_error("mm_messenger_adaptive: not available for composite-pointing plans");
+    return MM_ERR_UNSUPPORTED;
+  }
   MM_ARG(p != nullptr && levels != nullptr && map_inout != nullptr && chi2_out != nullptr &&
          lambda_out != nullptr && n_done != nullptr, "NULL argument");
   MM_ARG(n_levels >= 1 && n_levels <= kMaxLevels, "n_levels must be in [1, %d]", kMaxLevels);
@@ -1659,6 +1787,10 @@ extern "C" mm_status mm_messenger_adaptive(mm_plan p, const double* levels, int 
 
 extern "C" mm_status mm_messenger_graph(mm_plan p, const double* lambdas, int n_iter,
                                         double* map_inout, double* chi2_out, void* stream) {
+  if (p && p->composite) {
+    mm_set_error("mm_messenger_graph: not available for composite-pointing plans");
+    return MM_ERR_UNSUPPORTED;
+  }
   MM_ARG(p != nullptr && map_inout != nullptr, "NULL argument");
   MM_ARG(n_iter >= 0 && n_iter <= p->lam_cap, "n_iter must be in [0, %d]", p->lam_cap);
   MM_ARG(n_iter == 0 || lambdas != nullptr, "lambdas is NULL");
@@ -1696,6 +1828,10 @@ static mm_status apply_A(mm_plan p, cudaStream_t s) {
 
 extern "C" mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, void* state, int restart,
                                     double* chi2_out, void* stream) {
+  if (p && p->composite) {
+    mm_set_error("mm_pcg_iterate: not available for composite-pointing plans");
+    return MM_ERR_UNSUPPORTED;
+  }
   MM_ARG(p != nullptr && map_inout != nullptr && state != nullptr, "NULL argument");
   MM_ARG(((uintptr_t)state & 255) == 0, "state must be 256-byte aligned");
   MM_ARG(n_iter >= 0, "n_iter must be >= 0");
@@ -1955,6 +2091,10 @@ extern "C" mm_status mm_autotune(mm_plan p, void* stream) {
 }
 
 extern "C" mm_status mm_apply_pointing(mm_plan p, const double* map, float* tod_out, void* stream) {
+  if (p && p->composite) {
+    mm_set_error("mm_apply_pointing: not available for composite-pointing plans");
+    return MM_ERR_UNSUPPORTED;
+  }
   MM_ARG(p != nullptr && map != nullptr && tod_out != nullptr, "NULL argument");
   if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run (pixel cut unknown)"); return MM_ERR_STATE; }
   cudaStream_t s = S(stream);
@@ -1968,6 +2108,10 @@ extern "C" mm_status mm_apply_pointing(mm_plan p, const double* map, float* tod_
 }
 
 extern "C" mm_status mm_apply_pointing_T(mm_plan p, const float* tod, double* acc_out, void* stream) {
+  if (p && p->composite) {
+    mm_set_error("mm_apply_pointing_T: not available for composite-pointing plans");
+    return MM_ERR_UNSUPPORTED;
+  }
   MM_ARG(p != nullptr && tod != nullptr && acc_out != nullptr, "NULL argument");
   cudaStream_t s = S(stream);
   MM_CUDA(cudaMemsetAsync(acc_out, 0, sizeof(double) * p->ncomp * p->n_pix, s));

@@ -40,6 +40,12 @@ struct GenParams {
   const float* __restrict__ nbar;
   const float* __restrict__ nyq;
   RowArgs a;
+  // composite pointing (App. B): P = ga P_1 + gb P_2, the second component below
+  int composite;
+  float ga, gb;
+  const int32_t* __restrict__ pix2;
+  const void* cos2;
+  const void* sin2;
 };
 
 // k mod d for 0 <= k < 2^22 with d uniform: float reciprocal, then one correction step
@@ -202,25 +208,34 @@ __device__ __forceinline__ float2 gen_tw_big(const GenChunk& g, int e) {
   return cmul(__ldg(&g.tw_hi[e >> g.log_lo]), __ldg(&g.tw_lo[e & ((1 << g.log_lo) - 1)]));
 }
 
-// (P m)_s for one sample (Eq. 1); weights from the caller's natural-order arrays.
+// One pointing component's (P m)_s (Eq. 1); weights from the caller's natural-order arrays.
 template <int NC>
-__device__ __forceinline__ float gen_pm(const GenParams& q, int64_t s) {
-  const int p = __ldg(q.pix + s);
+__device__ __forceinline__ float gen_pm1(const GenParams& q, const int32_t* __restrict__ pix,
+                                         const void* cosw, const void* sinw, int64_t s) {
+  const int p = __ldg(pix + s);
   if (p < 0) return 0.f;
   if constexpr (NC == 1) {
     return __ldg(reinterpret_cast<const float*>(q.map4) + p);
   } else {
     float cw, sw;
     if (q.half_w) {
-      cw = __half2float(static_cast<const __half*>(q.cosw)[s]);
-      sw = __half2float(static_cast<const __half*>(q.sinw)[s]);
+      cw = __half2float(static_cast<const __half*>(cosw)[s]);
+      sw = __half2float(static_cast<const __half*>(sinw)[s]);
     } else {
-      cw = __ldg(static_cast<const float*>(q.cosw) + s);
-      sw = __ldg(static_cast<const float*>(q.sinw) + s);
+      cw = __ldg(static_cast<const float*>(cosw) + s);
+      sw = __ldg(static_cast<const float*>(sinw) + s);
     }
     const float4 m = __ldg(reinterpret_cast<const float4*>(q.map4) + p);
     return fmaf(sw, m.z, fmaf(cw, m.y, m.x));
   }
+}
+
+// (P m)_s: one component, or g_a P_a m + g_b P_b m for a composite plan (App. B).
+template <int NC>
+__device__ __forceinline__ float gen_pm(const GenParams& q, int64_t s) {
+  const float v = gen_pm1<NC>(q, q.pix, q.cosw, q.sinw, s);
+  if (!q.composite) return v;
+  return fmaf(q.gb, gen_pm1<NC>(q, q.pix2, q.cos2, q.sin2, s), q.ga * v);
 }
 
 // ------------------------------------------------------------ kernel A: columns forward
@@ -272,7 +287,9 @@ __global__ void __launch_bounds__(512) k_gen_col_forward(GenParams q) {
 // the first lane of each run issues one FP64 add per component.
 template <int NC>
 __device__ __forceinline__ void gen_scatter(const GenParams& q, const ChunkDesc& d, int j2_0,
-                                            int width, const float* smf, int NB, int lnb, int T) {
+                                            int width, const float* smf, int NB, int lnb, int T,
+                                            const int32_t* __restrict__ pix, const void* cosw,
+                                            const void* sinw, float gain) {
   const int rw = d.cplx ? NB : 2 * NB;          // samples per tile row
   const int lrw = d.cplx ? lnb : lnb + 1;
   const int valid_u = d.cplx ? width : 2 * width;
@@ -287,17 +304,17 @@ __device__ __forceinline__ void gen_scatter(const GenParams& q, const ChunkDesc&
       if (u < valid_u) {
         const int64_t s = d.off + (d.cplx ? (int64_t)j1 * d.M2 + j2_0 + u
                                           : 2 * ((int64_t)j1 * d.M2 + j2_0) + u);
-        p = __ldg(q.pix + s);
-        const float t = d.cplx ? smf[2 * e] : smf[e];
+        p = __ldg(pix + s);
+        const float t = gain * (d.cplx ? smf[2 * e] : smf[e]);
         v0 = t;
         if constexpr (NC == 3) {
           float cw, sw;
           if (q.half_w) {
-            cw = __half2float(static_cast<const __half*>(q.cosw)[s]);
-            sw = __half2float(static_cast<const __half*>(q.sinw)[s]);
+            cw = __half2float(static_cast<const __half*>(cosw)[s]);
+            sw = __half2float(static_cast<const __half*>(sinw)[s]);
           } else {
-            cw = __ldg(static_cast<const float*>(q.cosw) + s);
-            sw = __ldg(static_cast<const float*>(q.sinw) + s);
+            cw = __ldg(static_cast<const float*>(cosw) + s);
+            sw = __ldg(static_cast<const float*>(sinw) + s);
           }
           v1 = t * cw;
           v2 = t * sw;
@@ -340,7 +357,13 @@ __global__ void __launch_bounds__(512) k_gen_col_inverse(GenParams q) {
     }
     __syncthreads();
     const float2* r = gen_dft_cols<+1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, T);
-    gen_scatter<NC>(q, d, j2_0, width, reinterpret_cast<const float*>(r), NB, lnb, T);
+    const float* rf = reinterpret_cast<const float*>(r);
+    if (!q.composite) {
+      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.pix, q.cosw, q.sinw, 1.f);
+    } else {   // P^T t = g_a P_a^T t + g_b P_b^T t (App. B)
+      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.pix, q.cosw, q.sinw, q.ga);
+      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.pix2, q.cos2, q.sin2, q.gb);
+    }
     __syncthreads();
   }
 }
@@ -356,7 +379,8 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   const int mode = q.a.mode;
   const bool fwd = mode != kRowPcgRhs && mode != kRowMd;
   const bool mess = mode == kRowMessenger || mode == kRowMessengerF || mode == kRowMd;
-  const bool inv = mess || mode == kRowPcgApply || mode == kRowPcgRhs;
+  const bool resid = mode == kRowResidual;
+  const bool inv = mess || resid || mode == kRowPcgApply || mode == kRowPcgRhs;
   const bool load_d = mode != kRowSpectrum && mode != kRowNatural && mode != kRowPcgApply &&
                       mode != kRowMessengerF;
   double lambda = q.a.lambda;
@@ -368,7 +392,7 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   }
   const bool want_x2 = chi2 != nullptr &&
                        (mode == kRowMessenger || mode == kRowMessengerF || mode == kRowChi2 ||
-                        mode == kRowPcgRhs);
+                        mode == kRowPcgRhs || mode == kRowResidual);
   for (int64_t job = blockIdx.x; job < q.n_items; job += gridDim.x) {
     const int4 it = __ldg(q.jobs + q.base + job);
     const GenChunk& G = q.rec[it.x];
@@ -399,10 +423,11 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
     const float inv_n = 1.0f / (float)d.n;
     float lt = 0.f;
     bool lam_inf = false;
-    if (mess) {
+    if (mess || resid) {
       lam_inf = isinf(lambda);
       lt = lam_inf ? 0.f : (float)(lambda * d.tau);
     }
+    const float lamf = lam_inf ? 1.f : (float)lambda;
     const float cn = mode == kRowChi2 ? (float)(lambda * d.tau) : tau;
     const float sc = mess ? inv_n / tau : inv_n;
     const float2* dt = q.dtab + d.spec;
@@ -413,6 +438,8 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
         const float r = __fdividef(sc, lt + nbv);
         return make_float2((lt * D.x + nbv * X.x) * r, (lt * D.y + nbv * X.y) * r);
       }
+      if (resid)   // (d~ - X) / (n (Nbar / lambda + tau)); lambda = inf: / (n tau)
+        return cscale(csub(D, X), lam_inf ? __fdividef(sc, tau) : __fdividef(sc, __fdividef(nbv, lamf) + tau));
       if (mode == kRowPcgApply) return cscale(X, __fdividef(sc, nbv + tau));
       return cscale(D, __fdividef(sc, nbv + tau));  // kRowPcgRhs
     };
@@ -564,6 +591,12 @@ static GenParams gen_params(const mm_plan_s* p, const Batch& b, const int2* item
   q.dtab = p->dtab;
   q.nbar = p->nbar;
   q.nyq = p->nyq;
+  q.composite = p->composite;
+  q.ga = p->gain_a;
+  q.gb = p->gain_b;
+  q.pix2 = p->pix_b;
+  q.cos2 = p->cos_b;
+  q.sin2 = p->sin_b;
   return q;
 }
 

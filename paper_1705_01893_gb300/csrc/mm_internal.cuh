@@ -116,6 +116,12 @@ struct GenChunk {
 
 struct mm_plan_s {
   int n_chunks, ncomp, wdtype;
+  // composite pointing P = g_a P_a + g_b P_b (App. B); the first component is pix/cosw/sinw
+  int composite;
+  const int32_t* pix_b;
+  const void* cos_b;
+  const void* sin_b;
+  float gain_a, gain_b;
   int64_t n_pix, n_total, spec_total;
   double rcond_min;
   const int32_t* pix;
@@ -501,7 +507,9 @@ enum RowMode {
   // map-sized form m' = m_d(lambda) + F(lambda) m of the messenger step (Sec. 2.1):
   kRowMessengerF = 6, // forward, Y = Nbar X / (lambda tau + Nbar) (the F part, no d~), chi^2
                       // partial sum_k w_k |X_k|^2 / N_k / n, inverse
-  kRowMd = 7          // no forward: Y = lambda tau d~ / (lambda tau + Nbar) (the m_d part), inverse
+  kRowMd = 7,         // no forward: Y = lambda tau d~ / (lambda tau + Nbar) (the m_d part), inverse
+  // composite pointing (App. B), general path only:
+  kRowResidual = 8    // forward, Y = (d~ - X) / (n (Nbar / lambda + tau)), chi^2, inverse
 };
 
 struct RowArgs {
