@@ -79,6 +79,8 @@ def bytes_model(s):
     n = int(lens.sum())
     nc, npix = s["ncomp"], s["npix"]
     w = 0 if nc == 1 else (4 if s["cos"].dtype == np.float16 else 8)
+    if s.get("pix_b") is not None:
+        w = 2 * (4 + w) - 4          # two pointing entries per sample (App. B)
     Y = int(np.sum(np.where(lens % 2 == 1, 8 * lens, 4 * lens)))
     blk = 6 if nc == 3 else 1
     mapb = 16 if nc == 3 else 4
@@ -328,6 +330,41 @@ def measure_secondary(name, args, dev, stream):
     return out
 
 
+def measure_composite(dev, stream, steps=20):
+    """Differencing instrument (composite pointing, App. B): 512x512 T map, 9 raster
+    orientations x 2^21 samples, two beams 3 pixels apart with gains +1 / -1; iterations
+    launched from the host (mm_messenger_iterate), events around them."""
+    import torch
+    from paper_1705_01893_gb300 import binding, synth
+    s = synth.config_differential(width=512, n_chunks=9, n_per=1 << 21, sep=3.0)
+    plan = binding.plan_from_synth(s, dev)
+    plan.autotune()
+    lam = binding.cooling_schedule(plan.lambda_max(), 10, 10)
+    m = torch.zeros(s["npix"], 1, dtype=torch.float64, device=dev)
+    plan.messenger(m, lam[:3])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    plan.messenger(m, lam[3:3 + steps])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    hbm, src = hbm_peak()
+    _, strict, bpass = bytes_model(s)
+    n = int(s["offsets"][-1])
+    out = {"config": dict(workload_config("differential512_9x2^21", s),
+                          pointing="two beams per sample (+1 / -1), 3 px apart"),
+           "ms_per_iter": ms, "iters_per_s": 1e3 / ms, "tod_gsamples_per_s": n / ms / 1e6,
+           "schedule": dict(zip(("col_nb", "col_threads", "row_threads", "radix_order"), plan.tune)),
+           "iteration_hbm": {"bytes_pass": bpass, "bytes_strict": strict,
+                             "frac_pass": bpass / (ms * 1e-3) / 1e9 / hbm,
+                             "frac_strict": strict / (ms * 1e-3) / 1e9 / hbm,
+                             "peak_gbs": hbm, "peak": src},
+           "timing": "K iterations in one mm_messenger_iterate call, events around it"}
+    del plan
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -470,11 +507,12 @@ def run_gpu(args):
         else:
             tol = time_to_tolerance(plan, s, dev, stream, args)
 
-    secondary = None
+    secondary = composite = None
     if name == WORKLOAD and not args.no_secondary:
         del plan
         torch.cuda.empty_cache()
         secondary = measure_secondary("uneven64_1024", args, dev, stream)
+        composite = measure_composite(dev, stream)
 
     if rank != 0:
         return
@@ -509,6 +547,7 @@ def run_gpu(args):
         "gpu_launches": args.steps * (3 * nb + 1),   # per timed region
         "time_to_chi2_tol": tol,
         "uneven_chunks": secondary,
+        "composite_pointing": composite,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
