@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "messenger iters/s"
 UNIT = "iter/s"
 WORKLOAD = "iqu512_8det_2^22"
-WORKLOADS = ("iqu512_8det_2^22", "uneven64_1024", "crosslinked2048_32det_2^24")
+WORKLOADS = ("iqu512_8det_2^22", "uneven64_1024", "crosslinked2048_32det_2^24", "t64_1det_2^15")
 
 
 def load_workload(name):
@@ -49,6 +49,8 @@ def load_workload(name):
         return synth.config_uneven()
     if name == "crosslinked2048_32det_2^24":
         return synth.config_crosslinked()
+    if name == "t64_1det_2^15":
+        return synth.config_temperature_64()
     raise ValueError(name)
 
 
@@ -61,7 +63,9 @@ def workload_config(name, s):
            "chunks": int(len(lens)), "n_samples": n,
            "weights": ("fp16" if half else "fp32") + " cos2psi/sin2psi",
            "schedule": "10 levels x 10 iterations, cycled",
-           "l2": "inputs larger than L2 (>%d MB read per step), no flush" % (n * 12 // 2 ** 20),
+           "l2": ("inputs larger than L2 (>%d MB read per step), no flush" % (n * 12 // 2 ** 20)
+                  if n * 12 > 129 * 2 ** 20 else
+                  "inputs fit in L2 (not flushed): a latency figure, iterations/s only"),
            "parallelism": "replicas"}
     if len(set(lens.tolist())) == 1:
         cfg["samples_per_chunk"] = int(lens[0])
@@ -507,12 +511,13 @@ def run_gpu(args):
         else:
             tol = time_to_tolerance(plan, s, dev, stream, args)
 
-    secondary = composite = None
+    secondary = composite = small = None
     if name == WORKLOAD and not args.no_secondary:
         del plan
         torch.cuda.empty_cache()
         secondary = measure_secondary("uneven64_1024", args, dev, stream)
         composite = measure_composite(dev, stream)
+        small = measure_secondary("t64_1det_2^15", args, dev, stream)
 
     if rank != 0:
         return
@@ -548,6 +553,7 @@ def run_gpu(args):
         "time_to_chi2_tol": tol,
         "uneven_chunks": secondary,
         "composite_pointing": composite,
+        "temperature_64": small,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:
