@@ -369,6 +369,68 @@ def measure_composite(dev, stream, steps=20):
     return out
 
 
+def measure_adjoint(dev, stream, K=50):
+    """Differentiation workload (256x256 IQU, 4 x 2^20 samples): K = 50 cooled messenger
+    iterations forward, then the adjoint through all of them.  Timed: the plain forward, the
+    forward that keeps checkpoints every 10 iterations, the backward from those checkpoints
+    (recompute + transposed steps, dL/dd and dL/dtheta), the backward for dL/dd alone (no
+    forward iterate needed), and the all-in-one adjoint call (its own forward sweep)."""
+    import torch
+    from paper_1705_01893_gb300 import binding, synth
+    s = synth.config_iqu_256()
+    plan = binding.plan_from_synth(s, dev)
+    lam = binding.cooling_schedule(plan.lambda_max(), 5, 10)[:K]
+    m0 = torch.zeros(s["npix"], 3, dtype=torch.float64, device=dev)
+    gt = torch.empty(len(s["pix"]), dtype=torch.float32, device=dev)
+    gth = torch.empty(len(s["offsets"]) - 1, 3, dtype=torch.float64, device=dev)
+    g = torch.randn(s["npix"], 3, dtype=torch.float64, device=dev)
+
+    def fwd():
+        m = m0.clone()
+        plan.messenger(m, lam)
+
+    def fwd_ckpt():
+        m = m0.clone()
+        return plan.forward_ckpt(m, lam, 10)
+
+    ck = fwd_ckpt()
+
+    def bwd_theta():
+        plan.adjoint_ckpt(lam, ck, g, gt, gth, ckpt_every=10)
+
+    def bwd_data():
+        plan.adjoint_ckpt(lam, ck, g, gt, None, ckpt_every=10)
+
+    def all_in_one():
+        plan.adjoint(lam, m0, g, gt, gth, ckpt_every=10)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize(dev)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    f, fc = timed(fwd), timed(fwd_ckpt)
+    bt, bd, al = timed(bwd_theta), timed(bwd_data), timed(all_in_one)
+    out = {"config": workload_config("iqu256_4det_2^20", s), "iterations": K, "ckpt_every": 10,
+           "ms_forward": f, "ms_forward_ckpt": fc,
+           "ms_backward_theta": bt, "ms_backward_data_only": bd, "ms_adjoint_all_in_one": al,
+           "backward_theta_over_forward": bt / f, "backward_data_over_forward": bd / f,
+           "timing": "events on the launching stream, best of 3 after one untimed call; "
+                     "backward = mm_messenger_adjoint_ckpt from the forward's checkpoints"}
+    del plan
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -511,13 +573,14 @@ def run_gpu(args):
         else:
             tol = time_to_tolerance(plan, s, dev, stream, args)
 
-    secondary = composite = small = None
+    secondary = composite = small = adjoint = None
     if name == WORKLOAD and not args.no_secondary:
         del plan
         torch.cuda.empty_cache()
         secondary = measure_secondary("uneven64_1024", args, dev, stream)
         composite = measure_composite(dev, stream)
         small = measure_secondary("t64_1det_2^15", args, dev, stream)
+        adjoint = measure_adjoint(dev, stream)
 
     if rank != 0:
         return
@@ -554,6 +617,7 @@ def run_gpu(args):
         "uneven_chunks": secondary,
         "composite_pointing": composite,
         "temperature_64": small,
+        "adjoint": adjoint,
         "clocks": clocks,
     }
     if world == 1 and not args.no_cpu_baseline:

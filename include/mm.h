@@ -176,6 +176,25 @@ mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int n_iter,
                                float* grad_tod, double* grad_theta, int ckpt_every,
                                void* work, size_t work_bytes, void* stream);
 
+/* The two halves of mm_messenger_adjoint, for a caller (an autograd function) that runs the
+ * forward itself.  mm_messenger_forward_ckpt runs n_iter iterations of mm_messenger_iterate
+ * on map_inout (same results) and first copies m_0, m_E, m_2E, ... (E = ckpt_every) into
+ * ckpt: device float64 [ceil(n_iter / E)][n_pix][ncomp], caller-owned.
+ * mm_messenger_adjoint_ckpt then runs the backward sweep from those checkpoints, with the
+ * arguments, results and work space (mm_adjoint_work_bytes) of mm_messenger_adjoint.
+ * With grad_theta == NULL neither needs the forward iterates: the step is affine in (m, d)
+ * with the cooling sequence held constant, so its transpose, and hence dL/dd, does not
+ * depend on them; the backward then reads no checkpoint and recomputes nothing (ckpt may be
+ * any non-NULL pointer), and mm_messenger_adjoint skips its forward sweep.  Same errors as
+ * mm_messenger_adjoint (MM_ERR_ARG for a NULL map, checkpoint or output pointer). */
+mm_status mm_messenger_forward_ckpt(mm_plan p, const double* lambdas, int n_iter,
+                                    double* map_inout, int ckpt_every, double* ckpt,
+                                    void* stream);
+mm_status mm_messenger_adjoint_ckpt(mm_plan p, const double* lambdas, int n_iter,
+                                    const double* ckpt, const double* grad_map_out,
+                                    float* grad_tod, double* grad_theta, int ckpt_every,
+                                    void* work, size_t work_bytes, void* stream);
+
 /* Bytes of device state mm_pcg_iterate needs (caller-owned, 256-byte aligned). */
 mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes);
 

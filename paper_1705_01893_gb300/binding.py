@@ -48,6 +48,10 @@ SIGNATURES = {
     "mm_adjoint_work_bytes": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _szp]),
     "mm_messenger_adjoint": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.c_int,
                                             _vp, ctypes.c_size_t, _vp]),
+    "mm_messenger_forward_ckpt": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                                 _vp]),
+    "mm_messenger_adjoint_ckpt": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp,
+                                                 ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "mm_pcg_state_bytes": (ctypes.c_int, [_vp, _szp]),
     "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
@@ -264,6 +268,34 @@ class Plan:
             _ptr(grad_tod), _ptr(grad_theta), int(ckpt_every), wp, int(n.value), _stream(stream)))
         self._adj_work = work   # keep alive until the stream has run the call
 
+    def forward_ckpt(self, map_inout, lambdas, ckpt_every: int = 10, stream=None):
+        """len(lambdas) messenger iterations on map_inout; returns the checkpoints m_0, m_E,
+        ... (E = ckpt_every) as a CUDA float64 tensor [ceil(K / E), n_pix, ncomp]."""
+        import torch
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        nseg = (len(lam) + ckpt_every - 1) // ckpt_every
+        ckpt = torch.empty((nseg,) + tuple(map_inout.shape), dtype=torch.float64,
+                           device=self.device)
+        _check("mm_messenger_forward_ckpt", load().mm_messenger_forward_ckpt(
+            self._h, lam.ctypes.data_as(_dp), len(lam), _ptr(map_inout), int(ckpt_every),
+            _ptr(ckpt), _stream(stream)))
+        return ckpt
+
+    def adjoint_ckpt(self, lambdas, ckpt, grad_map_out, grad_tod, grad_theta=None,
+                     ckpt_every: int = 10, stream=None):
+        """The backward of forward_ckpt: dL/dd (and dL/dtheta) from its checkpoints."""
+        import torch
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        n = ctypes.c_size_t()
+        _check("mm_adjoint_work_bytes", load().mm_adjoint_work_bytes(self._h, len(lam), int(ckpt_every),
+                                                                     ctypes.byref(n)))
+        work = torch.empty(int(n.value) + 256, dtype=torch.uint8, device=self.device)
+        wp = (work.data_ptr() + 255) // 256 * 256
+        _check("mm_messenger_adjoint_ckpt", load().mm_messenger_adjoint_ckpt(
+            self._h, lam.ctypes.data_as(_dp), len(lam), _ptr(ckpt), _ptr(grad_map_out),
+            _ptr(grad_tod), _ptr(grad_theta), int(ckpt_every), wp, int(n.value), _stream(stream)))
+        self._adj_work = work   # keep alive until the stream has run the call
+
     def pcg_state(self):
         import torch
         if self._pcg_state is None:
@@ -410,25 +442,38 @@ def messenger_fn():
     """torch.autograd.Function running K cooled messenger iterations on the GPU, with the
     hand-written adjoint as its backward.  apply(plan, lambdas, map_in, tod, theta) ->
     m_K; gradients flow to tod (float32 [n]) and theta (float64 [n_chunks, 3] =
-    sigma, f_knee, alpha), which must be the data and parameters the plan was set up with."""
+    sigma, f_knee, alpha), which must be the data and parameters the plan was set up with.
+    When theta needs a gradient the forward keeps checkpoints every CKPT_EVERY iterations
+    for the backward's recomputation; otherwise the backward needs no forward iterate."""
     import torch
 
     class MessengerFn(torch.autograd.Function):
         @staticmethod
         def forward(ctx, plan, lambdas, map_in, tod, theta):
             m = map_in.detach().clone()
-            plan.messenger(m, lambdas)
-            ctx.plan, ctx.lambdas = plan, np.asarray(lambdas, dtype=np.float64)
-            ctx.save_for_backward(map_in)
+            lam = np.asarray(lambdas, dtype=np.float64)
+            ctx.plan, ctx.lambdas = plan, lam
+            ctx.want_theta = bool(ctx.needs_input_grad[4])
+            if ctx.want_theta:
+                # checkpoints every CKPT_EVERY iterations, taken during this forward
+                ctx.save_for_backward(plan.forward_ckpt(m, lam, MessengerFn.CKPT_EVERY))
+            else:
+                plan.messenger(m, lam)     # dL/dd needs no forward iterate
+                ctx.save_for_backward(m)
             return m
 
         @staticmethod
         def backward(ctx, grad_m):
-            (map_in,) = ctx.saved_tensors
+            (ckpt,) = ctx.saved_tensors
             plan = ctx.plan
             gt = torch.empty(int(plan.offsets[-1]), dtype=torch.float32, device=grad_m.device)
-            gth = torch.empty(plan.n_chunks, 3, dtype=torch.float64, device=grad_m.device)
-            plan.adjoint(ctx.lambdas, map_in, grad_m.contiguous().to(torch.float64), gt, gth)
+            gth = None
+            if ctx.want_theta:
+                gth = torch.empty(plan.n_chunks, 3, dtype=torch.float64, device=grad_m.device)
+            plan.adjoint_ckpt(ctx.lambdas, ckpt, grad_m.contiguous().to(torch.float64), gt, gth,
+                              ckpt_every=MessengerFn.CKPT_EVERY)
             return None, None, None, gt, gth
+
+    MessengerFn.CKPT_EVERY = 10
 
     return MessengerFn

@@ -12,7 +12,9 @@
 // gather + column-DFT kernel for v and for P m (the forward spectrum needed by dt/dtheta),
 // a row kernel that transforms both and forms the filtered adjoint spectrum and the
 // theta sums, and an inverse column kernel that bins P^T t and accumulates dL/dd.  Forward
-// iterates are recomputed from checkpoints taken every `ckpt_every` iterations.
+// iterates are recomputed from checkpoints taken every `ckpt_every` iterations.  Without a
+// theta gradient the forward spectrum is not needed: the step then gathers and transforms
+// v alone (two rows per row job instead of four).
 #include <math.h>
 
 #include "mm_colcommon.cuh"
@@ -60,12 +62,15 @@ struct DstRowsAdj {           // inverse row DFT output with the conjugate four-
   }
 };
 
-template <int M2, int T>
-__global__ void __launch_bounds__(T, 1) k_row_adjoint(AdjRowParams q) {
+// THETA: also transform the forward rows (yR) and form the theta sums; otherwise only the
+// filtered adjoint spectrum b v~ of the two rows of yV.
+template <int M2, int T, bool THETA>
+__global__ void __launch_bounds__(T, THETA ? 1 : 2) k_row_adjoint(AdjRowParams q) {
   extern __shared__ float2 sm[];
   using Lay = RowLayout<M2>;
+  constexpr int NR = THETA ? 4 : 2;
   __shared__ double red[kAdjN - 1][32];
-  float2* tws = sm + 4 * M2;
+  float2* tws = sm + NR * M2;
   for (int i = threadIdx.x; i < tw_size(M2); i += T) tws[i] = q.g.tw_row[i];
   __syncthreads();
   const int jobs_pc = q.g.M1 / 2 + 1;
@@ -81,14 +86,14 @@ __global__ void __launch_bounds__(T, 1) k_row_adjoint(AdjRowParams q) {
     const bool self = rA == rB;
     float2* yV = q.yV + (int64_t)ci * M;
     const float2* yR = q.yR + (int64_t)ci * M;
-    smem_fft<M2, 4, Lay, T, -1>(sm, tws, Src4Rows{yV, yR, rA * M2, rB * M2});
+    smem_fft<M2, NR, Lay, T, -1>(sm, tws, Src4Rows{yV, yR, rA * M2, rB * M2});
 
     const float tau = (float)d.tau;
     const float lt = lam_inf ? 0.f : (float)(q.lambda * d.tau);
     const float lam = lam_inf ? 0.f : (float)q.lambda;
     const float sc = 1.0f / ((float)d.n * tau);        // irfft 1/n and T^-1
     float fk = 1.f, fs = 1.f;
-    const bool has_par = q.params != nullptr;
+    const bool has_par = THETA && q.params != nullptr;
     if (has_par) { fk = (float)q.params[4 * c + 1]; fs = (float)q.params[4 * c + 3]; }
     const float2* dt = q.dtab + d.spec;
     const float* nb = q.nbar + d.spec;
@@ -97,14 +102,19 @@ __global__ void __launch_bounds__(T, 1) k_row_adjoint(AdjRowParams q) {
 
     // terms of one Fourier mode (index kk, multiplicity wt); returns the adjoint output b V sc
     auto mode = [&](float2 V, float2 R, float2 D, float nbv, int kk, float wt) -> float2 {
-      float2 T, Y;
+      if constexpr (!THETA) {
+        if (lam_inf) return make_float2(0.f, 0.f);
+        const float b = nbv / (lt + nbv);
+        return make_float2(b * V.x * sc, b * V.y * sc);
+      }
+      float2 Tm, Y;
       if (lam_inf) {
-        T = D;
+        Tm = D;
         Y = make_float2(0.f, 0.f);
       } else {
         const float den = lt + nbv;
         const float a = lt / den, b = nbv / den;
-        T = make_float2(a * D.x + b * R.x, a * D.y + b * R.y);
+        Tm = make_float2(a * D.x + b * R.x, a * D.y + b * R.y);
         const float c1 = V.x * (R.x - D.x) + V.y * (R.y - D.y);   // Re(conj V (R - D))
         const float g1 = lt * nbv / (den * den);
         s0 += wt * c1 * g1;
@@ -115,7 +125,7 @@ __global__ void __launch_bounds__(T, 1) k_row_adjoint(AdjRowParams q) {
         stau -= wt * c1 * lam * nbv / (den * den);
         Y = make_float2(b * V.x * sc, b * V.y * sc);
       }
-      sT += wt * (V.x * T.x + V.y * T.y);
+      sT += wt * (V.x * Tm.x + V.y * Tm.y);
       return Y;
     };
 
@@ -129,10 +139,11 @@ __global__ void __launch_bounds__(T, 1) k_row_adjoint(AdjRowParams q) {
       const int rowq = qs ? rB : rA;
       const int sk = rA * M2 + p, sp = rowq * M2 + qi;
       const float2 ZVk = sm[Lay::at(0, p)], ZVp = sm[Lay::at(qs, qi)];
-      const float2 ZRk = sm[Lay::at(2, p)], ZRp = sm[Lay::at(2 + qs, qi)];
+      const float2 ZRk = THETA ? sm[Lay::at(2, p)] : make_float2(0.f, 0.f);
+      const float2 ZRp = THETA ? sm[Lay::at(2 + qs, qi)] : make_float2(0.f, 0.f);
       if (rA == 0 && p == 0) {
         // k = 0 and k = M, both real: X_0 = Re Z_0 + Im Z_0, X_M = Re Z_0 - Im Z_0
-        const float2 D = dt[0];
+        const float2 D = THETA ? dt[0] : make_float2(0.f, 0.f);
         const float n0 = nb[0], nM = q.nyq[c];
         const float2 Y0 = mode(make_float2(ZVk.x + ZVk.y, 0.f), make_float2(ZRk.x + ZRk.y, 0.f),
                                make_float2(D.x, 0.f), n0, 0, 1.f);
@@ -151,30 +162,37 @@ __global__ void __launch_bounds__(T, 1) k_row_adjoint(AdjRowParams q) {
       };
       float2 Vk, Vp, Rk, Rp;
       split(ZVk, ZVp, Vk, Vp);
-      split(ZRk, ZRp, Rk, Rp);
+      if (THETA) split(ZRk, ZRp, Rk, Rp);
+      else Rk = Rp = make_float2(0.f, 0.f);
       const bool same = (qs == 0 && qi == p);
       const int k = rA + M1 * p;
-      const float2 Yk = mode(Vk, Rk, dt[sk], nb[sk], k, 2.f);
-      const float2 Yp = same ? Yk : mode(Vp, Rp, dt[sp], nb[sp], M - k, 2.f);
+      const float2 Dk = THETA ? dt[sk] : make_float2(0.f, 0.f);
+      const float2 Dq = THETA && !same ? dt[sp] : make_float2(0.f, 0.f);
+      const float2 Yk = mode(Vk, Rk, Dk, nb[sk], k, 2.f);
+      const float2 Yp = same ? Yk : mode(Vp, Rp, Dq, nb[sp], M - k, 2.f);
       sm[Lay::at(0, p)] = cadd(cadd(Yk, cconj(Yp)), mul_i<+1>(cmulc(csub(Yk, cconj(Yp)), w)));
       if (!same)
         sm[Lay::at(qs, qi)] = csub(cadd(Yp, cconj(Yk)), mul_i<+1>(cmul(w, csub(Yp, cconj(Yk)))));
     }
-    // block sums (FP32 within a warp, FP64 across warps), one FP64 add per chunk and term
-    float v4[4] = {s0, sal, stau, sT};
+    if constexpr (THETA) {
+      // block sums (FP32 within a warp, FP64 across warps), one FP64 add per chunk and term
+      float v4[4] = {s0, sal, stau, sT};
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < 4; ++j) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v4[j] += __shfl_down_sync(0xffffffffu, v4[j], o);
-      if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = v4[j];
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-      double s = 0.0;
-      for (int i = 0; i < T / 32; ++i) s += red[threadIdx.x][i];
-      const int slot = threadIdx.x == 0 ? kAdjA0 : threadIdx.x == 1 ? kAdjAal
-                       : threadIdx.x == 2 ? kAdjAtau : kAdjAT;
-      atomicAdd(q.acc + kAdjN * c + slot, s);
+        for (int o = 16; o > 0; o >>= 1) v4[j] += __shfl_down_sync(0xffffffffu, v4[j], o);
+        if ((threadIdx.x & 31) == 0) red[j][threadIdx.x >> 5] = v4[j];
+      }
+      __syncthreads();
+      if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int i = 0; i < T / 32; ++i) s += red[threadIdx.x][i];
+        const int slot = threadIdx.x == 0 ? kAdjA0 : threadIdx.x == 1 ? kAdjAal
+                         : threadIdx.x == 2 ? kAdjAtau : kAdjAT;
+        atomicAdd(q.acc + kAdjN * c + slot, s);
+      }
+    } else {
+      __syncthreads();
     }
     smem_fft<M2, 2, Lay, T, +1>(sm, tws, SmemIO{}, DstRowsAdj{yV, &q.g, rA, rB, self});
     __syncthreads();
@@ -196,8 +214,8 @@ __device__ __forceinline__ float4 gather4_map(const ColParams& q, const void* ma
 }
 
 // Inverse column DFTs of the adjoint spectrum -> t = irfft(b v~)/tau; bin P^T t (the next
-// gbar), accumulate dL/dd += v/tau - t and <v, P m'> per chunk.
-template <int M1, int CB, int T, int NC>
+// gbar), accumulate dL/dd += v/tau - t and (THETA) <v, P m'> per chunk.
+template <int M1, int CB, int T, int NC, bool THETA>
 __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse_adjoint(ColParams q,
                                                                              AdjColExtra x) {
   extern __shared__ float2 sm[];
@@ -224,8 +242,10 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse_adjoint(C
       const float4 t4 = *reinterpret_cast<const float4*>(smf + e);
       scatter4<NC>(q, tbase + e, t4, e4 & 7);
       const float4 v4 = gather4_map<NC>(q, x.mapV4, tbase + e);
-      const float4 r4 = gather4_map<NC>(q, x.mapRp4, tbase + e);
-      dot += v4.x * r4.x + v4.y * r4.y + v4.z * r4.z + v4.w * r4.w;
+      if constexpr (THETA) {
+        const float4 r4 = gather4_map<NC>(q, x.mapRp4, tbase + e);
+        dot += v4.x * r4.x + v4.y * r4.y + v4.z * r4.z + v4.w * r4.w;
+      }
       // tile sample e -> original sample off + 2 (j1 M2 + cb CB) + (e mod 2 CB)
       const int j1 = e / RUN, wpos = e % RUN;
       float4* gt = reinterpret_cast<float4*>(x.grad_tod + d.off + 2ll * j1 * M2 + RUN * cb + wpos);
@@ -236,14 +256,16 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse_adjoint(C
       g.w += v4.w * itau - t4.w;
       *gt = g;
     }
+    if constexpr (THETA) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dot;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int i = 0; i < T / 32; ++i) s += red[i];
-      atomicAdd(x.acc + kAdjN * c + kAdjDot, s);
+      for (int o = 16; o > 0; o >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, o);
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dot;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < T / 32; ++i) s += red[i];
+        atomicAdd(x.acc + kAdjN * c + kAdjDot, s);
+      }
     }
     __syncthreads();
   }
@@ -309,7 +331,7 @@ __global__ void k_adj_theta(int n_chunks, const ChunkDesc* desc, const double* p
 template <int M2>
 static cudaError_t row_adjoint_m2(const mm_plan_s* p, const Batch& b, float2* yV,
                                   const float2* yR, double lambda, double* acc,
-                                  cudaStream_t st) {
+                                  cudaStream_t st) {   // yR == NULL: no theta sums
   constexpr int T = M2 / 8 < 32 ? 32 : (M2 / 8 > 1024 ? 1024 : M2 / 8);
   const Group& g = p->groups[b.group];
   AdjRowParams q;
@@ -325,8 +347,9 @@ static cudaError_t row_adjoint_m2(const mm_plan_s* p, const Batch& b, float2* yV
   q.params = p->theta_ok ? p->params : nullptr;
   q.lambda = lambda;
   q.acc = acc;
-  const size_t smem = sizeof(float2) * (4 * M2 + tw_size(M2));
-  auto k = k_row_adjoint<M2, T>;
+  const bool theta = yR != nullptr;
+  const size_t smem = sizeof(float2) * ((theta ? 4 : 2) * M2 + tw_size(M2));
+  auto k = theta ? k_row_adjoint<M2, T, true> : k_row_adjoint<M2, T, false>;
   int grid = 0;
   cudaError_t e = persistent_grid(k, T, smem, (g.M1 / 2 + 1) * b.count, &grid);
   if (e != cudaSuccess) return e;
@@ -351,7 +374,7 @@ static cudaError_t launch_row_adjoint(const mm_plan_s* p, const Batch& b, float2
   return cudaErrorInvalidValue;
 }
 
-template <int M1>
+template <int M1, bool THETA>
 static cudaError_t col_adjoint_m1(const mm_plan_s* p, const Batch& b, const AdjColExtra& x,
                                   cudaStream_t st) {
   constexpr int T = col_threads(M1);
@@ -374,29 +397,35 @@ static cudaError_t col_adjoint_m1(const mm_plan_s* p, const Batch& b, const AdjC
   int grid = 0;
   cudaError_t e;
   if (p->ncomp == 3) {
-    auto k = k_col_inverse_adjoint<M1, kColCB, T, 3>;
+    auto k = k_col_inverse_adjoint<M1, kColCB, T, 3, THETA>;
     if ((e = persistent_grid(k, T, smem, ntiles, &grid)) != cudaSuccess) return e;
     k<<<grid, T, smem, st>>>(q, x);
   } else {
-    auto k = k_col_inverse_adjoint<M1, kColCB, T, 1>;
+    auto k = k_col_inverse_adjoint<M1, kColCB, T, 1, THETA>;
     if ((e = persistent_grid(k, T, smem, ntiles, &grid)) != cudaSuccess) return e;
     k<<<grid, T, smem, st>>>(q, x);
   }
   return cudaGetLastError();
 }
 
-static cudaError_t launch_col_adjoint(const mm_plan_s* p, const Batch& b, const AdjColExtra& x,
-                                      cudaStream_t st) {
+template <bool THETA>
+static cudaError_t col_adjoint(const mm_plan_s* p, const Batch& b, const AdjColExtra& x,
+                               cudaStream_t st) {
   switch (p->groups[b.group].M1) {
-    case 16: return col_adjoint_m1<16>(p, b, x, st);
-    case 32: return col_adjoint_m1<32>(p, b, x, st);
-    case 64: return col_adjoint_m1<64>(p, b, x, st);
-    case 128: return col_adjoint_m1<128>(p, b, x, st);
-    case 256: return col_adjoint_m1<256>(p, b, x, st);
-    case 512: return col_adjoint_m1<512>(p, b, x, st);
-    case 1024: return col_adjoint_m1<1024>(p, b, x, st);
+    case 16: return col_adjoint_m1<16, THETA>(p, b, x, st);
+    case 32: return col_adjoint_m1<32, THETA>(p, b, x, st);
+    case 64: return col_adjoint_m1<64, THETA>(p, b, x, st);
+    case 128: return col_adjoint_m1<128, THETA>(p, b, x, st);
+    case 256: return col_adjoint_m1<256, THETA>(p, b, x, st);
+    case 512: return col_adjoint_m1<512, THETA>(p, b, x, st);
+    case 1024: return col_adjoint_m1<1024, THETA>(p, b, x, st);
   }
   return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_col_adjoint(const mm_plan_s* p, const Batch& b, const AdjColExtra& x,
+                                      bool theta, cudaStream_t st) {
+  return theta ? col_adjoint<true>(p, b, x, st) : col_adjoint<false>(p, b, x, st);
 }
 
 }  // namespace mm
@@ -451,51 +480,55 @@ extern "C" mm_status mm_adjoint_work_bytes(mm_plan p, int n_iter, int ckpt_every
     }                                                                                      \
   } while (0)
 
-extern "C" mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int n_iter,
-                                          const double* map_in, const double* grad_map_out,
-                                          float* grad_tod, double* grad_theta, int ckpt_every,
-                                          void* work, size_t work_bytes, void* stream) {
-  if (!p || !lambdas || !map_in || !grad_map_out || !grad_tod || !work || n_iter < 1 ||
-      ckpt_every < 1) {
-    mm_set_error("mm_messenger_adjoint: NULL pointer or non-positive count");
-    return MM_ERR_ARG;
-  }
-  if (((uintptr_t)grad_tod & 15) != 0) {
-    mm_set_error("mm_messenger_adjoint: grad_tod must be 16-byte aligned");
+// Checks shared by the adjoint entry points.
+static mm_status adjoint_check(mm_plan p, const double* lambdas, int n_iter, int ckpt_every,
+                               const char* fn) {
+  if (!p || !lambdas || n_iter < 1 || ckpt_every < 1) {
+    mm_set_error("%s: NULL pointer or non-positive count", fn);
     return MM_ERR_ARG;
   }
   if (!p->noise_set) {
-    mm_set_error("mm_messenger_adjoint: mm_set_noise_psd has not run");
+    mm_set_error("%s: mm_set_noise_psd has not run", fn);
     return MM_ERR_STATE;
   }
-  if (grad_theta && !p->theta_ok) {
-    mm_set_error("mm_messenger_adjoint: theta gradients need the parametric noise model with "
-                 "tau = sigma^2");
-    return MM_ERR_UNSUPPORTED;
-  }
   if (p->n_gen > 0) {
-    mm_set_error("mm_messenger_adjoint: chunk lengths that are not powers of two are not supported");
+    mm_set_error("%s: chunk lengths that are not powers of two are not supported", fn);
     return MM_ERR_UNSUPPORTED;
   }
   for (int g = 0; g < p->n_groups; ++g)
     if (p->groups[g].M2 > 4096) {
-      mm_set_error("mm_messenger_adjoint: chunks longer than 2^22 samples are not supported");
+      mm_set_error("%s: chunks longer than 2^22 samples are not supported", fn);
       return MM_ERR_UNSUPPORTED;
     }
   for (int i = 0; i < n_iter; ++i)
     if (!(lambdas[i] >= 1.0 || isinf(lambdas[i]))) {
-      mm_set_error("mm_messenger_adjoint: lambdas[%d] must be >= 1 or inf", i);
+      mm_set_error("%s: lambdas[%d] must be >= 1 or inf", fn, i);
       return MM_ERR_ARG;
     }
-  const AdjLayout L = adj_layout(p, n_iter, ckpt_every);
-  if (((uintptr_t)work & 255) != 0 || work_bytes < L.total) {
-    mm_set_error("mm_messenger_adjoint: work must be 256-byte aligned and >= %zu bytes", L.total);
-    return MM_ERR_NOMEM;
-  }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  char* w = static_cast<char*>(work);
+  return MM_OK;
+}
+
+// n_iter iterations on map_inout in segments of ckpt_every, m_{kE} copied to ckpt[k] first.
+static mm_status forward_ckpt(mm_plan p, const double* lambdas, int n_iter, double* map_inout,
+                              int every, double* ckpt, cudaStream_t s) {
   const size_t mapb = sizeof(double) * p->ncomp * (size_t)p->n_pix;
-  double* ckpt = reinterpret_cast<double*>(w + L.ckpt);
+  const size_t mstride = (size_t)p->ncomp * (size_t)p->n_pix;
+  for (int i0 = 0; i0 < n_iter; i0 += every) {
+    ADJ_CUDA(cudaMemcpyAsync(ckpt + (i0 / every) * mstride, map_inout, mapb,
+                             cudaMemcpyDeviceToDevice, s));
+    const int n = i0 + every < n_iter ? every : n_iter - i0;
+    mm_status st = mm_messenger_iterate(p, lambdas + i0, n, MM_FP32_MIXED, map_inout, nullptr, s);
+    if (st != MM_OK) return st;
+  }
+  return MM_OK;
+}
+
+// The backward sweep from the checkpoints m_0, m_E, ... (segments recomputed in `work`).
+static mm_status adjoint_backward(mm_plan p, const double* lambdas, int n_iter,
+                                  const double* ckpt, const double* grad_map_out,
+                                  float* grad_tod, double* grad_theta, int ckpt_every,
+                                  const AdjLayout& L, char* w, cudaStream_t s) {
+  const size_t mapb = sizeof(double) * p->ncomp * (size_t)p->n_pix;
   double* seg = reinterpret_cast<double*>(w + L.seg);
   double* g = reinterpret_cast<double*>(w + L.g);
   void* u4 = w + L.u4;
@@ -505,55 +538,146 @@ extern "C" mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int 
   double* acc = reinterpret_cast<double*>(w + L.acc);
   const int64_t len = p->ncomp * p->n_pix;
   const size_t mstride = (size_t)len;
+  const bool theta = grad_theta != nullptr;
 
-  // forward sweep: checkpoint m_i at i = 0, E, 2E, ...
-  ADJ_CUDA(cudaMemcpyAsync(seg, map_in, mapb, cudaMemcpyDeviceToDevice, s));
-  for (int i = 0; i < n_iter; ++i) {
-    if (i % ckpt_every == 0)
-      ADJ_CUDA(cudaMemcpyAsync(ckpt + (i / ckpt_every) * mstride, seg, mapb,
-                               cudaMemcpyDeviceToDevice, s));
-    mm_status st = mm_messenger_iterate(p, lambdas + i, 1, MM_FP32_MIXED, seg, nullptr, stream);
-    if (st != MM_OK) return st;
-  }
-  // backward sweep
   ADJ_CUDA(cudaMemcpyAsync(g, grad_map_out, mapb, cudaMemcpyDeviceToDevice, s));
   ADJ_CUDA(cudaMemsetAsync(grad_tod, 0, sizeof(float) * (size_t)p->n_total, s));
   ADJ_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * kAdjN * p->n_chunks, s));
   const unsigned nbp = (unsigned)((p->n_pix + 255) / 256), nbl = (unsigned)((len + 255) / 256);
+  // transposed step i (mi = m_i, mo = m_{i+1}: read only for the theta terms)
+  auto step = [&](int i, const double* mi, const double* mo) -> mm_status {
+    if (p->ncomp == 3)
+      k_adj_prep<3><<<nbp, 256, 0, s>>>(p->n_pix, p->W, g, mi, mo, p->valid, u4, m4, mp4);
+    else
+      k_adj_prep<1><<<nbp, 256, 0, s>>>(p->n_pix, p->W, g, mi, mo, p->valid, u4, m4, mp4);
+    ADJ_CUDA(cudaGetLastError());
+    const AdjColExtra x{u4, mp4, grad_tod, acc};
+    for (int b = 0; b < p->n_batches; ++b) {
+      const Batch& B = p->h_batches[b];
+      ADJ_CUDA(launch_col_forward_ex(p, B, kSrcGather, nullptr, u4, p->ybuf, s));
+      if (theta) ADJ_CUDA(launch_col_forward_ex(p, B, kSrcGather, nullptr, m4, yR, s));
+      ADJ_CUDA(launch_row_adjoint(p, B, p->ybuf, theta ? yR : nullptr, lambdas[i], acc, s));
+      ADJ_CUDA(launch_col_adjoint(p, B, x, theta, s));
+    }
+    k_adj_take_g<<<nbl, 256, 0, s>>>(len, p->ncomp, p->acc, p->valid, g);
+    ADJ_CUDA(cudaGetLastError());
+    return MM_OK;
+  };
+  if (!theta) {
+    // with lambda held constant the step is affine in (m, d): its transpose does not depend
+    // on the iterates, so no checkpoint is read and nothing is recomputed
+    for (int i = n_iter - 1; i >= 0; --i) {
+      mm_status st = step(i, g, g);
+      if (st != MM_OK) return st;
+    }
+    return MM_OK;
+  }
   for (int sg = L.nseg - 1; sg >= 0; --sg) {
     const int i0 = sg * ckpt_every;
     const int i1 = i0 + ckpt_every < n_iter ? i0 + ckpt_every : n_iter;
     ADJ_CUDA(cudaMemcpyAsync(seg, ckpt + sg * mstride, mapb, cudaMemcpyDeviceToDevice, s));
-    for (int i = i0; i < i1; ++i) {   // recompute the segment's iterates
+    for (int i = i0; i < i1; ++i) {   // recompute the segment's iterates m_{i0+1} .. m_{i1}
       double* nxt = seg + (i - i0 + 1) * mstride;
       ADJ_CUDA(cudaMemcpyAsync(nxt, seg + (i - i0) * mstride, mapb, cudaMemcpyDeviceToDevice, s));
-      mm_status st = mm_messenger_iterate(p, lambdas + i, 1, MM_FP32_MIXED, nxt, nullptr, stream);
+      mm_status st = mm_messenger_iterate(p, lambdas + i, 1, MM_FP32_MIXED, nxt, nullptr, s);
       if (st != MM_OK) return st;
     }
     for (int i = i1 - 1; i >= i0; --i) {
-      const double* mi = seg + (i - i0) * mstride;
-      const double* mo = seg + (i - i0 + 1) * mstride;
-      if (p->ncomp == 3)
-        k_adj_prep<3><<<nbp, 256, 0, s>>>(p->n_pix, p->W, g, mi, mo, p->valid, u4, m4, mp4);
-      else
-        k_adj_prep<1><<<nbp, 256, 0, s>>>(p->n_pix, p->W, g, mi, mo, p->valid, u4, m4, mp4);
-      ADJ_CUDA(cudaGetLastError());
-      const AdjColExtra x{u4, mp4, grad_tod, acc};
-      for (int b = 0; b < p->n_batches; ++b) {
-        const Batch& B = p->h_batches[b];
-        ADJ_CUDA(launch_col_forward_ex(p, B, kSrcGather, nullptr, u4, p->ybuf, s));
-        ADJ_CUDA(launch_col_forward_ex(p, B, kSrcGather, nullptr, m4, yR, s));
-        ADJ_CUDA(launch_row_adjoint(p, B, p->ybuf, yR, lambdas[i], acc, s));
-        ADJ_CUDA(launch_col_adjoint(p, B, x, s));
-      }
-      k_adj_take_g<<<nbl, 256, 0, s>>>(len, p->ncomp, p->acc, p->valid, g);
-      ADJ_CUDA(cudaGetLastError());
+      mm_status st = step(i, seg + (i - i0) * mstride, seg + (i - i0 + 1) * mstride);
+      if (st != MM_OK) return st;
     }
   }
-  if (grad_theta) {
+  if (theta) {
     k_adj_theta<<<(p->n_chunks + 127) / 128, 128, 0, s>>>(p->n_chunks, p->d_desc, p->params, acc,
                                                         grad_theta);
     ADJ_CUDA(cudaGetLastError());
   }
   return MM_OK;
+}
+
+static mm_status adjoint_outputs_check(mm_plan p, const double* grad_map_out,
+                                       const float* grad_tod, const double* grad_theta,
+                                       void* work, size_t work_bytes, const AdjLayout& L,
+                                       const char* fn) {
+  if (!grad_map_out || !grad_tod || !work) {
+    mm_set_error("%s: NULL pointer", fn);
+    return MM_ERR_ARG;
+  }
+  if (((uintptr_t)grad_tod & 15) != 0) {
+    mm_set_error("%s: grad_tod must be 16-byte aligned", fn);
+    return MM_ERR_ARG;
+  }
+  if (grad_theta && !p->theta_ok) {
+    mm_set_error("%s: theta gradients need the parametric noise model with tau = sigma^2", fn);
+    return MM_ERR_UNSUPPORTED;
+  }
+  if (((uintptr_t)work & 255) != 0 || work_bytes < L.total) {
+    mm_set_error("%s: work must be 256-byte aligned and >= %zu bytes", fn, L.total);
+    return MM_ERR_NOMEM;
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int n_iter,
+                                          const double* map_in, const double* grad_map_out,
+                                          float* grad_tod, double* grad_theta, int ckpt_every,
+                                          void* work, size_t work_bytes, void* stream) {
+  const char* fn = "mm_messenger_adjoint";
+  mm_status st = adjoint_check(p, lambdas, n_iter, ckpt_every, fn);
+  if (st != MM_OK) return st;
+  if (!map_in) {
+    mm_set_error("%s: map_in is NULL", fn);
+    return MM_ERR_ARG;
+  }
+  const AdjLayout L = adj_layout(p, n_iter, ckpt_every);
+  st = adjoint_outputs_check(p, grad_map_out, grad_tod, grad_theta, work, work_bytes, L, fn);
+  if (st != MM_OK) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  char* w = static_cast<char*>(work);
+  double* ckpt = reinterpret_cast<double*>(w + L.ckpt);
+  double* seg = reinterpret_cast<double*>(w + L.seg);
+  const size_t mapb = sizeof(double) * p->ncomp * (size_t)p->n_pix;
+  if (grad_theta) {
+    // forward sweep (in the segment buffer), checkpoints into the work space; the data
+    // gradient alone needs no forward iterate
+    ADJ_CUDA(cudaMemcpyAsync(seg, map_in, mapb, cudaMemcpyDeviceToDevice, s));
+    st = forward_ckpt(p, lambdas, n_iter, seg, ckpt_every, ckpt, s);
+    if (st != MM_OK) return st;
+  }
+  return adjoint_backward(p, lambdas, n_iter, ckpt, grad_map_out, grad_tod, grad_theta,
+                          ckpt_every, L, w, s);
+}
+
+extern "C" mm_status mm_messenger_forward_ckpt(mm_plan p, const double* lambdas, int n_iter,
+                                               double* map_inout, int ckpt_every, double* ckpt,
+                                               void* stream) {
+  const char* fn = "mm_messenger_forward_ckpt";
+  mm_status st = adjoint_check(p, lambdas, n_iter, ckpt_every, fn);
+  if (st != MM_OK) return st;
+  if (!map_inout || !ckpt) {
+    mm_set_error("%s: NULL map or checkpoint buffer", fn);
+    return MM_ERR_ARG;
+  }
+  return forward_ckpt(p, lambdas, n_iter, map_inout, ckpt_every, ckpt,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" mm_status mm_messenger_adjoint_ckpt(mm_plan p, const double* lambdas, int n_iter,
+                                               const double* ckpt, const double* grad_map_out,
+                                               float* grad_tod, double* grad_theta,
+                                               int ckpt_every, void* work, size_t work_bytes,
+                                               void* stream) {
+  const char* fn = "mm_messenger_adjoint_ckpt";
+  mm_status st = adjoint_check(p, lambdas, n_iter, ckpt_every, fn);
+  if (st != MM_OK) return st;
+  if (!ckpt) {
+    mm_set_error("%s: ckpt is NULL", fn);
+    return MM_ERR_ARG;
+  }
+  const AdjLayout L = adj_layout(p, n_iter, ckpt_every);
+  st = adjoint_outputs_check(p, grad_map_out, grad_tod, grad_theta, work, work_bytes, L, fn);
+  if (st != MM_OK) return st;
+  return adjoint_backward(p, lambdas, n_iter, ckpt, grad_map_out, grad_tod, grad_theta,
+                          ckpt_every, L, static_cast<char*>(work),
+                          reinterpret_cast<cudaStream_t>(stream));
 }

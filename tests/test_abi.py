@@ -71,6 +71,10 @@ def test_null_arguments_rejected_on_host(lib):
     r = lib.mm_plan_pointing(ctypes.byref(h), 1, offp, None, None, None, 0, 16, 1, 1e-3, None, 0, None)
     assert r == binding.MM_ERR_ARG
     assert lib.mm_messenger_iterate(None, None, 0, 0, None, None, None) == binding.MM_ERR_ARG
+    lam = (ctypes.c_double * 1)(1.0)
+    assert lib.mm_messenger_forward_ckpt(None, lam, 1, None, 1, None, None) == binding.MM_ERR_ARG
+    assert lib.mm_messenger_adjoint_ckpt(None, lam, 1, None, None, None, None, 1, None, 0,
+                                         None) == binding.MM_ERR_ARG
     lib.mm_plan_destroy(None)
 
 

@@ -90,6 +90,72 @@ def test_autograd_function_backward():
     assert np.max(np.abs(theta.grad.cpu().numpy() - dth)) <= 1e-6 * np.max(np.abs(dth))
 
 
+def test_data_gradient_without_theta_matches():
+    """With grad_theta = NULL the backward runs no forward iterate (the transposed step does
+    not depend on them): dL/dd must equal the one computed beside the theta terms."""
+    s = synth.config_iqu(16, 2, 1 << 12, 24)
+    prob = O.problem_from_synth(s)
+    lam = O.cooling_schedule(O.lambda_max(prob), 3, 3)
+    m_true = s["m_true"] * prob.valid[:, None]
+    dd, _, plan = gpu_grads(s, lam, m_true, ckpt_every=4)
+    m0 = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    m = m0.clone()
+    plan.messenger(m, lam)
+    g = m - torch.as_tensor(m_true, device=DEV)
+    gt = torch.empty(len(s["pix"]), dtype=torch.float32, device=DEV)
+    plan.adjoint(lam, m0, g, gt, None, ckpt_every=4)
+    torch.cuda.synchronize()
+    d2 = gt.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(d2 - dd) <= 1e-6 * np.linalg.norm(dd)
+
+
+def test_forward_ckpt_then_backward_matches_all_in_one():
+    """mm_messenger_forward_ckpt + mm_messenger_adjoint_ckpt against mm_messenger_adjoint:
+    the same final map and the same gradients (checkpoint spacing 4 over 11 iterations, so
+    the last segment is short)."""
+    s = synth.config_iqu(16, 2, 1 << 12, 25)
+    prob = O.problem_from_synth(s)
+    lam = O.cooling_schedule(O.lambda_max(prob), 2, 5)
+    assert len(lam) == 11
+    m_true = s["m_true"] * prob.valid[:, None]
+    dd, dth, plan = gpu_grads(s, lam, m_true, ckpt_every=4)
+    m0 = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    m_ref = m0.clone()
+    plan.messenger(m_ref, lam)
+    m = m0.clone()
+    ckpt = plan.forward_ckpt(m, lam, 4)
+    assert ckpt.shape == (3, s["npix"], 3)
+    torch.cuda.synchronize()
+    assert torch.equal(m, m_ref)
+    assert torch.equal(ckpt[0], m0)
+    g = m - torch.as_tensor(m_true, device=DEV)
+    gt = torch.empty(len(s["pix"]), dtype=torch.float32, device=DEV)
+    gth = torch.empty(len(s["offsets"]) - 1, 3, dtype=torch.float64, device=DEV)
+    plan.adjoint_ckpt(lam, ckpt, g, gt, gth, ckpt_every=4)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(gt.cpu().numpy() - dd) <= 1e-7 * np.linalg.norm(dd)
+    assert np.max(np.abs(gth.cpu().numpy() - dth)) <= 1e-7 * np.max(np.abs(dth))
+
+
+def test_autograd_function_data_gradient_only():
+    """theta without requires_grad: the autograd backward takes the path without forward
+    iterates and gives the same dL/dd."""
+    s = synth.config_iqu(16, 2, 1 << 12, 23)
+    prob = O.problem_from_synth(s)
+    lam = O.cooling_schedule(O.lambda_max(prob), 2, 2)
+    m_true = torch.as_tensor(s["m_true"] * prob.valid[:, None], device=DEV)
+    plan = binding.plan_from_synth(s, DEV)
+    tod = plan.tod.clone().requires_grad_(True)
+    theta = torch.as_tensor(s["params"][:, :3].copy(), device=DEV)
+    m0 = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    mK = binding.messenger_fn().apply(plan, lam, m0, tod, theta)
+    loss = 0.5 * ((mK - m_true) ** 2).sum()
+    loss.backward()
+    assert theta.grad is None
+    dd, _, _ = gpu_grads(s, lam, m_true.cpu().numpy())
+    assert np.linalg.norm(tod.grad.cpu().numpy() - dd) <= 1e-6 * np.linalg.norm(dd)
+
+
 @pytest.mark.slow
 def test_adjoint_full_size_dot_product():
     """256^2 IQU, 4 detectors x 2^20 samples, 20 cooled iterations, checkpoint every 10:
