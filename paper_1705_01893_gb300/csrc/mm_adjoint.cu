@@ -308,8 +308,9 @@ __global__ void k_adj_take_g(int64_t len, int ncomp, double* __restrict__ acc,
                              const uint8_t* __restrict__ valid, double* __restrict__ g) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= len) return;
-  g[i] = valid[i / ncomp] ? acc[i] : 0.0;
-  acc[i] = 0.0;
+  const int64_t a = (i % ncomp) * (len / ncomp) + i / ncomp;   // planar accumulators
+  g[i] = valid[i / ncomp] ? acc[a] : 0.0;
+  acc[a] = 0.0;
 }
 
 // dL/dtheta from the per-chunk sums (tau = sigma^2, Nbar = sigma^2 (f_knee / f)^alpha).
@@ -392,6 +393,7 @@ static cudaError_t col_adjoint_m1(const mm_plan_s* p, const Batch& b, const AdjC
   q.tod = nullptr;
   q.ybuf = p->ybuf;
   q.acc = p->acc;
+  q.acc_stride = p->n_pix;
   const int ntiles = (g.M2 / kColCB) * b.count;
   const size_t smem = sizeof(float2) * M1 * kColCB;
   int grid = 0;

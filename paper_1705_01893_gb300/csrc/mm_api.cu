@@ -172,7 +172,7 @@ static size_t tw_count(int M, int M1, int M2, bool general) {
 struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
       ybuf, scal, tpix, tcos, tsin, lam, iter, map64, groups, gen, gen_rec, gen_ctab, gen_rtab,
-      adapt, total, ybytes;
+      adapt, queue, total, ybytes;
   int64_t gen_ccap, gen_rcap;
   int lam_cap;
   int n_groups;
@@ -321,6 +321,7 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->gen_ctab = take(sizeof(int2) * ctiles);
   L->gen_rtab = take(sizeof(int4) * rjobs);
   L->adapt = take(sizeof(AdaptState));
+  L->queue = take(64);
   L->total = o;
   return MM_OK;
 }
@@ -605,7 +606,7 @@ __global__ void k_bin_apply(int64_t n_pix, double* __restrict__ acc, const doubl
   constexpr int B = NC == 3 ? 6 : 1;
   double a[NC], w[B], m[NC];
 #pragma unroll
-  for (int i = 0; i < NC; ++i) { a[i] = acc[NC * p + i]; acc[NC * p + i] = 0.0; }
+  for (int i = 0; i < NC; ++i) { a[i] = acc[i * n_pix + p]; acc[i * n_pix + p] = 0.0; }
 #pragma unroll
   for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
   sym_apply<NC>(w, a, m);
@@ -626,7 +627,7 @@ __global__ void k_bin_resid(int64_t n_pix, double* __restrict__ acc, const doubl
   constexpr int B = NC == 3 ? 6 : 1;
   double a[NC], w[B], u[NC], m[NC];
 #pragma unroll
-  for (int i = 0; i < NC; ++i) { a[i] = acc[NC * p + i]; acc[NC * p + i] = 0.0; }
+  for (int i = 0; i < NC; ++i) { a[i] = acc[i * n_pix + p]; acc[i * n_pix + p] = 0.0; }
 #pragma unroll
   for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
   sym_apply<NC>(w, a, u);
@@ -726,8 +727,9 @@ __global__ void k_finish_b(int64_t len, int ncomp, double* __restrict__ acc,
                            const uint8_t* __restrict__ valid, double* __restrict__ b) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= len) return;
-  b[i] = valid[i / ncomp] ? acc[i] : 0.0;
-  acc[i] = 0.0;
+  const int64_t a = (i % ncomp) * (len / ncomp) + i / ncomp;   // planar accumulators
+  b[i] = valid[i / ncomp] ? acc[a] : 0.0;
+  acc[a] = 0.0;
 }
 
 // ------------------------------------------------------------------------ PCG kernels
@@ -772,8 +774,8 @@ __global__ void k_pcg_init(int64_t n_pix, double* __restrict__ acc, const double
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
       const int64_t j = NC * p + i;
-      rr[i] = ok ? bvec[j] - acc[j] : 0.0;
-      acc[j] = 0.0;
+      rr[i] = ok ? bvec[j] - acc[i * n_pix + p] : 0.0;
+      acc[i * n_pix + p] = 0.0;
     }
     block_apply<NC>(Minv, p, rr, zz);
 #pragma unroll
@@ -806,8 +808,9 @@ __global__ void k_pcg_q(int64_t len, int ncomp, double* __restrict__ acc, const 
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double s = 0.0;
   if (i < len) {
-    const double qq = valid[i / ncomp] ? acc[i] : 0.0;
-    acc[i] = 0.0;
+    const int64_t a = (i % ncomp) * (len / ncomp) + i / ncomp;   // planar accumulators
+    const double qq = valid[i / ncomp] ? acc[a] : 0.0;
+    acc[a] = 0.0;
     q[i] = qq;
     s = pv[i] * qq;
   }
@@ -1042,6 +1045,7 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
   p->map64 = reinterpret_cast<double*>(ws + L.map64);
   p->adapt_exec = nullptr;
   p->adapt_st = ws + L.adapt;
+  p->row_queue = reinterpret_cast<unsigned*>(ws + L.queue);
   p->scal = reinterpret_cast<double*>(ws + L.scal);
   p->params = reinterpret_cast<double*>(ws + L.params);
   p->tpix = reinterpret_cast<int32_t*>(ws + L.tpix);
@@ -1176,6 +1180,7 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
   if ((e = cudaMemsetAsync(p->hits, 0, sizeof(int32_t) * n_pix, s)) != cudaSuccess) return fail("memset", e);
   if ((e = cudaMemsetAsync(p->scal, 0, sizeof(double) * kScalCount, s)) != cudaSuccess) return fail("memset", e);
   if ((e = cudaMemsetAsync(p->acc, 0, sizeof(double) * ncomp * n_pix, s)) != cudaSuccess) return fail("memset", e);
+  if ((e = cudaMemsetAsync(p->row_queue, 0, 64, s)) != cudaSuccess) return fail("memset", e);
   if (L.n_total > 0)
     k_hits<<<blocks_for(L.n_total, 256), 256, 0, s>>>(pix, L.n_total, n_pix, p->hits, p->scal + kScalTmp);
   if (L.n_total > 0 && p->composite)
@@ -1432,7 +1437,7 @@ __global__ void k_bin_md(int64_t n_pix, double* __restrict__ acc, const double* 
     constexpr int B = NC == 3 ? 6 : 1;
     double a[NC], w[B], m[NC];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) { a[i] = acc[NC * p + i]; acc[NC * p + i] = 0.0; }
+    for (int i = 0; i < NC; ++i) { a[i] = acc[i * n_pix + p]; acc[i * n_pix + p] = 0.0; }
 #pragma unroll
     for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
     sym_apply<NC>(w, a, m);

@@ -36,6 +36,7 @@ struct GenParams {
   const float* tod;
   float2* ybuf;
   double* acc;
+  int64_t acc_stride;   // planar accumulators: component k of pixel p at k * acc_stride + p
   float2* dtab;
   const float* __restrict__ nbar;
   const float* __restrict__ nyq;
@@ -333,7 +334,7 @@ __device__ __forceinline__ void gen_scatter(const GenParams& q, const ChunkDesc&
       const int so = __shfl_down_sync(0xffffffffu, seg, o);
       if (lane + o < 32 && so == seg) { v0 += a0; v1 += a1; v2 += a2; }
     }
-    if (head) emit_run<NC>(q.acc, p, v0, v1, v2);
+    if (head) emit_run<NC>(q.acc, q.acc_stride, p, v0, v1, v2);
   }
 }
 
@@ -588,6 +589,7 @@ static GenParams gen_params(const mm_plan_s* p, const Batch& b, const int2* item
   q.map4 = p->map4;
   q.ybuf = p->ybuf;
   q.acc = p->acc;
+  q.acc_stride = p->n_pix;
   q.dtab = p->dtab;
   q.nbar = p->nbar;
   q.nyq = p->nyq;

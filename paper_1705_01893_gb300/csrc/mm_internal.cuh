@@ -141,7 +141,7 @@ struct mm_plan_s {
   uint8_t* valid;
   double* W;        // [n_pix][6] (IQU, symmetric upper triangle 00 01 02 11 12 22) or [n_pix]
   double* Minv;     // PCG block preconditioner, same layout
-  double* acc;      // [n_pix][ncomp] FP64 accumulators of P^T T^-1 t
+  double* acc;      // [ncomp][n_pix] (planar) FP64 accumulators of P^T T^-1 t
   double* acc12;    // [n_pix][12] set-up scratch: P^T T^-1 P and sum c0 P^T P (6 each)
   void* map4;       // float4 [n_pix] (IQU) or float [n_pix] (T)
   double* bvec;     // [n_pix][ncomp] b = P^T N^-1 d
@@ -163,6 +163,8 @@ struct mm_plan_s {
   // adaptive cooling: graph with a device-side loop (conditional WHILE node) and its state
   cudaGraphExec_t adapt_exec;
   void* adapt_st;      // device mm::AdaptState followed by the level table
+  unsigned* row_queue; // device [2]: the row kernel's job counter and finished-CTA count
+                       // (zero between launches: the last CTA of each launch resets both)
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;
