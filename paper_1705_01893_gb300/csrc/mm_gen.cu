@@ -239,6 +239,65 @@ __device__ __forceinline__ float gen_pm(const GenParams& q, int64_t s) {
   return fmaf(q.gb, gen_pm1<NC>(q, q.pix2, q.cos2, q.sin2, s), q.ga * v);
 }
 
+// (P m) of a tile of one pointing component into tile a (element e = j1 NB + c holds samples
+// 2 (j1 M2 + j2_0 + c) + {0, 1}, or the one sample j1 M2 + j2_0 + c of an odd-length chunk).
+// U elements per thread are in flight at once: their pointing loads first, then the map
+// loads that depend on them (one element at a time leaves both round trips exposed).
+template <int NC>
+__device__ __forceinline__ void gen_gather_tile(const GenParams& q, const ChunkDesc& d, int j2_0,
+                                                int width, float2* a, int NB, int lnb, int T) {
+  constexpr int U = 4;
+  const int n = d.M1 * NB;
+  const int nh = d.cplx ? 1 : 2;
+  for (int e0 = threadIdx.x; e0 < n; e0 += U * T) {
+    int pi[U][2];
+    float cw[U][2], sw[U][2];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * T;
+      const int j1 = e >> lnb, c = e & (NB - 1);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        pi[u][h] = -1;
+        cw[u][h] = sw[u][h] = 0.f;
+        if (e < n && c < width && h < nh) {
+          const int64_t j = (int64_t)j1 * d.M2 + j2_0 + c;
+          const int64_t s = d.cplx ? d.off + j : d.off + 2 * j + h;
+          pi[u][h] = __ldg(q.pix + s);
+          if constexpr (NC == 3) {
+            if (q.half_w) {
+              cw[u][h] = __half2float(static_cast<const __half*>(q.cosw)[s]);
+              sw[u][h] = __half2float(static_cast<const __half*>(q.sinw)[s]);
+            } else {
+              cw[u][h] = __ldg(static_cast<const float*>(q.cosw) + s);
+              sw[u][h] = __ldg(static_cast<const float*>(q.sinw) + s);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * T;
+      if (e >= n) continue;
+      float z[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int pp = pi[u][h];
+        if (pp < 0) {
+          z[h] = 0.f;
+        } else if constexpr (NC == 1) {
+          z[h] = __ldg(reinterpret_cast<const float*>(q.map4) + pp);
+        } else {
+          const float4 m = __ldg(reinterpret_cast<const float4*>(q.map4) + pp);
+          z[h] = fmaf(sw[u][h], m.z, fmaf(cw[u][h], m.y, m.x));
+        }
+      }
+      a[e] = make_float2(z[0], z[1]);   // odd-length chunk: z[1] = 0 (imaginary part)
+    }
+  }
+}
+
 // ------------------------------------------------------------ kernel A: columns forward
 template <int NC, int SRC>
 __global__ void __launch_bounds__(512) k_gen_col_forward(GenParams q) {
@@ -253,7 +312,9 @@ __global__ void __launch_bounds__(512) k_gen_col_forward(GenParams q) {
     const int width = min(NB, M2 - j2_0);
     float2* a = gsm;
     float2* b = gsm + M1 * NB;
-    for (int e = threadIdx.x; e < M1 * NB; e += T) {
+    if (SRC == kSrcGather && !q.composite) {
+      gen_gather_tile<NC>(q, d, j2_0, width, a, NB, lnb, T);
+    } else for (int e = threadIdx.x; e < M1 * NB; e += T) {
       const int j1 = e >> lnb, c = e & (NB - 1);
       float2 z = make_float2(0.f, 0.f);
       if (c < width) {
@@ -296,45 +357,59 @@ __device__ __forceinline__ void gen_scatter(const GenParams& q, const ChunkDesc&
   const int valid_u = d.cplx ? width : 2 * width;
   const int total = d.M1 * rw;
   const int lane = threadIdx.x & 31;
-  for (int base = threadIdx.x - lane; base < total; base += T) {
-    const int e = base + lane;
-    int p = -1;
-    float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-    if (e < total) {
-      const int j1 = e >> lrw, u = e & (rw - 1);
-      if (u < valid_u) {
-        const int64_t s = d.off + (d.cplx ? (int64_t)j1 * d.M2 + j2_0 + u
-                                          : 2 * ((int64_t)j1 * d.M2 + j2_0) + u);
-        p = __ldg(pix + s);
-        const float t = gain * (d.cplx ? smf[2 * e] : smf[e]);
-        v0 = t;
-        if constexpr (NC == 3) {
-          float cw, sw;
-          if (q.half_w) {
-            cw = __half2float(static_cast<const __half*>(cosw)[s]);
-            sw = __half2float(static_cast<const __half*>(sinw)[s]);
-          } else {
-            cw = __ldg(static_cast<const float*>(cosw) + s);
-            sw = __ldg(static_cast<const float*>(sinw) + s);
+  // two rounds of 32 samples per warp: both rounds' pointing loads are issued before the
+  // first scan
+  constexpr int U = 2;
+  for (int base0 = threadIdx.x - lane; base0 < total; base0 += U * T) {
+    int pv[U];
+    float tv[U], cv[U], sv[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int e = base0 + k * T + lane;
+      pv[k] = -1;
+      tv[k] = cv[k] = sv[k] = 0.f;
+      if (e < total) {
+        const int j1 = e >> lrw, u = e & (rw - 1);
+        if (u < valid_u) {
+          const int64_t s = d.off + (d.cplx ? (int64_t)j1 * d.M2 + j2_0 + u
+                                            : 2 * ((int64_t)j1 * d.M2 + j2_0) + u);
+          pv[k] = __ldg(pix + s);
+          tv[k] = gain * (d.cplx ? smf[2 * e] : smf[e]);
+          if constexpr (NC == 3) {
+            if (q.half_w) {
+              cv[k] = __half2float(static_cast<const __half*>(cosw)[s]);
+              sv[k] = __half2float(static_cast<const __half*>(sinw)[s]);
+            } else {
+              cv[k] = __ldg(static_cast<const float*>(cosw) + s);
+              sv[k] = __ldg(static_cast<const float*>(sinw) + s);
+            }
           }
-          v1 = t * cw;
-          v2 = t * sw;
         }
       }
     }
-    const int pp = __shfl_up_sync(0xffffffffu, p, 1);
-    const bool head = lane == 0 || p != pp;
-    const unsigned hm = __ballot_sync(0xffffffffu, head);
-    const int seg = __popc(hm & (0xffffffffu >> (31 - lane)));
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const float a0 = __shfl_down_sync(0xffffffffu, v0, o);
-      const float a1 = __shfl_down_sync(0xffffffffu, v1, o);
-      const float a2 = __shfl_down_sync(0xffffffffu, v2, o);
-      const int so = __shfl_down_sync(0xffffffffu, seg, o);
-      if (lane + o < 32 && so == seg) { v0 += a0; v1 += a1; v2 += a2; }
+    for (int k = 0; k < U; ++k) {
+      if (base0 + k * T >= total) break;   // warp-uniform
+      const int p = pv[k];
+      float v0 = tv[k], v1 = 0.f, v2 = 0.f;
+      if constexpr (NC == 3) {
+        v1 = tv[k] * cv[k];
+        v2 = tv[k] * sv[k];
+      }
+      const int pp = __shfl_up_sync(0xffffffffu, p, 1);
+      const bool head = lane == 0 || p != pp;
+      const unsigned hm = __ballot_sync(0xffffffffu, head);
+      const int seg = __popc(hm & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float a0 = __shfl_down_sync(0xffffffffu, v0, o);
+        const float a1 = __shfl_down_sync(0xffffffffu, v1, o);
+        const float a2 = __shfl_down_sync(0xffffffffu, v2, o);
+        const int so = __shfl_down_sync(0xffffffffu, seg, o);
+        if (lane + o < 32 && so == seg) { v0 += a0; v1 += a1; v2 += a2; }
+      }
+      if (head) emit_run<NC>(q.acc, q.acc_stride, p, v0, v1, v2);
     }
-    if (head) emit_run<NC>(q.acc, q.acc_stride, p, v0, v1, v2);
   }
 }
 
