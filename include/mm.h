@@ -103,6 +103,18 @@ mm_status mm_lambda_max(mm_plan p, double* out, void* stream);
 mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int precision,
                                double* map_inout, double* chi2_out, void* stream);
 
+/* Fault flags of the plan's kernels since the last call, then cleared: bit 0 = a bounded
+ * wait of the fused iteration kernel (one launch for the column, row and inverse column
+ * passes of a batch, whose work items wait for their chunk's earlier passes) ran out after
+ * about a second; the results of that iteration are then wrong.  Synchronises `stream`.
+ * No counterpart in the paper: a check of this library's own scheduling. */
+mm_status mm_plan_fault_flags(mm_plan p, int* flags, void* stream);
+
+/* How many of the plan's batches mm_messenger_iterate and mm_messenger_graph run as one
+ * fused launch (column, row and inverse column passes together; chunks of 2^22 samples,
+ * single pointing); the others run the three kernels one after the other. */
+mm_status mm_plan_fused_batches(mm_plan p, int* n_fused);
+
 /* Chunks run in batches that share one four-step FFT intermediate buffer of at most 1 GB by
  * default (environment variable MM_YBUF_MB, read when the plan is made; a budget of about a
  * quarter of L2 keeps each batch's intermediate resident in L2 between passes).
@@ -111,8 +123,10 @@ mm_status mm_plan_batches(mm_plan p, int* n_batches);
 
 /* One stage of a messenger iteration, for callers that interleave their own work (or
  * CUDA events) between the kernels of an iteration.  mm_messenger_iterate runs one LOAD,
- * then per iteration: for each batch b, GATHER_FFT(b), FILTER(b), IFFT_BIN(b); then MAP.
- * The same sequence through this entry point gives identical results.
+ * then per iteration: for each batch b, FUSED(b) where the batch is fused
+ * (mm_plan_fused_batches), else GATHER_FFT(b), FILTER(b), IFFT_BIN(b); then MAP.  The same
+ * sequence through this entry point gives identical results, and the three separate stages
+ * on a fused batch the same up to the order of the FP64 pixel additions.
  *   MM_STAGE_LOAD:       map_inout (device float64 [n_pix][ncomp]) -> internal FP32 map;
  *   MM_STAGE_GATHER_FFT: P m gathered from the internal map, packed, column DFTs (Eq. 1);
  *   MM_STAGE_FILTER:     row DFTs, per-mode messenger filter at `lambda` (>= 1 or INFINITY),
@@ -120,12 +134,14 @@ mm_status mm_plan_batches(mm_plan p, int* n_batches);
  *                        zeroes it), inverse row DFTs (Sec. 2.1, Sec. 3.1);
  *   MM_STAGE_IFFT_BIN:   inverse column DFTs and P^T T^-1 t into FP64 accumulators;
  *   MM_STAGE_MAP:        m = (P^T T^-1 P)^-1 acc per pixel; written to map_inout if non-NULL,
- *                        and to the internal map for the next GATHER_FFT.
- * `batch` selects the batch of the three per-batch stages and is ignored otherwise; a
+ *                        and to the internal map for the next GATHER_FFT;
+ *   MM_STAGE_FUSED:      GATHER_FFT, FILTER and IFFT_BIN of the batch in one launch
+ *                        (MM_ERR_UNSUPPORTED for a batch that is not fused).
+ * `batch` selects the batch of the per-batch stages and is ignored otherwise; a
  * batch's GATHER_FFT, FILTER and IFFT_BIN must run in that order before the next batch's
  * GATHER_FFT (they share one intermediate buffer).  Unused pointers may be NULL. */
 enum { MM_STAGE_LOAD = 0, MM_STAGE_GATHER_FFT = 1, MM_STAGE_FILTER = 2, MM_STAGE_IFFT_BIN = 3,
-       MM_STAGE_MAP = 4 };
+       MM_STAGE_MAP = 4, MM_STAGE_FUSED = 5 };
 mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double lambda,
                              double* map_inout, double* chi2_slot, void* stream);
 

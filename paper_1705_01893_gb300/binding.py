@@ -20,7 +20,7 @@ MM_OK, MM_ERR_ARG, MM_ERR_CUDA, MM_ERR_NOMEM, MM_ERR_TIMEOUT, MM_ERR_STATE, MM_E
     MM_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 MM_W_F32, MM_W_F16 = 0, 1
 MM_FP32_MIXED = 0
-MM_STAGE_LOAD, MM_STAGE_GATHER_FFT, MM_STAGE_FILTER, MM_STAGE_IFFT_BIN, MM_STAGE_MAP = range(5)
+MM_STAGE_LOAD, MM_STAGE_GATHER_FFT, MM_STAGE_FILTER, MM_STAGE_IFFT_BIN, MM_STAGE_MAP, MM_STAGE_FUSED = range(6)
 
 _vp = ctypes.c_void_p
 _i64p = ctypes.POINTER(ctypes.c_int64)
@@ -52,6 +52,8 @@ SIGNATURES = {
                                                  _vp]),
     "mm_messenger_adjoint_ckpt": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp,
                                                  ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "mm_plan_fault_flags": (ctypes.c_int, [_vp, _ip, _vp]),
+    "mm_plan_fused_batches": (ctypes.c_int, [_vp, _ip]),
     "mm_pcg_state_bytes": (ctypes.c_int, [_vp, _szp]),
     "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
     "mm_chi2": (ctypes.c_int, [_vp, _vp, ctypes.c_double, _vp, _vp]),
@@ -241,6 +243,18 @@ class Plan:
         _check("mm_messenger_plain_fp64", load().mm_messenger_plain_fp64(
             self._h, _ptr(tod), lam.ctypes.data_as(_dp), len(lam), _ptr(map_inout),
             _ptr(chi2_out), wp, int(n.value), _stream(stream)))
+
+    def fault_flags(self, stream=None) -> int:
+        """Fault flags of the plan's kernels since the last call (then cleared); 0 = none."""
+        f = ctypes.c_int()
+        _check("mm_plan_fault_flags", load().mm_plan_fault_flags(self._h, ctypes.byref(f),
+                                                                 _stream(stream)))
+        return f.value
+
+    def n_fused_batches(self) -> int:
+        n = ctypes.c_int()
+        _check("mm_plan_fused_batches", load().mm_plan_fused_batches(self._h, ctypes.byref(n)))
+        return n.value
 
     def n_batches(self) -> int:
         n = ctypes.c_int()

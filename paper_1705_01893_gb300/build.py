@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmm.so")
-SOURCES = ["mm_api.cu", "mm_col.cu", "mm_row.cu", "mm_adjoint.cu", "mm_plain.cu", "mm_noalloc.cu", "mm_gen.cu"]
+SOURCES = ["mm_api.cu", "mm_col.cu", "mm_row.cu", "mm_adjoint.cu", "mm_plain.cu", "mm_noalloc.cu", "mm_gen.cu", "mm_fused.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "--use_fast_math=false"]
 

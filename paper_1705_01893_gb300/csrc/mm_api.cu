@@ -172,7 +172,7 @@ static size_t tw_count(int M, int M1, int M2, bool general) {
 struct Layout {
   size_t desc, chunks, params, tw, hits, valid, W, Minv, acc, acc12, map4, bvec, dtab, nbar, nyq, c0,
       ybuf, scal, tpix, tcos, tsin, lam, iter, map64, groups, gen, gen_rec, gen_ctab, gen_rtab,
-      adapt, queue, total, ybytes;
+      adapt, queue, fitems, fctr, fault, total, ybytes;
   int64_t gen_ccap, gen_rcap;
   int lam_cap;
   int n_groups;
@@ -322,6 +322,13 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->gen_rtab = take(sizeof(int4) * rjobs);
   L->adapt = take(sizeof(AdaptState));
   L->queue = take(64);
+  // fused iteration kernel: item lists of the batches it covers, counters, fault flag
+  size_t fitems = 0;
+  for (int g = 0; g < L->n_groups; ++g)
+    fitems += (size_t)L->gcount[g] * fused_items_per_chunk(L->gM1[g], L->gM2[g], L->ggen[g]);
+  L->fitems = take(sizeof(int2) * (fitems > 0 ? fitems : 1));
+  L->fctr = take(sizeof(unsigned) * (2 + 2 * (size_t)n_chunks));
+  L->fault = take(16);
   L->total = o;
   return MM_OK;
 }
@@ -1046,6 +1053,11 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
   p->adapt_exec = nullptr;
   p->adapt_st = ws + L.adapt;
   p->row_queue = reinterpret_cast<unsigned*>(ws + L.queue);
+  p->fused_items = reinterpret_cast<int2*>(ws + L.fitems);
+  p->fused_ctr = reinterpret_cast<unsigned*>(ws + L.fctr);
+  p->fault = reinterpret_cast<int*>(ws + L.fault);
+  p->h_fused_first = nullptr;
+  p->h_fused_n = nullptr;
   p->scal = reinterpret_cast<double*>(ws + L.scal);
   p->params = reinterpret_cast<double*>(ws + L.params);
   p->tpix = reinterpret_cast<int32_t*>(ws + L.tpix);
@@ -1134,6 +1146,24 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
     }
     for (const Batch& b : L.gen_batches) p->h_batches[p->n_batches++] = b;
   }
+  // item lists of the batches the fused iteration kernel covers
+  std::vector<int2> fitems;
+  {
+    p->h_fused_first = new (std::nothrow) int[p->n_batches > 0 ? p->n_batches : 1];
+    p->h_fused_n = new (std::nothrow) int[p->n_batches > 0 ? p->n_batches : 1];
+    if (!p->h_fused_first || !p->h_fused_n) { mm_plan_destroy(p); mm_set_error("host allocation failed"); return MM_ERR_NOMEM; }
+    for (int b = 0; b < p->n_batches; ++b) {
+      const Batch& B = p->h_batches[b];
+      p->h_fused_first[b] = (int)fitems.size();
+      p->h_fused_n[b] = 0;
+      if (B.group < 0 || p->composite) continue;
+      const Group& G = p->groups[B.group];
+      const int per = fused_items_per_chunk(G.M1, G.M2, G.general);
+      if (per == 0) continue;
+      fitems.resize(fitems.size() + (size_t)per * B.count);
+      p->h_fused_n[b] = fused_build_items(G.M1, G.M2, B.count, fitems.data() + p->h_fused_first[b]);
+    }
+  }
   // general list and its prefix sums (column tiles of the tuned width, row jobs, offsets)
   if (p->n_gen > 0) {
     const int ng = p->n_gen;
@@ -1181,6 +1211,13 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
   if ((e = cudaMemsetAsync(p->scal, 0, sizeof(double) * kScalCount, s)) != cudaSuccess) return fail("memset", e);
   if ((e = cudaMemsetAsync(p->acc, 0, sizeof(double) * ncomp * n_pix, s)) != cudaSuccess) return fail("memset", e);
   if ((e = cudaMemsetAsync(p->row_queue, 0, 64, s)) != cudaSuccess) return fail("memset", e);
+  if ((e = cudaMemsetAsync(p->fused_ctr, 0, sizeof(unsigned) * (2 + 2 * (size_t)n_chunks), s)) != cudaSuccess)
+    return fail("memset", e);
+  if ((e = cudaMemsetAsync(p->fault, 0, 16, s)) != cudaSuccess) return fail("memset", e);
+  if (!fitems.empty() &&
+      (e = cudaMemcpyAsync(p->fused_items, fitems.data(), sizeof(int2) * fitems.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return fail("fused item lists", e);
   if (L.n_total > 0)
     k_hits<<<blocks_for(L.n_total, 256), 256, 0, s>>>(pix, L.n_total, n_pix, p->hits, p->scal + kScalTmp);
   if (L.n_total > 0 && p->composite)
@@ -1207,6 +1244,8 @@ extern "C" void mm_plan_destroy(mm_plan p) {
   delete[] p->h_desc;
   delete[] p->h_chunk_group;
   delete[] p->h_batches;
+  delete[] p->h_fused_first;
+  delete[] p->h_fused_n;
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   if (p->adapt_exec) cudaGraphExecDestroy(p->adapt_exec);
   if (p->graph_stream) cudaStreamDestroy(p->graph_stream);
@@ -1403,8 +1442,9 @@ extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int 
   }
   for (int it = 0; it < n_iter; ++it) {
     RowArgs a{kRowMessenger, lambdas[it], chi2_out ? chi2_out + it : nullptr, nullptr};
-    FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
-                L_(launch_col_inverse(p, B, s)));
+    FOR_BATCHES(if (fused_eligible(p, B)) { L_(launch_fused(p, B, a, s)); } else {
+                  L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
+                  L_(launch_col_inverse(p, B, s)); });
     double* mo = it == n_iter - 1 ? map_inout : nullptr;
     if (p->ncomp == 3) k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, mo);
     else k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, mo);
@@ -1554,6 +1594,25 @@ extern "C" mm_status mm_messenger_iterate_md(mm_plan p, const double* lambdas, i
   return MM_OK;
 }
 
+extern "C" mm_status mm_plan_fault_flags(mm_plan p, int* flags, void* stream) {
+  MM_ARG(p != nullptr && flags != nullptr, "NULL argument");
+  cudaStream_t s = S(stream);
+  int f = 0;
+  MM_CUDA(cudaMemcpyAsync(&f, p->fault, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  MM_CUDA(cudaMemsetAsync(p->fault, 0, sizeof(int), s));
+  *flags = f;
+  return MM_OK;
+}
+
+extern "C" mm_status mm_plan_fused_batches(mm_plan p, int* n_fused) {
+  MM_ARG(p != nullptr && n_fused != nullptr, "NULL argument");
+  int n = 0;
+  for (int b = 0; b < p->n_batches; ++b) n += fused_eligible(p, p->h_batches[b]) ? 1 : 0;
+  *n_fused = n;
+  return MM_OK;
+}
+
 extern "C" mm_status mm_plan_batches(mm_plan p, int* n_batches) {
   MM_ARG(p != nullptr && n_batches != nullptr, "NULL argument");
   *n_batches = p->n_batches;
@@ -1570,7 +1629,7 @@ extern "C" mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double 
   if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
   cudaStream_t s = S(stream);
   const bool per_batch = stage == MM_STAGE_GATHER_FFT || stage == MM_STAGE_FILTER ||
-                         stage == MM_STAGE_IFFT_BIN;
+                         stage == MM_STAGE_IFFT_BIN || stage == MM_STAGE_FUSED;
   if (per_batch) MM_ARG(batch >= 0 && batch < p->n_batches, "batch %d out of range", batch);
   cudaError_t e = cudaSuccess;
   switch (stage) {
@@ -1589,6 +1648,16 @@ extern "C" mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double 
     case MM_STAGE_IFFT_BIN:
       e = launch_col_inverse(p, p->h_batches[batch], s);
       break;
+    case MM_STAGE_FUSED: {
+      MM_ARG(lambda >= 1.0 || isinf(lambda), "lambda = %g must be >= 1 or inf", lambda);
+      if (!fused_eligible(p, p->h_batches[batch])) {
+        mm_set_error("batch %d does not run as one fused launch", batch);
+        return MM_ERR_UNSUPPORTED;
+      }
+      RowArgs a{kRowMessenger, lambda, chi2_slot, nullptr};
+      e = launch_fused(p, p->h_batches[batch], a, s);
+      break;
+    }
     case MM_STAGE_MAP:
       if (p->ncomp == 3) k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, map_inout);
       else k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, map_inout);
@@ -1617,6 +1686,10 @@ static cudaError_t launch_iteration(mm_plan p, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < p->n_batches && e == cudaSuccess; ++b) {
     const Batch& B = p->h_batches[b];
+    if (fused_eligible(p, B)) {
+      e = launch_fused(p, B, a, s);
+      continue;
+    }
     if ((e = launch_col_forward(p, B, kSrcGather, nullptr, s)) != cudaSuccess) break;
     if ((e = launch_row(p, B, a, s)) != cudaSuccess) break;
     e = launch_col_inverse(p, B, s);

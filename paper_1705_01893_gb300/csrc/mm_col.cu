@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse(ColParams
                                            SrcY{q.ybuf + (int64_t)ci * d.M, cb * CB, M2});
     // tile-ordered pointing: the tile's samples are contiguous, in the same order as t
     const int64_t tbase = d.off + (int64_t)cb * NS;
-#pragma unroll 2
+#pragma unroll 4
     for (int e4 = threadIdx.x; e4 < NS / 4; e4 += T) {
       const int e = 4 * e4;
       scatter4<NC>(q, tbase + e, *reinterpret_cast<const float4*>(smf + e), e4 & 7);
@@ -119,6 +119,10 @@ static ColParams make_params(const mm_plan_s* p, const Batch& b, const float* to
   q.acc = p->acc;
   q.acc_stride = p->n_pix;
   return q;
+}
+
+ColParams make_col_params(const mm_plan_s* p, const Batch& b) {
+  return make_params(p, b, nullptr);
 }
 
 template <int M1>

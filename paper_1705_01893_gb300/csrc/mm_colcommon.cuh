@@ -25,6 +25,9 @@ struct ColParams {
   int64_t acc_stride;  // n_pix
 };
 
+// The column kernels' parameters for batch b (plan-owned tile-order pointing, map, buffers).
+ColParams make_col_params(const mm_plan_s* p, const Batch& b);
+
 // Four consecutive samples (s a multiple of 4): one 16-byte load per stream.
 __device__ __forceinline__ float4 load_w4(const void* w, int half_w, int64_t s) {
   if (half_w) {
@@ -200,7 +203,8 @@ struct SrcY {        // filtered spectrum rows for the inverse column DFTs
   int j2_0;
   int M2;
   __device__ __forceinline__ float2 operator()(int b, int k1) const {
-    return y[(int64_t)k1 * M2 + j2_0 + b];
+    // L2 only: in the fused iteration kernel other CTAs wrote these rows in this launch
+    return __ldcg(y + (int64_t)k1 * M2 + j2_0 + b);
   }
 };
 

@@ -1,0 +1,203 @@
+// One launch for the three streaming passes of a messenger iteration over a batch of
+// equal-length chunks (the column pass A, the row pass B with the Fourier-diagonal update of
+// Sec. 2.1, and the inverse column pass C with the binning of P^T T^-1 t).
+//
+// The batch's work is a list of items -- A tiles, B row-pair jobs, C tiles -- in chunk
+// order with a lag: step s holds the A tiles of chunk s, the B jobs of chunk s - 2 and the
+// C tiles of chunk s - 5, interleaved.  CTAs take items from a queue counter; a B job of
+// chunk c waits until all A tiles of c are done, a C tile until all B jobs of c are done
+// (per-chunk counters).  The tails of three separate kernels (each ends on a partly filled
+// wave of 20-30 us items) and the gaps between their launches disappear.  Every item, including a CTA's first, comes from the queue, so a CTA
+// only ever waits for items that CTAs already running hold: no deadlock whatever number of
+// CTAs is resident.  Waits are bounded (about a second): on expiry the kernel sets the plan's
+// fault flag and carries on (the result is then wrong, and mm_plan_fault_flags reports it).
+#include "mm_colcommon.cuh"
+#include "mm_rowcommon.cuh"
+
+namespace mm {
+
+struct FusedParams {
+  ColParams c;            // A and C
+  RowParams r;            // B
+  const int2* items;      // x = kind << 16 | chunk of the batch, y = tile / job of the chunk
+  int n_items;
+  unsigned* ctr;          // [0] queue, [1] CTAs done, [2, 2 + count) A tiles done per chunk,
+                          // [2 + count, 2 + 2 count) B jobs done per chunk; zero between launches
+  int* fault;
+};
+
+enum { kItemA = 0, kItemB = 1, kItemC = 2 };
+
+// Poll *c (acquire, GPU scope) until it reaches target; about a second at most.
+__device__ __forceinline__ void wait_count(const unsigned* c, unsigned target, int* fault) {
+  for (int n = 0; n < (1 << 22); ++n) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    if (v >= target) return;
+    __nanosleep(256);
+  }
+  atomicExch(fault, 1);
+}
+
+template <int M1, int M2, int CB, int T, int NC>
+__global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
+  extern __shared__ float2 sm[];
+  __shared__ float red[32];
+  __shared__ int2 s_it;
+  // chunks this CTA has already seen complete (A tiles, B jobs): no second acquire poll
+  constexpr int kMaskWords = 64;
+  __shared__ unsigned s_mask[2][kMaskWords];
+  static_assert(M1 * CB <= 2 * M2, "column tiles share the row jobs' buffer");
+  // The row twiddles stay in global memory (L1 / L2): staging them in shared memory, as the
+  // row kernel does, would take the shared-memory reservation of every item from 64 to
+  // 100 KB, and the column items lose the L1 their map gathers hit (measured: a separate
+  // column pass slows from 140 to 202 us with the larger reservation).
+  const float2* tws = q.r.g.tw_row;
+  for (int i = threadIdx.x; i < 2 * kMaskWords; i += T) s_mask[i / kMaskWords][i % kMaskWords] = 0u;
+  const int count = q.c.count;
+  constexpr unsigned nA = M2 / CB, nB = M1 / 2 + 1;
+  unsigned* doneA = q.ctr + 2;
+  unsigned* doneB = q.ctr + 2 + count;
+  if (threadIdx.x == 0) {
+    const int w = (int)atomicAdd(q.ctr, 1u);
+    s_it = w < q.n_items ? __ldg(q.items + w) : make_int2(-1, 0);
+  }
+  __syncthreads();
+  while (true) {
+    const int2 it = s_it;
+    if (it.x < 0) break;
+    const int kind = it.x >> 16, ci = it.x & 0xffff, idx = it.y;
+    int2 nxt = make_int2(-1, 0);
+    if (threadIdx.x == 0) {
+      // the next item is taken now; its index and entry arrive while this one runs
+      const int w = (int)atomicAdd(q.ctr, 1u);
+      if (w < q.n_items) nxt = __ldg(q.items + w);
+      if (kind != kItemA) {
+        const int m = kind == kItemB ? 0 : 1;
+        const bool cached = ci < 32 * kMaskWords && ((s_mask[m][ci >> 5] >> (ci & 31)) & 1u);
+        if (!cached) {
+          wait_count((m == 0 ? doneA : doneB) + ci, m == 0 ? nA : nB, q.fault);
+          if (ci < 32 * kMaskWords) s_mask[m][ci >> 5] |= 1u << (ci & 31);
+        }
+      }
+    }
+    __syncthreads();
+    const ChunkDesc d = q.c.desc[q.c.chunks[ci]];
+    if (kind == kItemA) {
+      const DstY dst{q.c.ybuf + (int64_t)ci * d.M, &q.c.g, idx * CB, M2};
+      smem_fft<M1, CB, ColLayout<CB>, T, -1>(
+          sm, q.c.g.tw_col, SrcGather<NC, CB>{&q.c, d.off + (int64_t)idx * (2 * CB * M1)}, dst);
+    } else if (kind == kItemB) {
+      if (threadIdx.x == 0) {
+        // this job's d~ and Nbar rows into L2 while the forward row DFTs run
+        const int rb = (M1 - idx) & (M1 - 1);
+        prefetch_l2(q.r.dtab + d.spec + (int64_t)idx * M2, 8 * M2);
+        prefetch_l2(q.r.nbar + d.spec + (int64_t)idx * M2, 4 * M2);
+        if (rb != idx) {
+          prefetch_l2(q.r.dtab + d.spec + (int64_t)rb * M2, 8 * M2);
+          prefetch_l2(q.r.nbar + d.spec + (int64_t)rb * M2, 4 * M2);
+        }
+      }
+      kernel_body_job<M2, T, kRowMessenger>(q.r, sm, tws, red, ci, idx);
+    } else {
+      constexpr int NS = M1 * 2 * CB;
+      const float* smf = reinterpret_cast<const float*>(sm);
+      smem_fft<M1, CB, ColLayout<CB>, T, +1>(sm, q.c.g.tw_col,
+                                             SrcY{q.c.ybuf + (int64_t)ci * d.M, idx * CB, M2});
+      const int64_t tbase = d.off + (int64_t)idx * NS;
+#pragma unroll 2
+      for (int e4 = threadIdx.x; e4 < NS / 4; e4 += T) {
+        const int e = 4 * e4;
+        scatter4<NC>(q.c, tbase + e, *reinterpret_cast<const float4*>(smf + e), e4 & 7);
+      }
+    }
+    // release the intermediate rows written by an A tile or a B job before its count
+    if (kind != kItemC) __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (kind == kItemA) atomicAdd(doneA + ci, 1u);
+      if (kind == kItemB) atomicAdd(doneB + ci, 1u);
+      s_it = nxt;
+    }
+    __syncthreads();
+  }
+  // the last CTA out clears the counters for the next launch
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(q.ctr + 1, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    for (int i = threadIdx.x; i < 2 + 2 * count; i += T) q.ctr[i] = 0u;
+    __threadfence();
+  }
+}
+
+// The fused path covers the shape instantiated here: chunks of 2^22 samples (M = 2^21 =
+// 512 x 4096), the column and row passes both at 512 threads.
+static bool fused_shape(int M1, int M2, bool general) {
+  return !general && M1 == 512 && M2 == 4096;
+}
+
+bool fused_eligible(const mm_plan_s* p, const Batch& b) {
+  if (b.group < 0 || p->composite || p->h_fused_n == nullptr) return false;
+  const Group& g = p->groups[b.group];
+  return fused_shape(g.M1, g.M2, g.general) && p->h_fused_n[&b - p->h_batches] > 0;
+}
+
+int fused_items_per_chunk(int M1, int M2, bool general) {
+  return fused_shape(M1, M2, general) ? 2 * (M2 / kColCB) + M1 / 2 + 1 : 0;
+}
+
+// Item list of a batch of `count` chunks: step s has the A tiles of chunk s, the B jobs of
+// chunk s - kLagAB and the C tiles of chunk s - kLagAB - kLagBC, taken round-robin.  Every
+// item's prerequisites (all A tiles of its chunk for a B job, all B jobs for a C tile) come
+// earlier in the list.  Measured on 8 x 2^22 samples (us per launch): lags 1/1 546, 1/2 490,
+// 2/1 518, 2/2 449, 2/3 447, 3/3 447, 4/4 447, 8/8 (all A, then all B, then all C) 449:
+// short lags leave items waiting; beyond that the order hardly matters, and the gain over
+// three launches (A + B + C = 465 us) is their tails and the gaps between them.
+int fused_build_items(int M1, int M2, int count, int2* out) {
+  constexpr int kLagAB = 2, kLagBC = 3;
+  const int nA = M2 / kColCB, nB = M1 / 2 + 1, nC = nA;
+  int n = 0;
+  for (int s = 0; s < count + kLagAB + kLagBC; ++s) {
+    const int ca = s, cb = s - kLagAB, cc = s - kLagAB - kLagBC;
+    const bool ha = ca < count, hb = cb >= 0 && cb < count, hc = cc >= 0 && cc < count;
+    const int m = (ha ? nA : 0) > (hb ? nB : 0) ? (ha ? nA : 0) : (hb ? nB : 0);
+    const int mm = m > (hc ? nC : 0) ? m : (hc ? nC : 0);
+    for (int i = 0; i < mm; ++i) {
+      if (ha && i < nA) out[n++] = make_int2(kItemA << 16 | ca, i);
+      if (hb && i < nB) out[n++] = make_int2(kItemB << 16 | cb, i);
+      if (hc && i < nC) out[n++] = make_int2(kItemC << 16 | cc, i);
+    }
+  }
+  return n;
+}
+
+cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
+  const int bi = (int)(&b - p->h_batches);
+  const Group& g = p->groups[b.group];
+  FusedParams q;
+  q.c = make_col_params(p, b);
+  q.r = make_row_params(p, b, a);
+  q.items = p->fused_items + p->h_fused_first[bi];
+  q.n_items = p->h_fused_n[bi];
+  q.ctr = p->fused_ctr;
+  q.fault = p->fault;
+  const size_t smem = sizeof(float2) * 2 * g.M2;
+  int grid = 0;
+  cudaError_t e;
+  if (p->ncomp == 3) {
+    auto k = k_fused<512, 4096, kColCB, 512, 3>;
+    if ((e = persistent_grid(k, 512, smem, q.n_items, &grid)) != cudaSuccess) return e;
+    k<<<grid, 512, smem, st>>>(q);
+  } else {
+    auto k = k_fused<512, 4096, kColCB, 512, 1>;
+    if ((e = persistent_grid(k, 512, smem, q.n_items, &grid)) != cudaSuccess) return e;
+    k<<<grid, 512, smem, st>>>(q);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mm

@@ -165,6 +165,12 @@ struct mm_plan_s {
   void* adapt_st;      // device mm::AdaptState followed by the level table
   unsigned* row_queue; // device [2]: the row kernel's job counter and finished-CTA count
                        // (zero between launches: the last CTA of each launch resets both)
+  // fused iteration kernel (mm_fused.cu): per-batch item lists, counters, fault flag
+  int2* fused_items;   // device, all eligible batches' lists back to back
+  int* h_fused_first;  // host [n_batches]: offset of the batch's list (items)
+  int* h_fused_n;      // host [n_batches]: items of the batch's list, 0 = not fused
+  unsigned* fused_ctr; // device [2 + 2 n_chunks], zero between launches
+  int* fault;          // device flag: a bounded wait of a kernel expired
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;
@@ -533,6 +539,11 @@ enum ColSrc { kSrcGather = 0, kSrcTod = 1 };
 cudaError_t launch_col_forward(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                cudaStream_t st);
 cudaError_t launch_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
+// Fused A + B + C launch of one batch's messenger iteration (mm_fused.cu).
+bool fused_eligible(const mm_plan_s* p, const Batch& b);
+int fused_items_per_chunk(int M1, int M2, bool general);
+int fused_build_items(int M1, int M2, int count, int2* out);
+cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
 cudaError_t launch_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st);
 cudaError_t launch_tile_pointing(const mm_plan_s* p, cudaStream_t st);
 // General path (mm_gen.cu): the same three stages for a batch of general-length chunks,

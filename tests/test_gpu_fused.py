@@ -1,0 +1,105 @@
+"""The fused iteration kernel (one launch for the column, row and inverse column passes of a
+batch of 2^22-sample chunks, its work items ordered by chunk and waiting on per-chunk
+counters) against the three separate kernels of the stage API and against the FP64 oracle.
+
+Tolerances: the fused and the separate kernels do the same FP32 arithmetic per tile and row
+job; only the order of the FP64 pixel additions differs, so their maps agree to 1e-9
+(a rare FP32 rounding of the gather copy may differ after that).  Against the oracle the
+FP32 path keeps the 1e-5 map tolerance of the other one-step tests."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle.messenger as O
+from paper_1705_01893_gb300 import binding, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+N22 = 1 << 22
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1705_01893_gb300 import build
+    build.build()
+    binding.load()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def stage_iterate(plan, m, lams):
+    plan.stage(binding.MM_STAGE_LOAD, map_inout=m)
+    for i, lam in enumerate(lams):
+        for b in range(plan.n_batches()):
+            plan.stage(binding.MM_STAGE_GATHER_FFT, b)
+            plan.stage(binding.MM_STAGE_FILTER, b, lam)
+            plan.stage(binding.MM_STAGE_IFFT_BIN, b)
+        plan.stage(binding.MM_STAGE_MAP, map_inout=m if i == len(lams) - 1 else None)
+
+
+@pytest.mark.parametrize("n_det", [1, 3, 5])
+def test_fused_matches_separate_kernels(n_det):
+    """1, 3 and 5 chunks: fewer chunks than the lag between the passes, and more."""
+    s = synth.config_iqu(64, n_det, N22, 40 + n_det)
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_batches() == 1 and plan.n_fused_batches() == 1
+    lams = [math.inf, 300.0, 30.0, 3.0, 1.0]
+    m_f = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    chi_f = torch.zeros(len(lams), dtype=torch.float64, device=DEV)
+    plan.messenger(m_f, lams, chi2_out=chi_f)
+    m_s = torch.zeros_like(m_f)
+    stage_iterate(plan, m_s, lams)
+    torch.cuda.synchronize()
+    assert plan.fault_flags() == 0
+    assert rel(m_f.cpu().numpy(), m_s.cpu().numpy()) <= 1e-9
+    # chi^2 of each iteration's input map from the fused row jobs, against mm_chi2 of the
+    # separate path's iterates
+    m_c = torch.zeros_like(m_f)
+    for i, lam in enumerate(lams):
+        if i > 0:
+            ref = plan.chi2(m_c).item()
+            assert abs(chi_f[i].item() - ref) <= 1e-7 * ref, (i, chi_f[i].item(), ref)
+        stage_iterate(plan, m_c, [lam])
+
+
+def test_fused_graph_and_repeated_launches():
+    """The graph-replayed iteration (counters reset by each launch's last CTA) gives the
+    iterate of the host-launched one, twice in a row."""
+    s = synth.config_iqu(64, 2, N22, 46)
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_fused_batches() == 1
+    lams = np.array([math.inf] + [100.0] * 4 + [10.0] * 4 + [1.0] * 4)
+    m1 = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    plan.messenger(m1, lams)
+    for _ in range(2):
+        m2 = torch.zeros_like(m1)
+        plan.messenger_graph(m2, lams)
+        torch.cuda.synchronize()
+        assert rel(m2.cpu().numpy(), m1.cpu().numpy()) <= 1e-9
+    assert plan.fault_flags() == 0
+
+
+def test_fused_one_step_against_oracle():
+    """Two chunks of 2^22 samples, 32x32 IQU: the binned start and one cooled step."""
+    s = synth.config_iqu(32, 2, N22, 47)
+    prob = O.problem_from_synth(s)
+    lams = [math.inf, O.lambda_max(prob)]
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_fused_batches() == 1
+    m = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    plan.messenger(m, lams)
+    torch.cuda.synchronize()
+    assert plan.fault_flags() == 0
+    m_ref, _ = O.run_messenger(prob, lams)
+    assert rel(m.cpu().numpy(), m_ref) <= 1e-5
+
+
+def test_fused_not_used_for_other_shapes():
+    """Chunks of other lengths keep the three separate kernels."""
+    s = synth.config_iqu(32, 2, 1 << 18, 48)
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_fused_batches() == 0
