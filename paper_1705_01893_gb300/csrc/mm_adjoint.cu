@@ -9,12 +9,11 @@
 //   dL/dm   = sum_c P_c^T irfft(b v~) / tau_c,
 //   dL/dtheta_c += <v/tau, dt/dtheta> + <v, P m' - t> dtau/dtheta / tau^2,
 // the last term from W's dependence on tau.  The transposed step reuses the forward
-// gather + column-DFT kernel for v and for P m (the forward spectrum needed by dt/dtheta),
-// a row kernel that transforms both and forms the filtered adjoint spectrum and the
-// theta sums, and an inverse column kernel that bins P^T t and accumulates dL/dd.  Forward
-// iterates are recomputed from checkpoints taken every `ckpt_every` iterations.  Without a
-// theta gradient the forward spectrum is not needed: the step then gathers and transforms
-// v alone (two rows per row job instead of four).
+// gather + column-DFT kernel for v, a row kernel that transforms it and forms the filtered
+// adjoint spectrum (and the theta sums), and an inverse column kernel that bins P^T t and
+// accumulates dL/dd.  Forward iterates are recomputed from checkpoints taken every
+// `ckpt_every` iterations; the recomputation keeps each iteration's forward spectrum
+// (P m_i)~, which the theta sums read (without a theta gradient nothing is recomputed).
 #include <math.h>
 
 #include "mm_colcommon.cuh"
@@ -31,7 +30,7 @@ struct AdjRowParams {
   int count;
   Group g;
   float2* yV;                 // adjoint intermediate (in: column pass of v; out: of b v~)
-  const float2* yR;           // forward intermediate (column pass of P m)
+  const float2* rspec;        // forward spectrum (P m_i)~ in row layout (theta only)
   const float2* dtab;
   const float* nbar;
   const float* nyq;
@@ -40,13 +39,11 @@ struct AdjRowParams {
   double* acc;                // [n_chunks][kAdjN]
 };
 
-struct Src4Rows {             // b = 0, 1: rows rA, rB of yV;  b = 2, 3: the same rows of yR
+struct Src2Rows {             // rows rA (b = 0) and rB (b = 1) of yV
   const float2* yV;
-  const float2* yR;
   int offA, offB;
   __device__ __forceinline__ float2 operator()(int b, int i) const {
-    const float2* y = b < 2 ? yV : yR;
-    return y[((b & 1) ? offB : offA) + i];
+    return yV[(b ? offB : offA) + i];
   }
 };
 
@@ -62,15 +59,14 @@ struct DstRowsAdj {           // inverse row DFT output with the conjugate four-
   }
 };
 
-// THETA: also transform the forward rows (yR) and form the theta sums; otherwise only the
-// filtered adjoint spectrum b v~ of the two rows of yV.
+// The filtered adjoint spectrum b v~ of rows rA, rB of yV; THETA: also the theta sums, with
+// the forward spectrum read from rspec.
 template <int M2, int T, bool THETA>
-__global__ void __launch_bounds__(T, THETA ? 1 : 2) k_row_adjoint(AdjRowParams q) {
+__global__ void __launch_bounds__(T, 2) k_row_adjoint(AdjRowParams q) {
   extern __shared__ float2 sm[];
   using Lay = RowLayout<M2>;
-  constexpr int NR = THETA ? 4 : 2;
   __shared__ double red[kAdjN - 1][32];
-  float2* tws = sm + NR * M2;
+  float2* tws = sm + 2 * M2;
   for (int i = threadIdx.x; i < tw_size(M2); i += T) tws[i] = q.g.tw_row[i];
   __syncthreads();
   const int jobs_pc = q.g.M1 / 2 + 1;
@@ -85,8 +81,7 @@ __global__ void __launch_bounds__(T, THETA ? 1 : 2) k_row_adjoint(AdjRowParams q
     const int rB = (M1 - rA) & (M1 - 1);
     const bool self = rA == rB;
     float2* yV = q.yV + (int64_t)ci * M;
-    const float2* yR = q.yR + (int64_t)ci * M;
-    smem_fft<M2, NR, Lay, T, -1>(sm, tws, Src4Rows{yV, yR, rA * M2, rB * M2});
+    smem_fft<M2, 2, Lay, T, -1>(sm, tws, Src2Rows{yV, rA * M2, rB * M2});
 
     const float tau = (float)d.tau;
     const float lt = lam_inf ? 0.f : (float)(q.lambda * d.tau);
@@ -96,6 +91,7 @@ __global__ void __launch_bounds__(T, THETA ? 1 : 2) k_row_adjoint(AdjRowParams q
     const bool has_par = THETA && q.params != nullptr;
     if (has_par) { fk = (float)q.params[4 * c + 1]; fs = (float)q.params[4 * c + 3]; }
     const float2* dt = q.dtab + d.spec;
+    const float2* rs = THETA ? q.rspec + d.spec : nullptr;
     const float* nb = q.nbar + d.spec;
     const float2 wa = q.g.tw_pack_a[rA];
     float s0 = 0.f, sal = 0.f, stau = 0.f, sT = 0.f;
@@ -139,15 +135,14 @@ __global__ void __launch_bounds__(T, THETA ? 1 : 2) k_row_adjoint(AdjRowParams q
       const int rowq = qs ? rB : rA;
       const int sk = rA * M2 + p, sp = rowq * M2 + qi;
       const float2 ZVk = sm[Lay::at(0, p)], ZVp = sm[Lay::at(qs, qi)];
-      const float2 ZRk = THETA ? sm[Lay::at(2, p)] : make_float2(0.f, 0.f);
-      const float2 ZRp = THETA ? sm[Lay::at(2 + qs, qi)] : make_float2(0.f, 0.f);
       if (rA == 0 && p == 0) {
         // k = 0 and k = M, both real: X_0 = Re Z_0 + Im Z_0, X_M = Re Z_0 - Im Z_0
         const float2 D = THETA ? dt[0] : make_float2(0.f, 0.f);
+        const float2 R0 = THETA ? rs[0] : make_float2(0.f, 0.f);   // (X_0, X_M)
         const float n0 = nb[0], nM = q.nyq[c];
-        const float2 Y0 = mode(make_float2(ZVk.x + ZVk.y, 0.f), make_float2(ZRk.x + ZRk.y, 0.f),
+        const float2 Y0 = mode(make_float2(ZVk.x + ZVk.y, 0.f), make_float2(R0.x, 0.f),
                                make_float2(D.x, 0.f), n0, 0, 1.f);
-        const float2 YM = mode(make_float2(ZVk.x - ZVk.y, 0.f), make_float2(ZRk.x - ZRk.y, 0.f),
+        const float2 YM = mode(make_float2(ZVk.x - ZVk.y, 0.f), make_float2(R0.y, 0.f),
                                make_float2(D.y, 0.f), nM, M, 1.f);
         sm[Lay::at(0, 0)] = make_float2(Y0.x + YM.x, Y0.x - YM.x);
         continue;
@@ -160,11 +155,11 @@ __global__ void __launch_bounds__(T, THETA ? 1 : 2) k_row_adjoint(AdjRowParams q
         Xk = cadd(E, wO);
         Xp = cconj(csub(E, wO));
       };
-      float2 Vk, Vp, Rk, Rp;
+      float2 Vk, Vp;
       split(ZVk, ZVp, Vk, Vp);
-      if (THETA) split(ZRk, ZRp, Rk, Rp);
-      else Rk = Rp = make_float2(0.f, 0.f);
       const bool same = (qs == 0 && qi == p);
+      const float2 Rk = THETA ? rs[sk] : make_float2(0.f, 0.f);
+      const float2 Rp = THETA && !same ? rs[sp] : make_float2(0.f, 0.f);
       const int k = rA + M1 * p;
       const float2 Dk = THETA ? dt[sk] : make_float2(0.f, 0.f);
       const float2 Dq = THETA && !same ? dt[sp] : make_float2(0.f, 0.f);
@@ -331,8 +326,8 @@ __global__ void k_adj_theta(int n_chunks, const ChunkDesc* desc, const double* p
 // ------------------------------------------------------------------------ launchers
 template <int M2>
 static cudaError_t row_adjoint_m2(const mm_plan_s* p, const Batch& b, float2* yV,
-                                  const float2* yR, double lambda, double* acc,
-                                  cudaStream_t st) {   // yR == NULL: no theta sums
+                                  const float2* rspec, double lambda, double* acc,
+                                  cudaStream_t st) {   // rspec == NULL: no theta sums
   constexpr int T = M2 / 8 < 32 ? 32 : (M2 / 8 > 1024 ? 1024 : M2 / 8);
   const Group& g = p->groups[b.group];
   AdjRowParams q;
@@ -341,15 +336,15 @@ static cudaError_t row_adjoint_m2(const mm_plan_s* p, const Batch& b, float2* yV
   q.count = b.count;
   q.g = g;
   q.yV = yV;
-  q.yR = yR;
+  q.rspec = rspec;
   q.dtab = p->dtab;
   q.nbar = p->nbar;
   q.nyq = p->nyq;
   q.params = p->theta_ok ? p->params : nullptr;
   q.lambda = lambda;
   q.acc = acc;
-  const bool theta = yR != nullptr;
-  const size_t smem = sizeof(float2) * ((theta ? 4 : 2) * M2 + tw_size(M2));
+  const bool theta = rspec != nullptr;
+  const size_t smem = sizeof(float2) * (2 * M2 + tw_size(M2));
   auto k = theta ? k_row_adjoint<M2, T, true> : k_row_adjoint<M2, T, false>;
   int grid = 0;
   cudaError_t e = persistent_grid(k, T, smem, (g.M1 / 2 + 1) * b.count, &grid);
@@ -359,18 +354,18 @@ static cudaError_t row_adjoint_m2(const mm_plan_s* p, const Batch& b, float2* yV
 }
 
 static cudaError_t launch_row_adjoint(const mm_plan_s* p, const Batch& b, float2* yV,
-                                      const float2* yR, double lambda, double* acc,
+                                      const float2* rspec, double lambda, double* acc,
                                       cudaStream_t st) {
   switch (p->groups[b.group].M2) {
-    case 16: return row_adjoint_m2<16>(p, b, yV, yR, lambda, acc, st);
-    case 32: return row_adjoint_m2<32>(p, b, yV, yR, lambda, acc, st);
-    case 64: return row_adjoint_m2<64>(p, b, yV, yR, lambda, acc, st);
-    case 128: return row_adjoint_m2<128>(p, b, yV, yR, lambda, acc, st);
-    case 256: return row_adjoint_m2<256>(p, b, yV, yR, lambda, acc, st);
-    case 512: return row_adjoint_m2<512>(p, b, yV, yR, lambda, acc, st);
-    case 1024: return row_adjoint_m2<1024>(p, b, yV, yR, lambda, acc, st);
-    case 2048: return row_adjoint_m2<2048>(p, b, yV, yR, lambda, acc, st);
-    case 4096: return row_adjoint_m2<4096>(p, b, yV, yR, lambda, acc, st);
+    case 16: return row_adjoint_m2<16>(p, b, yV, rspec, lambda, acc, st);
+    case 32: return row_adjoint_m2<32>(p, b, yV, rspec, lambda, acc, st);
+    case 64: return row_adjoint_m2<64>(p, b, yV, rspec, lambda, acc, st);
+    case 128: return row_adjoint_m2<128>(p, b, yV, rspec, lambda, acc, st);
+    case 256: return row_adjoint_m2<256>(p, b, yV, rspec, lambda, acc, st);
+    case 512: return row_adjoint_m2<512>(p, b, yV, rspec, lambda, acc, st);
+    case 1024: return row_adjoint_m2<1024>(p, b, yV, rspec, lambda, acc, st);
+    case 2048: return row_adjoint_m2<2048>(p, b, yV, rspec, lambda, acc, st);
+    case 4096: return row_adjoint_m2<4096>(p, b, yV, rspec, lambda, acc, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -437,7 +432,7 @@ using namespace mm;
 static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct AdjLayout {
-  size_t ckpt, seg, g, u4, m4, mp4, yR, acc, total;
+  size_t ckpt, seg, g, u4, m4, mp4, keep, acc, total;
   int nseg;
 };
 
@@ -454,7 +449,8 @@ static AdjLayout adj_layout(const mm_plan_s* p, int n_iter, int every) {
   L.u4 = take(m4);
   L.m4 = take(m4);
   L.mp4 = take(m4);
-  L.yR = take(p->ybuf_bytes);
+  // forward spectra (P m_i)~ of one segment's iterations, row layout, for the theta sums
+  L.keep = take(sizeof(float2) * (size_t)p->spec_total * (size_t)every);
   L.acc = take(sizeof(double) * kAdjN * (size_t)p->n_chunks);
   L.total = o;
   return L;
@@ -536,7 +532,8 @@ static mm_status adjoint_backward(mm_plan p, const double* lambdas, int n_iter,
   void* u4 = w + L.u4;
   void* m4 = w + L.m4;
   void* mp4 = w + L.mp4;
-  float2* yR = reinterpret_cast<float2*>(w + L.yR);
+  float2* keep = reinterpret_cast<float2*>(w + L.keep);
+  const size_t kstride = (size_t)p->spec_total;
   double* acc = reinterpret_cast<double*>(w + L.acc);
   const int64_t len = p->ncomp * p->n_pix;
   const size_t mstride = (size_t)len;
@@ -546,8 +543,8 @@ static mm_status adjoint_backward(mm_plan p, const double* lambdas, int n_iter,
   ADJ_CUDA(cudaMemsetAsync(grad_tod, 0, sizeof(float) * (size_t)p->n_total, s));
   ADJ_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * kAdjN * p->n_chunks, s));
   const unsigned nbp = (unsigned)((p->n_pix + 255) / 256), nbl = (unsigned)((len + 255) / 256);
-  // transposed step i (mi = m_i, mo = m_{i+1}: read only for the theta terms)
-  auto step = [&](int i, const double* mi, const double* mo) -> mm_status {
+  // transposed step i (mi = m_i, mo = m_{i+1}, rs = (P m_i)~: read only for the theta terms)
+  auto step = [&](int i, const double* mi, const double* mo, const float2* rs) -> mm_status {
     if (p->ncomp == 3)
       k_adj_prep<3><<<nbp, 256, 0, s>>>(p->n_pix, p->W, g, mi, mo, p->valid, u4, m4, mp4);
     else
@@ -557,8 +554,7 @@ static mm_status adjoint_backward(mm_plan p, const double* lambdas, int n_iter,
     for (int b = 0; b < p->n_batches; ++b) {
       const Batch& B = p->h_batches[b];
       ADJ_CUDA(launch_col_forward_ex(p, B, kSrcGather, nullptr, u4, p->ybuf, s));
-      if (theta) ADJ_CUDA(launch_col_forward_ex(p, B, kSrcGather, nullptr, m4, yR, s));
-      ADJ_CUDA(launch_row_adjoint(p, B, p->ybuf, theta ? yR : nullptr, lambdas[i], acc, s));
+      ADJ_CUDA(launch_row_adjoint(p, B, p->ybuf, theta ? rs : nullptr, lambdas[i], acc, s));
       ADJ_CUDA(launch_col_adjoint(p, B, x, theta, s));
     }
     k_adj_take_g<<<nbl, 256, 0, s>>>(len, p->ncomp, p->acc, p->valid, g);
@@ -569,7 +565,7 @@ static mm_status adjoint_backward(mm_plan p, const double* lambdas, int n_iter,
     // with lambda held constant the step is affine in (m, d): its transpose does not depend
     // on the iterates, so no checkpoint is read and nothing is recomputed
     for (int i = n_iter - 1; i >= 0; --i) {
-      mm_status st = step(i, g, g);
+      mm_status st = step(i, g, g, nullptr);
       if (st != MM_OK) return st;
     }
     return MM_OK;
@@ -578,14 +574,16 @@ static mm_status adjoint_backward(mm_plan p, const double* lambdas, int n_iter,
     const int i0 = sg * ckpt_every;
     const int i1 = i0 + ckpt_every < n_iter ? i0 + ckpt_every : n_iter;
     ADJ_CUDA(cudaMemcpyAsync(seg, ckpt + sg * mstride, mapb, cudaMemcpyDeviceToDevice, s));
-    for (int i = i0; i < i1; ++i) {   // recompute the segment's iterates m_{i0+1} .. m_{i1}
+    for (int i = i0; i < i1; ++i) {
+      // recompute m_{i+1} from m_i, keeping the forward spectrum (P m_i)~
       double* nxt = seg + (i - i0 + 1) * mstride;
       ADJ_CUDA(cudaMemcpyAsync(nxt, seg + (i - i0) * mstride, mapb, cudaMemcpyDeviceToDevice, s));
-      mm_status st = mm_messenger_iterate(p, lambdas + i, 1, MM_FP32_MIXED, nxt, nullptr, s);
+      mm_status st = messenger_step_keep(p, lambdas[i], nxt, keep + (i - i0) * kstride, s);
       if (st != MM_OK) return st;
     }
     for (int i = i1 - 1; i >= i0; --i) {
-      mm_status st = step(i, seg + (i - i0) * mstride, seg + (i - i0 + 1) * mstride);
+      mm_status st = step(i, seg + (i - i0) * mstride, seg + (i - i0 + 1) * mstride,
+                          keep + (i - i0) * kstride);
       if (st != MM_OK) return st;
     }
   }

@@ -1453,6 +1453,19 @@ extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int 
   return MM_OK;
 }
 
+mm_status mm::messenger_step_keep(mm_plan_s* p, double lambda, double* map_inout, float2* keep,
+                                  cudaStream_t s) {
+  mm_status st = load_map(p, map_inout, s);
+  if (st != MM_OK) return st;
+  RowArgs a{kRowMessengerKeep, lambda, nullptr, keep};
+  FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
+              L_(launch_col_inverse(p, B, s)));
+  if (p->ncomp == 3) k_bin_apply<3><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, map_inout);
+  else k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, map_inout);
+  LAUNCHED("k_bin_apply");
+  return MM_OK;
+}
+
 // ------------------------------------------------------- map-sized form of the iteration
 // Sec. 2.1 writes the step as m' = m_d(lambda) + F(lambda) m with
 //   m_d(lambda) = W P^T T^-1 F^-1[ lambda tau d~ / (lambda tau + Nbar) ]   (data only)

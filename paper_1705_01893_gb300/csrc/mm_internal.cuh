@@ -517,14 +517,17 @@ enum RowMode {
                       // partial sum_k w_k |X_k|^2 / N_k / n, inverse
   kRowMd = 7,         // no forward: Y = lambda tau d~ / (lambda tau + Nbar) (the m_d part), inverse
   // composite pointing (App. B), general path only:
-  kRowResidual = 8    // forward, Y = (d~ - X) / (n (Nbar / lambda + tau)), chi^2, inverse
+  kRowResidual = 8,   // forward, Y = (d~ - X) / (n (Nbar / lambda + tau)), chi^2, inverse
+  // the messenger step that also keeps its forward spectrum X = (P m)~ in row layout at
+  // RowArgs::natural + spec (the adjoint's recomputation; run-time instance only)
+  kRowMessengerKeep = 9
 };
 
 struct RowArgs {
   int mode;
   double lambda;       // cooling parameter (messenger) / N' = N + (lambda-1) tau (chi^2)
   double* chi2;        // device accumulator or nullptr
-  float2* natural;     // kRowNatural output
+  float2* natural;     // kRowNatural output (natural order), kRowMessengerKeep output (row layout)
   // Graph mode (lam_table != nullptr): lambda = lam_table[*iter] and the chi^2 slot is
   // chi2_base[0] + *iter when chi2_base[0] is set; the values live in device memory so one
   // captured CUDA graph serves every iteration of a schedule.
@@ -539,6 +542,10 @@ enum ColSrc { kSrcGather = 0, kSrcTod = 1 };
 cudaError_t launch_col_forward(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                cudaStream_t st);
 cudaError_t launch_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
+// One messenger iteration on map_inout (as mm_messenger_iterate) that also keeps each
+// chunk's forward spectrum (P m)~ in row layout at keep + ChunkDesc::spec (mm_api.cu).
+mm_status messenger_step_keep(mm_plan_s* p, double lambda, double* map_inout, float2* keep,
+                              cudaStream_t s);
 // Fused A + B + C launch of one batch's messenger iteration (mm_fused.cu).
 bool fused_eligible(const mm_plan_s* p, const Batch& b);
 int fused_items_per_chunk(int M1, int M2, bool general);

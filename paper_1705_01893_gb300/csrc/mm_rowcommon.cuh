@@ -67,7 +67,8 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   const int mode = MODE >= 0 ? MODE : q.a.mode;   // compile-time for the hot mode
   float2* y = q.ybuf + (int64_t)ci * d.M;
   const bool fwd = mode != kRowPcgRhs && mode != kRowMd;
-  const bool mess = mode == kRowMessenger || mode == kRowMessengerF || mode == kRowMd;
+  const bool mess = mode == kRowMessenger || mode == kRowMessengerF || mode == kRowMd ||
+                    mode == kRowMessengerKeep;
   const bool inv = mess || mode == kRowPcgApply || mode == kRowPcgRhs;
 
   if (fwd) {
@@ -164,6 +165,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
           o[M] = make_float2(XM, 0.f);
           continue;
         }
+        if (mode == kRowMessengerKeep) q.a.natural[d.spec] = make_float2(X0, XM);
         const float2 D = load_d ? dt[0] : make_float2(0.f, 0.f);
         const float n0 = nb[0], nM = __ldg(q.nyq + c);
         if (want_x2) {
@@ -195,6 +197,10 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
         o[k] = Xk;
         o[M - k] = Xp;
         continue;
+      }
+      if (mode == kRowMessengerKeep) {
+        q.a.natural[d.spec + sk] = Xk;
+        if (!same) q.a.natural[d.spec + sp] = Xp;
       }
       if (want_x2) {
         const float2 ek = csub(Dk[u], Xk), ep = csub(Dp[u], Xp);
