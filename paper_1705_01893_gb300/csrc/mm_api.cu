@@ -162,8 +162,10 @@ static int log_lo_of(int M) {
 static const int kGenLogLo = 10;
 
 static size_t tw_count(int M, int M1, int M2, bool general) {
+  // general lengths: per-pass tables of the column and row DFTs (fewer than 2 L entries for
+  // any radix plan of L), then the four-step and packing tables
   if (general)
-    return (size_t)M1 + M2 + (size_t(1) << kGenLogLo) + (size_t)(M >> kGenLogLo) + 1 + M1 + M2;
+    return (size_t)2 * M1 + 2 * M2 + (size_t(1) << kGenLogLo) + (size_t)(M >> kGenLogLo) + 1 + M1 + M2;
   const int lo = log_lo_of(M);
   return (size_t)tw_size(M1) + tw_size(M2) + (size_t(1) << lo) + (size_t)(M >> lo) + M1 + M2;
 }
@@ -377,6 +379,36 @@ __global__ void k_pass_twiddles(float2* out, int L) {
     off += ns * r;
     ns *= r;
   }
+}
+
+// Per-pass twiddles of a mixed-radix Stockham plan of length L: pass p (sub-transforms of
+// length Ns, radix R) stores w_{Ns R}^{r k} at [off_p + r Ns + k], r < R, k < Ns, so the
+// lanes of a pass (consecutive k) read consecutive words.  FP64, rounded to FP32.
+struct PassPlan {
+  int nr;
+  int8_t rad[kMaxRadices];
+};
+__global__ void k_plan_twiddles(float2* out, PassPlan pl) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  int off = 0, ns = 1;
+  for (int p = 0; p < pl.nr; ++p) {
+    const int r = pl.rad[p];
+    if (e < off + ns * r) {
+      const int loc = e - off, rr = loc / ns, k = loc % ns;
+      double sn, cs;
+      sincospi(-2.0 * (double)(rr * k) / (double)(ns * r), &sn, &cs);
+      out[e] = make_float2((float)cs, (float)sn);
+      return;
+    }
+    off += ns * r;
+    ns *= r;
+  }
+}
+
+static int plan_twiddle_count(const PassPlan& pl) {
+  int off = 0, ns = 1;
+  for (int p = 0; p < pl.nr; ++p) { off += ns * pl.rad[p]; ns *= pl.rad[p]; }
+  return off;
 }
 
 __global__ void k_twiddles(float2* out, int count, int denom_mul, int L) {
@@ -935,6 +967,23 @@ static cudaError_t gen_upload(mm_plan_s* p, cudaStream_t s) {
   p->h_gen_rjob[ng] = rj;
   p->h_gen_yoff[ng] = yo;
   if (ct_n > p->gen_ccap) return cudaErrorInvalidValue;
+  // per-pass DFT tables of every general group, for the radix order in use
+  for (int g = 0; g < p->n_groups; ++g) {
+    const Group& G = p->groups[g];
+    if (!G.general) continue;
+    for (int dim = 0; dim < 2; ++dim) {
+      PassPlan pl;
+      memset(&pl, 0, sizeof(pl));
+      pl.nr = radix_plan(dim ? G.M2 : G.M1, pl.rad, p->gen_tune.radix_order);
+      if (pl.nr < 0) return cudaErrorInvalidValue;
+      const int cnt = plan_twiddle_count(pl);
+      if (cnt > 2 * (dim ? G.M2 : G.M1)) return cudaErrorInvalidValue;
+      if (cnt > 0)   // a length-1 DFT has no pass
+        k_plan_twiddles<<<blocks_for(cnt, 256), 256, 0, s>>>(dim ? G.tw_row : G.tw_col, pl);
+    }
+  }
+  cudaError_t ek = cudaGetLastError();
+  if (ek != cudaSuccess) return ek;
   cudaError_t e;
   const size_t b = sizeof(int64_t) * (ng + 1);
   if ((e = cudaMemcpyAsync(p->gen_ctile, p->h_gen_ctile, b, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
@@ -1123,8 +1172,8 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
     for (int c = 0; c < n_chunks; ++c)
       if (L.chunk_group[c] == g) { order.push_back(c); G.n_chunks++; }
     float2* t = p->tw_pool + tw_off;
-    G.tw_col = t; t += G.general ? G.M1 : tw_size(G.M1);
-    G.tw_row = t; t += G.general ? G.M2 : tw_size(G.M2);
+    G.tw_col = t; t += G.general ? 2 * G.M1 : tw_size(G.M1);
+    G.tw_row = t; t += G.general ? 2 * G.M2 : tw_size(G.M2);
     G.tw_lo = t; t += (1 << G.log_lo);
     G.tw_hi = t; t += (G.M >> G.log_lo) + (G.general ? 1 : 0);
     G.tw_pack_a = t; t += G.M1;
@@ -1188,8 +1237,7 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
   for (int g = 0; g < L.n_groups; ++g) {
     const Group& G = p->groups[g];
     if (G.general) {
-      k_twiddles<<<blocks_for(G.M1, 256), 256, 0, s>>>(G.tw_col, G.M1, 1, G.M1);
-      k_twiddles<<<blocks_for(G.M2, 256), 256, 0, s>>>(G.tw_row, G.M2, 1, G.M2);
+      // per-pass DFT tables: built for the tuned radix order by gen_upload
     } else {
       k_pass_twiddles<<<blocks_for(tw_size(G.M1), 256), 256, 0, s>>>(G.tw_col, G.M1);
       k_pass_twiddles<<<blocks_for(tw_size(G.M2), 256), 256, 0, s>>>(G.tw_row, G.M2);

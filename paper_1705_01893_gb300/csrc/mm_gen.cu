@@ -84,7 +84,7 @@ __device__ __forceinline__ int lay(int e, bool pad) { return pad ? e + (e >> 4) 
 template <int R, int DIR>
 __device__ __forceinline__ void gpass_cols(const float2* src, float2* dst, int L, int Ns, int NB,
                                            int lnb, const float2* __restrict__ tw, int T) {
-  const int nb = L / R, mul = L / (Ns * R);
+  const int nb = L / R;
   const int c = threadIdx.x & (NB - 1);
   const int di = T >> lnb;
   int i = threadIdx.x >> lnb;
@@ -99,7 +99,7 @@ __device__ __forceinline__ void gpass_cols(const float2* src, float2* dst, int L
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const float2 w = __ldg(tw + r * k * mul);
+        const float2 w = __ldg(tw + r * Ns + k);   // this pass's table: w_{Ns R}^{r k}
         v[r] = DIR < 0 ? cmul(v[r], w) : cmulc(v[r], w);
       }
     }
@@ -118,7 +118,7 @@ __device__ __forceinline__ void gpass_cols(const float2* src, float2* dst, int L
 template <int R, int DIR, bool PS, bool PD>
 __device__ __forceinline__ void gpass_rows(const float2* src, float2* dst, int L, int Ns, int nseq,
                                            const float2* __restrict__ tw, int T) {
-  const int nb = L / R, mul = L / (Ns * R);
+  const int nb = L / R;
   const int total = nb * nseq;
   int b = threadIdx.x;
   if (b >= total) return;
@@ -135,7 +135,7 @@ __device__ __forceinline__ void gpass_rows(const float2* src, float2* dst, int L
     if (Ns > 1) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const float2 w = __ldg(tw + r * k * mul);
+        const float2 w = __ldg(tw + r * Ns + k);   // this pass's table: w_{Ns R}^{r k}
         v[r] = DIR < 0 ? cmul(v[r], w) : cmulc(v[r], w);
       }
     }
@@ -179,6 +179,7 @@ __device__ float2* gen_dft_rows(float2* a, float2* b, bool& pad, int L, int nr, 
     __syncthreads();
     float2* t = a; a = b; b = t;
     pad = (R & 1) == 0;
+    tw += Ns * R;   // the next pass's table
     Ns *= R;
   }
   return a;
@@ -200,6 +201,7 @@ __device__ float2* gen_dft_cols(float2* a, float2* b, int L, int nr, const int8_
     }
     __syncthreads();
     float2* t = a; a = b; b = t;
+    tw += Ns * R;   // the next pass's table
     Ns *= R;
   }
   return a;

@@ -41,9 +41,9 @@ struct Group {
   int nr1, nr2;            // general: radix sequences of the M1 and M2 DFTs
   int8_t rad1[kMaxRadices], rad2[kMaxRadices];
   int* chunks;             // device: chunk indices of this group
-  float2* tw_col;          // per-pass twiddles of the length-M1 DFT (see tw_offset);
-                           // general: [M1] exp(-2 pi i m / M1)
-  float2* tw_row;          // per-pass twiddles of the length-M2 DFT; general: [M2]
+  float2* tw_col;          // per-pass twiddles of the length-M1 DFT (see tw_offset;
+                           // general: [< 2 M1], pass tables of the tuned radix plan)
+  float2* tw_row;          // per-pass twiddles of the length-M2 DFT (general: [< 2 M2])
   float2* tw_lo;           // [2^log_lo]          exp(-2 pi i m / M)
   float2* tw_hi;           // [M >> log_lo (+1)]   exp(-2 pi i m 2^log_lo / M)
   float2* tw_pack_a;       // [M1]  exp(-2 pi i m / (2M))     (real-pack twiddle, k1 part)
@@ -103,8 +103,8 @@ struct GenChunk {
   int c;                   // chunk index in the plan
   int log_lo, nr1, nr2;
   int64_t yoff;            // intermediate offset in the general list
-  const float2* tw_col;    // [M1] exp(-2 pi i m / M1)
-  const float2* tw_row;    // [M2] exp(-2 pi i m / M2)
+  const float2* tw_col;    // per-pass tables of the M1 DFT for the radix plan rad1
+  const float2* tw_row;    // per-pass tables of the M2 DFT for the radix plan rad2
   const float2* tw_lo;
   const float2* tw_hi;
   const float2* pack_a;
