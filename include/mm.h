@@ -24,8 +24,14 @@
  *  - Maps are float64 row-major [n_pix][ncomp], ncomp = 1 (T) or 3 (I, Q, U).  Pixels that
  *    are unobserved or cut read back as 0.  Cut: a pixel is kept iff it has >= 1 hit and,
  *    for IQU, eigmin/eigmax of its 3x3 block of P^T T^-1 P is >= rcond_min.
- *  - Chunk lengths: n_c even with n_c/2 a power of two in [2^8, 2^23] in this version;
- *    other lengths return MM_ERR_UNSUPPORTED.
+ *  - Chunk lengths: any n_c in [4, 2^24] whose prime factors are 2, 3 and 5, with
+ *    m = n_c/2 (even n_c) or n_c (odd n_c) splitting as m = M1 M2, M1 <= 512, M2 <= 4096.
+ *    n_c = 2m with m a power of two in [2^8, 2^23] and a chunk offset divisible by 4 runs
+ *    the compile-time kernels (and, for m = 2^21 with single pointing, the fused launch);
+ *    the other lengths run the general mixed-radix kernels.  Other lengths return
+ *    MM_ERR_UNSUPPORTED.  Entry points that support only the compile-time lengths say so.
+ *  - One plan, one call at a time: calls on the same plan share its workspace (buffers,
+ *    counters) and must not overlap in time; order them on one stream or synchronise.
  *  - Errors: every call returns an mm_status; on failure mm_last_error() describes it.
  *    A failed call leaves caller buffers unspecified and the plan usable, except
  *    MM_ERR_STATE, which marks an entry point called out of order.
@@ -155,7 +161,9 @@ mm_status mm_messenger_stage(mm_plan p, int stage, int batch, double lambda,
 mm_status mm_messenger_graph(mm_plan p, const double* lambdas, int n_iter, double* map_inout,
                              double* chi2_out, void* stream);
 
-/* Bytes of device work space mm_messenger_plain_fp64 needs (all chunks one length). */
+/* Bytes of device work space mm_messenger_plain_fp64 needs.  The plain step takes plans
+ * whose chunks all have one compile-time length (power-of-two half); others return
+ * MM_ERR_UNSUPPORTED. */
 mm_status mm_plain_work_bytes(mm_plan p, size_t* bytes);
 
 /* The plain FP64 messenger iteration, the same-GPU comparison bar of the FP32 path: per
@@ -186,7 +194,8 @@ mm_status mm_adjoint_work_bytes(mm_plan p, int n_iter, int ckpt_every, size_t* b
  * dL/dm = P^T irfft(b v~)/tau, with a = lambda tau / (lambda tau + Nbar), b = 1 - a) runs on
  * the GPU for every iteration in reverse; forward iterates are recomputed from checkpoints
  * taken every ckpt_every iterations (the plan's own buffers are reused).  FP32 timestreams
- * and FFTs, FP64 accumulation.  Chunks up to 2^22 samples.  Asynchronous on `stream`. */
+ * and FFTs, FP64 accumulation.  Compile-time chunk lengths only (power-of-two halves), up
+ * to 2^22 samples; other plans return MM_ERR_UNSUPPORTED.  Asynchronous on `stream`. */
 mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int n_iter,
                                const double* map_in, const double* grad_map_out,
                                float* grad_tod, double* grad_theta, int ckpt_every,
