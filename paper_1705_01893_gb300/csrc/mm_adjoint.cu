@@ -303,7 +303,7 @@ __global__ void k_adj_take_g(int64_t len, int ncomp, double* __restrict__ acc,
                              const uint8_t* __restrict__ valid, double* __restrict__ g) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= len) return;
-  const int64_t a = (i % ncomp) * (len / ncomp) + i / ncomp;   // planar accumulators
+  const int64_t a = (i % ncomp) * acc_stride_of(len / ncomp, ncomp) + i / ncomp;   // planar
   g[i] = valid[i / ncomp] ? acc[a] : 0.0;
   acc[a] = 0.0;
 }
@@ -388,7 +388,7 @@ static cudaError_t col_adjoint_m1(const mm_plan_s* p, const Batch& b, const AdjC
   q.tod = nullptr;
   q.ybuf = p->ybuf;
   q.acc = p->acc;
-  q.acc_stride = p->n_pix;
+  q.acc_stride = acc_stride_of(p->n_pix, p->ncomp);
   const int ntiles = (g.M2 / kColCB) * b.count;
   const size_t smem = sizeof(float2) * M1 * kColCB;
   int grid = 0;

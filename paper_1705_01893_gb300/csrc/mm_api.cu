@@ -286,7 +286,7 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->valid = take(np);
   L->W = take(sizeof(double) * blk * np);
   L->Minv = take(sizeof(double) * blk * np);
-  L->acc = take(sizeof(double) * ncomp * np);
+  L->acc = take(sizeof(double) * ncomp * (size_t)acc_stride_of((int64_t)np, ncomp));
   L->acc12 = take(sizeof(double) * 2 * blk * np);
   L->map4 = take((ncomp == 3 ? 16 : 4) * np);
   L->bvec = take(sizeof(double) * ncomp * np);
@@ -645,7 +645,11 @@ __global__ void k_bin_apply(int64_t n_pix, double* __restrict__ acc, const doubl
   constexpr int B = NC == 3 ? 6 : 1;
   double a[NC], w[B], m[NC];
 #pragma unroll
-  for (int i = 0; i < NC; ++i) { a[i] = acc[i * n_pix + p]; acc[i * n_pix + p] = 0.0; }
+  for (int i = 0; i < NC; ++i) {
+    const int64_t j_ = i * acc_stride_of(n_pix, NC) + p;   // planar accumulators
+    a[i] = acc[j_];
+    acc[j_] = 0.0;
+  }
 #pragma unroll
   for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
   sym_apply<NC>(w, a, m);
@@ -666,7 +670,11 @@ __global__ void k_bin_resid(int64_t n_pix, double* __restrict__ acc, const doubl
   constexpr int B = NC == 3 ? 6 : 1;
   double a[NC], w[B], u[NC], m[NC];
 #pragma unroll
-  for (int i = 0; i < NC; ++i) { a[i] = acc[i * n_pix + p]; acc[i * n_pix + p] = 0.0; }
+  for (int i = 0; i < NC; ++i) {
+    const int64_t j_ = i * acc_stride_of(n_pix, NC) + p;   // planar accumulators
+    a[i] = acc[j_];
+    acc[j_] = 0.0;
+  }
 #pragma unroll
   for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
   sym_apply<NC>(w, a, u);
@@ -766,7 +774,7 @@ __global__ void k_finish_b(int64_t len, int ncomp, double* __restrict__ acc,
                            const uint8_t* __restrict__ valid, double* __restrict__ b) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= len) return;
-  const int64_t a = (i % ncomp) * (len / ncomp) + i / ncomp;   // planar accumulators
+  const int64_t a = (i % ncomp) * acc_stride_of(len / ncomp, ncomp) + i / ncomp;   // planar
   b[i] = valid[i / ncomp] ? acc[a] : 0.0;
   acc[a] = 0.0;
 }
@@ -813,8 +821,9 @@ __global__ void k_pcg_init(int64_t n_pix, double* __restrict__ acc, const double
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
       const int64_t j = NC * p + i;
-      rr[i] = ok ? bvec[j] - acc[i * n_pix + p] : 0.0;
-      acc[i * n_pix + p] = 0.0;
+      const int64_t ja = i * acc_stride_of(n_pix, NC) + p;   // planar accumulators
+      rr[i] = ok ? bvec[j] - acc[ja] : 0.0;
+      acc[ja] = 0.0;
     }
     block_apply<NC>(Minv, p, rr, zz);
 #pragma unroll
@@ -847,7 +856,7 @@ __global__ void k_pcg_q(int64_t len, int ncomp, double* __restrict__ acc, const 
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double s = 0.0;
   if (i < len) {
-    const int64_t a = (i % ncomp) * (len / ncomp) + i / ncomp;   // planar accumulators
+    const int64_t a = (i % ncomp) * acc_stride_of(len / ncomp, ncomp) + i / ncomp;   // planar
     const double qq = valid[i / ncomp] ? acc[a] : 0.0;
     acc[a] = 0.0;
     q[i] = qq;
@@ -1257,7 +1266,8 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
   }
   if ((e = cudaMemsetAsync(p->hits, 0, sizeof(int32_t) * n_pix, s)) != cudaSuccess) return fail("memset", e);
   if ((e = cudaMemsetAsync(p->scal, 0, sizeof(double) * kScalCount, s)) != cudaSuccess) return fail("memset", e);
-  if ((e = cudaMemsetAsync(p->acc, 0, sizeof(double) * ncomp * n_pix, s)) != cudaSuccess) return fail("memset", e);
+  if ((e = cudaMemsetAsync(p->acc, 0, sizeof(double) * ncomp * acc_stride_of(n_pix, ncomp), s)) != cudaSuccess)
+    return fail("memset", e);
   if ((e = cudaMemsetAsync(p->row_queue, 0, 64, s)) != cudaSuccess) return fail("memset", e);
   if ((e = cudaMemsetAsync(p->fused_ctr, 0, sizeof(unsigned) * (2 + 2 * (size_t)n_chunks), s)) != cudaSuccess)
     return fail("memset", e);
@@ -1419,7 +1429,7 @@ extern "C" mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const do
   }
   // b = P^T N^-1 d and d^T N^-1 d
   {
-    MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * p->ncomp * p->n_pix, s));
+    MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * p->ncomp * acc_stride_of(p->n_pix, p->ncomp), s));
     RowArgs a{kRowPcgRhs, 1.0, p->scal + kScalCdd, nullptr};
     FOR_BATCHES(L_(launch_row(p, B, a, s)); L_(launch_col_inverse(p, B, s)));
     const int64_t len = p->ncomp * p->n_pix;
@@ -1538,7 +1548,11 @@ __global__ void k_bin_md(int64_t n_pix, double* __restrict__ acc, const double* 
     constexpr int B = NC == 3 ? 6 : 1;
     double a[NC], w[B], m[NC];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) { a[i] = acc[i * n_pix + p]; acc[i * n_pix + p] = 0.0; }
+    for (int i = 0; i < NC; ++i) {
+    const int64_t j_ = i * acc_stride_of(n_pix, NC) + p;   // planar accumulators
+    a[i] = acc[j_];
+    acc[j_] = 0.0;
+  }
 #pragma unroll
     for (int i = 0; i < B; ++i) w[i] = W[B * p + i];
     sym_apply<NC>(w, a, m);
@@ -1620,7 +1634,7 @@ extern "C" mm_status mm_messenger_iterate_md(mm_plan p, const double* lambdas, i
   const int64_t len = p->ncomp * p->n_pix;
   cudaStream_t s = S(stream);
   const unsigned nbp = blocks_for(p->n_pix, 256);
-  MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * len, s));
+  MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * p->ncomp * acc_stride_of(p->n_pix, p->ncomp), s));
   for (size_t j = 0; j < lv.size(); ++j) {
     RowArgs a{kRowMd, lv[j], nullptr, nullptr};
     FOR_BATCHES(L_(launch_row(p, B, a, s)); L_(launch_col_inverse(p, B, s)));
@@ -2224,7 +2238,7 @@ extern "C" mm_status mm_autotune(mm_plan p, void* stream) {
   }
   mm_status st = apply_tune(p, best, s);
   if (st != MM_OK) return st;
-  MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * p->ncomp * p->n_pix, s));
+  MM_CUDA(cudaMemsetAsync(p->acc, 0, sizeof(double) * p->ncomp * acc_stride_of(p->n_pix, p->ncomp), s));
   MM_CUDA(cudaStreamSynchronize(s));
   return MM_OK;
 }

@@ -117,7 +117,7 @@ static ColParams make_params(const mm_plan_s* p, const Batch& b, const float* to
   q.tod = tod;
   q.ybuf = ybuf ? ybuf : p->ybuf;
   q.acc = p->acc;
-  q.acc_stride = p->n_pix;
+  q.acc_stride = acc_stride_of(p->n_pix, p->ncomp);
   return q;
 }
 

@@ -666,7 +666,7 @@ static GenParams gen_params(const mm_plan_s* p, const Batch& b, const int2* item
   q.map4 = p->map4;
   q.ybuf = p->ybuf;
   q.acc = p->acc;
-  q.acc_stride = p->n_pix;
+  q.acc_stride = acc_stride_of(p->n_pix, p->ncomp);
   q.dtab = p->dtab;
   q.nbar = p->nbar;
   q.nyq = p->nyq;

@@ -230,6 +230,13 @@ __device__ __forceinline__ float2 mul_i(float2 a) {
 
 __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
 
+// Distance between the component planes of the FP64 pixel accumulators ([ncomp][stride]):
+// n_pix rounded up to 32 and skewed by 32 more, so that planes are never a power of two
+// apart (measured: the 4 M-pixel map step 0.256 -> 0.244 ms, no change at 262 k pixels).
+__host__ __device__ __forceinline__ int64_t acc_stride_of(int64_t n_pix, int ncomp) {
+  return ncomp == 1 ? n_pix : ((n_pix + 31) / 32) * 32 + 32;
+}
+
 // ------------------------------------------------------------------------- butterflies
 // In-register DFTs of length 2, 4, 8 with kernel exp(DIR * 2 pi i jk / R).
 template <int DIR>
