@@ -1974,8 +1974,9 @@ extern "C" mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes) {
 
 static mm_status apply_A(mm_plan p, cudaStream_t s) {
   RowArgs a{kRowPcgApply, 1.0, nullptr, nullptr};
-  FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
-              L_(launch_col_inverse(p, B, s)));
+  FOR_BATCHES(if (fused_eligible(p, B)) { L_(launch_fused(p, B, a, s)); } else {
+                L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
+                L_(launch_col_inverse(p, B, s)); });
   return MM_OK;
 }
 

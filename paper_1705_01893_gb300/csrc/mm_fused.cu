@@ -39,7 +39,9 @@ __device__ __forceinline__ void wait_count(const unsigned* c, unsigned target, i
   atomicExch(fault, 1);
 }
 
-template <int M1, int M2, int CB, int T, int NC>
+// MODE: the row jobs' mode, kRowMessenger (the messenger step) or kRowPcgApply (the PCG
+// operator A p of the comparison solver).
+template <int M1, int M2, int CB, int T, int NC, int MODE>
 __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
   extern __shared__ float2 sm[];
   __shared__ float red[32];
@@ -89,16 +91,16 @@ __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
           sm, q.c.g.tw_col, SrcGather<NC, CB>{&q.c, d.off + (int64_t)idx * (2 * CB * M1)}, dst);
     } else if (kind == kItemB) {
       if (threadIdx.x == 0) {
-        // this job's d~ and Nbar rows into L2 while the forward row DFTs run
+        // this job's d~ (messenger only) and Nbar rows into L2 while the forward row DFTs run
         const int rb = (M1 - idx) & (M1 - 1);
-        prefetch_l2(q.r.dtab + d.spec + (int64_t)idx * M2, 8 * M2);
+        if (MODE == kRowMessenger) prefetch_l2(q.r.dtab + d.spec + (int64_t)idx * M2, 8 * M2);
         prefetch_l2(q.r.nbar + d.spec + (int64_t)idx * M2, 4 * M2);
         if (rb != idx) {
-          prefetch_l2(q.r.dtab + d.spec + (int64_t)rb * M2, 8 * M2);
+          if (MODE == kRowMessenger) prefetch_l2(q.r.dtab + d.spec + (int64_t)rb * M2, 8 * M2);
           prefetch_l2(q.r.nbar + d.spec + (int64_t)rb * M2, 4 * M2);
         }
       }
-      kernel_body_job<M2, T, kRowMessenger>(q.r, sm, tws, red, ci, idx);
+      kernel_body_job<M2, T, MODE>(q.r, sm, tws, red, ci, idx);
     } else {
       constexpr int NS = M1 * 2 * CB;
       const float* smf = reinterpret_cast<const float*>(sm);
@@ -175,6 +177,7 @@ int fused_build_items(int M1, int M2, int count, int2* out) {
   return n;
 }
 
+// a.mode: kRowMessenger or kRowPcgApply.
 cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
   const int bi = (int)(&b - p->h_batches);
   const Group& g = p->groups[b.group];
@@ -186,17 +189,16 @@ cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, c
   q.ctr = p->fused_ctr;
   q.fault = p->fault;
   const size_t smem = sizeof(float2) * 2 * g.M2;
+  const bool pcg = a.mode == kRowPcgApply;
+  if (a.mode != kRowMessenger && !pcg) return cudaErrorInvalidValue;
+  auto k = p->ncomp == 3 ? (pcg ? k_fused<512, 4096, kColCB, 512, 3, kRowPcgApply>
+                                : k_fused<512, 4096, kColCB, 512, 3, kRowMessenger>)
+                         : (pcg ? k_fused<512, 4096, kColCB, 512, 1, kRowPcgApply>
+                                : k_fused<512, 4096, kColCB, 512, 1, kRowMessenger>);
   int grid = 0;
-  cudaError_t e;
-  if (p->ncomp == 3) {
-    auto k = k_fused<512, 4096, kColCB, 512, 3>;
-    if ((e = persistent_grid(k, 512, smem, q.n_items, &grid)) != cudaSuccess) return e;
-    k<<<grid, 512, smem, st>>>(q);
-  } else {
-    auto k = k_fused<512, 4096, kColCB, 512, 1>;
-    if ((e = persistent_grid(k, 512, smem, q.n_items, &grid)) != cudaSuccess) return e;
-    k<<<grid, 512, smem, st>>>(q);
-  }
+  cudaError_t e = persistent_grid(k, 512, smem, q.n_items, &grid);
+  if (e != cudaSuccess) return e;
+  k<<<grid, 512, smem, st>>>(q);
   return cudaGetLastError();
 }
 

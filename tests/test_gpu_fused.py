@@ -103,3 +103,21 @@ def test_fused_not_used_for_other_shapes():
     s = synth.config_iqu(32, 2, 1 << 18, 48)
     plan = binding.plan_from_synth(s, DEV)
     assert plan.n_fused_batches() == 0
+
+
+def test_fused_pcg_operator_against_oracle():
+    """PCG on a chunk of 2^22 samples runs its operator A p = P^T N^-1 P p as one fused
+    launch per iteration (row jobs in the 1/N mode): 2 iterations against the FP64 PCG."""
+    s = synth.config_iqu(16, 1, N22, 49)
+    prob = O.problem_from_synth(s)
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_fused_batches() == 1
+    x_ref, chi_ref = O.pcg(prob, 2)
+    x = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    chi = torch.zeros(2, dtype=torch.float64, device=DEV)
+    plan.pcg(x, 2, restart=True, chi2_out=chi)
+    torch.cuda.synchronize()
+    assert plan.fault_flags() == 0
+    assert rel(x.cpu().numpy(), x_ref) <= 1e-5
+    c = chi.cpu().numpy()
+    assert np.max(np.abs(c - chi_ref) / chi_ref) <= 1e-5
