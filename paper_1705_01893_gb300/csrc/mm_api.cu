@@ -1655,8 +1655,9 @@ extern "C" mm_status mm_messenger_iterate_md(mm_plan p, const double* lambdas, i
   }
   for (int it = 0; it < n_iter; ++it) {
     RowArgs a{kRowMessengerF, lambdas[it], chi2_out ? chi2_out + it : nullptr, nullptr};
-    FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
-                L_(launch_col_inverse(p, B, s)));
+    FOR_BATCHES(if (fused_eligible(p, B)) { L_(launch_fused(p, B, a, s)); } else {
+                  L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s));
+                  L_(launch_col_inverse(p, B, s)); });
     const double* mdl = md + (size_t)p->ncomp * p->n_pix * lev[it];
     double* mo = it == n_iter - 1 ? map_inout : nullptr;
     double* cn = chi2_out && it + 1 < n_iter ? chi2_out + it + 1 : nullptr;

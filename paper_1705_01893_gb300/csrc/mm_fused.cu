@@ -39,8 +39,9 @@ __device__ __forceinline__ void wait_count(const unsigned* c, unsigned target, i
   atomicExch(fault, 1);
 }
 
-// MODE: the row jobs' mode, kRowMessenger (the messenger step) or kRowPcgApply (the PCG
-// operator A p of the comparison solver).
+// MODE: the row jobs' mode, kRowMessenger (the messenger step), kRowMessengerF (its
+// map-sized form, F(lambda) m) or kRowPcgApply (the PCG operator A p of the comparison
+// solver).
 template <int M1, int M2, int CB, int T, int NC, int MODE>
 __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
   extern __shared__ float2 sm[];
@@ -177,7 +178,7 @@ int fused_build_items(int M1, int M2, int count, int2* out) {
   return n;
 }
 
-// a.mode: kRowMessenger or kRowPcgApply.
+// a.mode: kRowMessenger, kRowMessengerF or kRowPcgApply.
 cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
   const int bi = (int)(&b - p->h_batches);
   const Group& g = p->groups[b.group];
@@ -189,12 +190,17 @@ cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, c
   q.ctr = p->fused_ctr;
   q.fault = p->fault;
   const size_t smem = sizeof(float2) * 2 * g.M2;
-  const bool pcg = a.mode == kRowPcgApply;
-  if (a.mode != kRowMessenger && !pcg) return cudaErrorInvalidValue;
-  auto k = p->ncomp == 3 ? (pcg ? k_fused<512, 4096, kColCB, 512, 3, kRowPcgApply>
-                                : k_fused<512, 4096, kColCB, 512, 3, kRowMessenger>)
-                         : (pcg ? k_fused<512, 4096, kColCB, 512, 1, kRowPcgApply>
-                                : k_fused<512, 4096, kColCB, 512, 1, kRowMessenger>);
+  void (*k)(FusedParams) = nullptr;
+  if (p->ncomp == 3) {
+    if (a.mode == kRowMessenger) k = k_fused<512, 4096, kColCB, 512, 3, kRowMessenger>;
+    if (a.mode == kRowMessengerF) k = k_fused<512, 4096, kColCB, 512, 3, kRowMessengerF>;
+    if (a.mode == kRowPcgApply) k = k_fused<512, 4096, kColCB, 512, 3, kRowPcgApply>;
+  } else {
+    if (a.mode == kRowMessenger) k = k_fused<512, 4096, kColCB, 512, 1, kRowMessenger>;
+    if (a.mode == kRowMessengerF) k = k_fused<512, 4096, kColCB, 512, 1, kRowMessengerF>;
+    if (a.mode == kRowPcgApply) k = k_fused<512, 4096, kColCB, 512, 1, kRowPcgApply>;
+  }
+  if (k == nullptr) return cudaErrorInvalidValue;
   int grid = 0;
   cudaError_t e = persistent_grid(k, 512, smem, q.n_items, &grid);
   if (e != cudaSuccess) return e;

@@ -121,3 +121,25 @@ def test_fused_pcg_operator_against_oracle():
     assert rel(x.cpu().numpy(), x_ref) <= 1e-5
     c = chi.cpu().numpy()
     assert np.max(np.abs(c - chi_ref) / chi_ref) <= 1e-5
+
+
+def test_fused_map_sized_form_matches_step():
+    """The map-sized form m' = m_d(lambda) + F(lambda) m (Sec. 2.1) with its F part as the
+    fused launch (row jobs in the F mode) against the fused messenger step on the same plan
+    (two chunks of 2^22 samples; same tolerances as the small-size map-sized test)."""
+    s = synth.config_iqu(32, 2, N22, 50)
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_fused_batches() == 1
+    lam = binding.cooling_schedule(plan.lambda_max(), 3, 2)
+    m0 = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    a = m0.clone()
+    ca = torch.zeros(len(lam), dtype=torch.float64, device=DEV)
+    plan.messenger_md(a, lam, ca)
+    b = m0.clone()
+    cb = torch.zeros(len(lam), dtype=torch.float64, device=DEV)
+    plan.messenger(b, lam, cb)
+    torch.cuda.synchronize()
+    assert plan.fault_flags() == 0
+    assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-5
+    c_a, c_b = ca.cpu().numpy()[1:], cb.cpu().numpy()[1:]
+    assert np.max(np.abs(c_a - c_b) / c_b) <= 1e-5
