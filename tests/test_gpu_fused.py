@@ -143,3 +143,48 @@ def test_fused_map_sized_form_matches_step():
     assert rel(a.cpu().numpy(), b.cpu().numpy()) <= 1e-5
     c_a, c_b = ca.cpu().numpy()[1:], cb.cpu().numpy()[1:]
     assert np.max(np.abs(c_a - c_b) / c_b) <= 1e-5
+
+
+def test_fused_stage_matches_iterate_and_refuses_other_batches():
+    """MM_STAGE_FUSED through the stage API gives mm_messenger_iterate's iterate; on a batch
+    that is not fused it returns MM_ERR_UNSUPPORTED and launches nothing."""
+    s = synth.config_iqu(32, 2, N22, 51)
+    plan = binding.plan_from_synth(s, DEV)
+    lams = [math.inf, 200.0, 20.0]
+    m1 = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    plan.messenger(m1, lams)
+    m2 = torch.zeros_like(m1)
+    plan.stage(binding.MM_STAGE_LOAD, map_inout=m2)
+    for i, lam in enumerate(lams):
+        for b in range(plan.n_batches()):
+            plan.stage(binding.MM_STAGE_FUSED, b, lam)
+        plan.stage(binding.MM_STAGE_MAP, map_inout=m2 if i == len(lams) - 1 else None)
+    torch.cuda.synchronize()
+    assert rel(m2.cpu().numpy(), m1.cpu().numpy()) <= 1e-9
+    assert plan.fault_flags() == 0
+    small = binding.plan_from_synth(synth.config_iqu(16, 2, 1 << 14, 52), DEV)
+    with pytest.raises(binding.MMError) as e:
+        small.stage(binding.MM_STAGE_FUSED, 0, 10.0)
+    assert e.value.code == binding.MM_ERR_UNSUPPORTED
+
+
+def test_fused_several_batches(monkeypatch):
+    """A 16 MB intermediate budget puts each 2^22-sample chunk in its own batch: three fused
+    launches per iteration, one after the other, against the single-batch plan."""
+    s = synth.config_iqu(32, 3, N22, 53)
+    lams = [math.inf, 100.0, 10.0, 1.0]
+    plan1 = binding.plan_from_synth(s, DEV)
+    assert plan1.n_batches() == 1
+    m1 = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    plan1.messenger(m1, lams)
+    monkeypatch.setenv("MM_YBUF_MB", "16")
+    plan3 = binding.plan_from_synth(s, DEV)
+    assert plan3.n_batches() == 3 and plan3.n_fused_batches() == 3
+    m3 = torch.zeros_like(m1)
+    plan3.messenger(m3, lams)
+    m4 = torch.zeros_like(m1)
+    plan3.messenger_graph(m4, lams)
+    torch.cuda.synchronize()
+    assert plan3.fault_flags() == 0
+    assert rel(m3.cpu().numpy(), m1.cpu().numpy()) <= 1e-9
+    assert rel(m4.cpu().numpy(), m1.cpu().numpy()) <= 1e-9
