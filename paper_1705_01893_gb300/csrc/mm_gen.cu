@@ -450,11 +450,14 @@ __global__ void __launch_bounds__(512) k_gen_col_inverse(GenParams q) {
 // A job is either one row that pairs with itself (k1 = 0, or k1 = M1/2 for even M1) or
 // `count` consecutive pairs of rows (k1, M1 - k1), k1 = first .. first + count - 1; tile
 // sequence 2j holds row first + j and sequence 2j + 1 its partner.
+// MODE >= 0: the row mode folded in at compile time (the messenger step and its map-sized
+// form); -1: read from q.a.mode (set-up, PCG, chi^2, composite and the other modes).
+template <int MODE>
 __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   extern __shared__ float2 gsm[];
   __shared__ double red[32];
   const int T = blockDim.x;
-  const int mode = q.a.mode;
+  const int mode = MODE >= 0 ? MODE : q.a.mode;
   const bool fwd = mode != kRowPcgRhs && mode != kRowMd;
   const bool mess = mode == kRowMessenger || mode == kRowMessengerF || mode == kRowMd;
   const bool resid = mode == kRowResidual;
@@ -741,7 +744,10 @@ cudaError_t launch_gen_row(const mm_plan_s* p, const Batch& b, const RowArgs& a,
   }
   q.tile = emax + (emax >> 4) + 1;
   const size_t smem = 2 * sizeof(float2) * (size_t)q.tile;
-  return gen_launch(k_gen_row, p->gen_tune.row_threads, smem, q.n_items, q, st);
+  auto k = a.mode == kRowMessenger    ? k_gen_row<kRowMessenger>
+           : a.mode == kRowMessengerF ? k_gen_row<kRowMessengerF>
+                                      : k_gen_row<-1>;
+  return gen_launch(k, p->gen_tune.row_threads, smem, q.n_items, q, st);
 }
 
 }  // namespace mm
