@@ -116,6 +116,14 @@ mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int
  * No counterpart in the paper: a check of this library's own scheduling. */
 mm_status mm_plan_fault_flags(mm_plan p, int* flags, void* stream);
 
+/* Check of the bounded wait that the fused iteration kernel's work items use: one GPU
+ * thread waits for a device flag to reach 1, at most n_polls polls about 256 ns apart
+ * (1 <= n_polls <= 2^22, the kernel's own limit).  flag_set != 0 sets the flag first (the
+ * wait returns at once); flag_set == 0 leaves it unset, so the wait runs out.  *expired
+ * receives 1 when it ran out.  Synchronises `stream`; the GPU context stays usable either
+ * way.  No counterpart in the paper: a check of this library's failure handling. */
+mm_status mm_check_bounded_wait(int n_polls, int flag_set, int* expired, void* stream);
+
 /* How many of the plan's batches mm_messenger_iterate and mm_messenger_graph run as one
  * fused launch (column, row and inverse column passes together; chunks of 2^22 samples,
  * single pointing); the others run the three kernels one after the other. */

@@ -53,6 +53,7 @@ SIGNATURES = {
     "mm_messenger_adjoint_ckpt": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp,
                                                  ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "mm_plan_fault_flags": (ctypes.c_int, [_vp, _ip, _vp]),
+    "mm_check_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip, _vp]),
     "mm_plan_fused_batches": (ctypes.c_int, [_vp, _ip]),
     "mm_pcg_state_bytes": (ctypes.c_int, [_vp, _szp]),
     "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
@@ -441,6 +442,15 @@ def binned_map_noalloc(pix, cos2psi, sin2psi, tod, n_pix: int, ncomp: int, map_o
     _check("mm_binned_map_noalloc", load().mm_binned_map_noalloc(
         _ptr(pix), _ptr(cos2psi), _ptr(sin2psi), wd, _ptr(tod), int(pix.numel()), int(n_pix),
         int(ncomp), float(rcond_min), _ptr(map_out), _stream(stream)))
+
+
+def check_bounded_wait(n_polls: int, flag_set: bool, stream=None) -> bool:
+    """Run the fused kernel's bounded wait on a device flag (set beforehand or never);
+    returns True when the wait ran out."""
+    e = ctypes.c_int()
+    _check("mm_check_bounded_wait", load().mm_check_bounded_wait(int(n_polls), int(bool(flag_set)),
+                                                                 ctypes.byref(e), _stream(stream)))
+    return bool(e.value)
 
 
 def cooling_schedule(lam_max: float, levels: int, iters: int) -> np.ndarray:

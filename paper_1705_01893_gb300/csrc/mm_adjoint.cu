@@ -622,6 +622,7 @@ extern "C" mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int 
                                           const double* map_in, const double* grad_map_out,
                                           float* grad_tod, double* grad_theta, int ckpt_every,
                                           void* work, size_t work_bytes, void* stream) {
+  MmRange nvtx_range_("mm_messenger_adjoint");
   const char* fn = "mm_messenger_adjoint";
   mm_status st = adjoint_check(p, lambdas, n_iter, ckpt_every, fn);
   if (st != MM_OK) return st;
@@ -651,6 +652,7 @@ extern "C" mm_status mm_messenger_adjoint(mm_plan p, const double* lambdas, int 
 extern "C" mm_status mm_messenger_forward_ckpt(mm_plan p, const double* lambdas, int n_iter,
                                                double* map_inout, int ckpt_every, double* ckpt,
                                                void* stream) {
+  MmRange nvtx_range_("mm_messenger_forward_ckpt");
   const char* fn = "mm_messenger_forward_ckpt";
   mm_status st = adjoint_check(p, lambdas, n_iter, ckpt_every, fn);
   if (st != MM_OK) return st;
@@ -667,6 +669,7 @@ extern "C" mm_status mm_messenger_adjoint_ckpt(mm_plan p, const double* lambdas,
                                                float* grad_tod, double* grad_theta,
                                                int ckpt_every, void* work, size_t work_bytes,
                                                void* stream) {
+  MmRange nvtx_range_("mm_messenger_adjoint_ckpt");
   const char* fn = "mm_messenger_adjoint_ckpt";
   mm_status st = adjoint_check(p, lambdas, n_iter, ckpt_every, fn);
   if (st != MM_OK) return st;

@@ -1024,6 +1024,7 @@ extern "C" mm_status mm_plan_pointing(mm_plan* out, int n_chunks, const int64_t*
                                       const void* sin2psi, int weight_dtype, int64_t n_pix,
                                       int ncomp, double rcond_min, void* workspace,
                                       size_t workspace_bytes, void* stream) {
+  MmRange nvtx_range_("mm_plan_pointing");
   return plan_create(out, n_chunks, offsets, pix, cos2psi, sin2psi, weight_dtype, n_pix, ncomp,
                      rcond_min, workspace, workspace_bytes, stream, nullptr);
 }
@@ -1034,6 +1035,7 @@ extern "C" mm_status mm_plan_composite(mm_plan* out, int n_chunks, const int64_t
                                        const void* sin_b, float gain_b, int weight_dtype,
                                        int64_t n_pix, int ncomp, double rcond_min, void* workspace,
                                        size_t workspace_bytes, void* stream) {
+  MmRange nvtx_range_("mm_plan_composite");
   MM_ARG(out != nullptr, "out is NULL");
   *out = nullptr;
   MM_ARG(pix_b != nullptr, "pix_b is NULL");
@@ -1341,6 +1343,7 @@ static mm_status check_launch(const char* what) {
 
 extern "C" mm_status mm_set_noise_psd(mm_plan p, const double* psd_dev, const double* params,
                                       const double* tau, const float* tod, void* stream) {
+  MmRange nvtx_range_("mm_set_noise_psd");
   MM_ARG(p != nullptr, "plan is NULL");
   MM_ARG((psd_dev != nullptr) != (params != nullptr), "give exactly one of psd / params");
   MM_ARG(tod != nullptr, "tod is NULL");
@@ -1465,6 +1468,7 @@ static mm_status load_map(mm_plan p, const double* map, cudaStream_t s) {
 
 extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int precision,
                                           double* map_inout, double* chi2_out, void* stream) {
+  MmRange nvtx_range_("mm_messenger_iterate");
   MM_ARG(p != nullptr, "plan is NULL");
   MM_ARG(n_iter >= 0, "n_iter must be >= 0");
   MM_ARG(n_iter == 0 || lambdas != nullptr, "lambdas is NULL");
@@ -1602,6 +1606,7 @@ extern "C" mm_status mm_messenger_md_bytes(mm_plan p, int n_levels, size_t* byte
 extern "C" mm_status mm_messenger_iterate_md(mm_plan p, const double* lambdas, int n_iter,
                                              double* map_inout, double* chi2_out, void* work,
                                              size_t work_bytes, void* stream) {
+  MmRange nvtx_range_("mm_messenger_iterate_md");
   if (p && p->composite) {
     mm_set_error("mm_messenger_iterate_md: not available for composite-pointing plans");
     return MM_ERR_UNSUPPORTED;
@@ -1891,6 +1896,7 @@ extern "C" mm_status mm_messenger_adaptive(mm_plan p, const double* levels, int 
                                            double rel_tol, int min_per_level, int max_per_level,
                                            int max_iter, double* map_inout, double* chi2_out,
                                            double* lambda_out, int* n_done, void* stream) {
+  MmRange nvtx_range_("mm_messenger_adaptive");
   if (p && p->composite) {
     mm_set_error("mm_messenger_adaptive: not available for composite-pointing plans");
     return MM_ERR_UNSUPPORTED;
@@ -1941,6 +1947,7 @@ extern "C" mm_status mm_messenger_adaptive(mm_plan p, const double* levels, int 
 
 extern "C" mm_status mm_messenger_graph(mm_plan p, const double* lambdas, int n_iter,
                                         double* map_inout, double* chi2_out, void* stream) {
+  MmRange nvtx_range_("mm_messenger_graph");
   if (p && p->composite) {
     mm_set_error("mm_messenger_graph: not available for composite-pointing plans");
     return MM_ERR_UNSUPPORTED;
@@ -1983,6 +1990,7 @@ static mm_status apply_A(mm_plan p, cudaStream_t s) {
 
 extern "C" mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, void* state, int restart,
                                     double* chi2_out, void* stream) {
+  MmRange nvtx_range_("mm_pcg_iterate");
   if (p && p->composite) {
     mm_set_error("mm_pcg_iterate: not available for composite-pointing plans");
     return MM_ERR_UNSUPPORTED;
@@ -2038,6 +2046,7 @@ extern "C" mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, vo
 }
 
 extern "C" mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev, void* stream) {
+  MmRange nvtx_range_("mm_chi2");
   MM_ARG(p != nullptr && map != nullptr && chi2_dev != nullptr, "NULL argument");
   MM_ARG(lambda >= 1.0 && isfinite(lambda), "lambda must be finite and >= 1");
   if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }
@@ -2096,6 +2105,7 @@ __global__ void k_chi2_modes(const ChunkDesc* __restrict__ desc, int n_chunks, i
 
 extern "C" mm_status mm_chi2_modes(mm_plan p, const double* map, double lambda, double* chi2_dev,
                                    double* modes, void* stream) {
+  MmRange nvtx_range_("mm_chi2_modes");
   MM_ARG(p != nullptr && map != nullptr && modes != nullptr, "NULL argument");
   MM_ARG(((uintptr_t)modes & 7) == 0, "modes must be 8-byte aligned");
   MM_ARG(lambda >= 1.0 && isfinite(lambda), "lambda must be finite and >= 1");
@@ -2181,6 +2191,7 @@ static cudaError_t time_min(cudaStream_t s, int reps, F fn, float* best) {
 }
 
 extern "C" mm_status mm_autotune(mm_plan p, void* stream) {
+  MmRange nvtx_range_("mm_autotune");
   MM_ARG(p != nullptr, "plan is NULL");
   if (p->n_gen == 0) return MM_OK;
   if (!p->noise_set) { mm_set_error("mm_set_noise_psd has not run"); return MM_ERR_STATE; }

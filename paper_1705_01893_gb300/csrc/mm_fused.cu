@@ -28,9 +28,11 @@ struct FusedParams {
 
 enum { kItemA = 0, kItemB = 1, kItemC = 2 };
 
-// Poll *c (acquire, GPU scope) until it reaches target; about a second at most.
-__device__ __forceinline__ void wait_count(const unsigned* c, unsigned target, int* fault) {
-  for (int n = 0; n < (1 << 22); ++n) {
+// Poll *c (acquire, GPU scope) until it reaches target, at most n_polls times (about 256 ns
+// apart); on expiry set *fault and return.
+__device__ __forceinline__ void wait_count(const unsigned* c, unsigned target, int* fault,
+                                           int n_polls = 1 << 22) {   // about a second
+  for (int n = 0; n < n_polls; ++n) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
     if (v >= target) return;
@@ -208,4 +210,42 @@ cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, c
   return cudaGetLastError();
 }
 
+// Check of the bounded wait above: one thread waits for a flag to reach 1; the flag is set
+// beforehand (the wait returns at once) or never (the wait runs out and reports it).
+static __device__ unsigned g_wait_flag;
+static __device__ int g_wait_fault;
+
+__global__ void k_wait_check(int n_polls) {
+  if (threadIdx.x == 0) wait_count(&g_wait_flag, 1u, &g_wait_fault, n_polls);
+}
+
 }  // namespace mm
+
+extern "C" mm_status mm_check_bounded_wait(int n_polls, int flag_set, int* expired, void* stream) {
+  using namespace mm;
+  if (!expired || n_polls < 1 || n_polls > (1 << 22)) {
+    mm_set_error("mm_check_bounded_wait: expired is NULL or n_polls outside [1, 2^22]");
+    return MM_ERR_ARG;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  void* flag = nullptr;
+  void* fault = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&flag, g_wait_flag);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(&fault, g_wait_fault);
+  const unsigned f = flag_set ? 1u : 0u;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flag, &f, sizeof(f), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fault, 0, sizeof(int), s);
+  if (e == cudaSuccess) {
+    k_wait_check<<<1, 32, 0, s>>>(n_polls);
+    e = cudaGetLastError();
+  }
+  int r = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&r, fault, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    mm_set_error("mm_check_bounded_wait: %s", cudaGetErrorString(e));
+    return MM_ERR_CUDA;
+  }
+  *expired = r;
+  return MM_OK;
+}

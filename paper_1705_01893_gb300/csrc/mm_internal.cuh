@@ -579,3 +579,13 @@ __host__ __device__ constexpr int col_threads(int M1) {
 
 // error reporting shared by the ABI translation units
 void mm_set_error(const char* fmt, ...);
+
+// NVTX range around an entry point (header-only NVTX 3: a no-op unless a profiler that
+// records ranges is attached).
+#include <nvtx3/nvToolsExt.h>
+struct MmRange {
+  explicit MmRange(const char* name) { nvtxRangePushA(name); }
+  ~MmRange() { nvtxRangePop(); }
+  MmRange(const MmRange&) = delete;
+  MmRange& operator=(const MmRange&) = delete;
+};

@@ -273,6 +273,7 @@ extern "C" mm_status mm_plain_work_bytes(mm_plan p, size_t* bytes) {
 extern "C" mm_status mm_messenger_plain_fp64(mm_plan p, const float* tod, const double* lambdas,
                                              int n_iter, double* map_inout, double* chi2_out,
                                              void* work, size_t work_bytes, void* stream) {
+  MmRange nvtx_range_("mm_messenger_plain_fp64");
   size_t need = 0;
   mm_status st = mm_plain_work_bytes(p, &need);
   if (st != MM_OK) return st;

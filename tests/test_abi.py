@@ -87,3 +87,10 @@ def test_workspace_too_small_is_nomem(lib):
                              ctypes.c_void_p(0x100000), 16, None)
     assert r == binding.MM_ERR_NOMEM
     assert b"workspace too small" in lib.mm_last_error()
+
+
+def test_bounded_wait_check_rejects_bad_limits(lib):
+    e = ctypes.c_int()
+    assert lib.mm_check_bounded_wait(0, 0, ctypes.byref(e), None) == binding.MM_ERR_ARG
+    assert lib.mm_check_bounded_wait((1 << 22) + 1, 0, ctypes.byref(e), None) == binding.MM_ERR_ARG
+    assert lib.mm_check_bounded_wait(10, 0, None, None) == binding.MM_ERR_ARG

@@ -188,3 +188,13 @@ def test_fused_several_batches(monkeypatch):
     assert plan3.fault_flags() == 0
     assert rel(m3.cpu().numpy(), m1.cpu().numpy()) <= 1e-9
     assert rel(m4.cpu().numpy(), m1.cpu().numpy()) <= 1e-9
+
+
+def test_bounded_wait_runs_out_and_reports():
+    """The fused kernel's bounded wait on a flag that nothing sets: it ends after its poll
+    limit and reports expiry, the context stays usable; with the flag set it returns at
+    once without a report."""
+    assert binding.check_bounded_wait(2000, flag_set=False) is True
+    assert binding.check_bounded_wait(2000, flag_set=True) is False
+    x = torch.ones(1024, device=DEV)
+    assert float((x * 2).sum()) == 2048.0
