@@ -116,6 +116,15 @@ mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int
  * No counterpart in the paper: a check of this library's own scheduling. */
 mm_status mm_plan_fault_flags(mm_plan p, int* flags, void* stream);
 
+/* The work list of the fused iteration kernel for a batch of `count` chunks whose complex
+ * length is m1 x m2 (m1 a power of two, m2 a multiple of 16): per item (kind, chunk, index)
+ * with kind 0 = column tile, 1 = row-pair job, 2 = inverse column tile, written to out
+ * (int [3 * capacity]; NULL to query the count).  Host only, no GPU.  The list puts every
+ * item's prerequisites (all column tiles of its chunk for a row job, all row jobs for an
+ * inverse tile) before it, which keeps the kernel free of deadlock; exposed so that this
+ * can be checked.  *n_items receives the number of items. */
+mm_status mm_fused_item_list(int m1, int m2, int count, int* out, int capacity, int* n_items);
+
 /* Check of the bounded wait that the fused iteration kernel's work items use: one GPU
  * thread waits for a device flag to reach 1, at most n_polls polls about 256 ns apart
  * (1 <= n_polls <= 2^22, the kernel's own limit).  flag_set != 0 sets the flag first (the

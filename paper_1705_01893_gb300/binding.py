@@ -54,6 +54,8 @@ SIGNATURES = {
                                                  ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "mm_plan_fault_flags": (ctypes.c_int, [_vp, _ip, _vp]),
     "mm_check_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip, _vp]),
+    "mm_fused_item_list": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip,
+                                          ctypes.c_int, _ip]),
     "mm_plan_fused_batches": (ctypes.c_int, [_vp, _ip]),
     "mm_pcg_state_bytes": (ctypes.c_int, [_vp, _szp]),
     "mm_pcg_iterate": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp]),
@@ -442,6 +444,17 @@ def binned_map_noalloc(pix, cos2psi, sin2psi, tod, n_pix: int, ncomp: int, map_o
     _check("mm_binned_map_noalloc", load().mm_binned_map_noalloc(
         _ptr(pix), _ptr(cos2psi), _ptr(sin2psi), wd, _ptr(tod), int(pix.numel()), int(n_pix),
         int(ncomp), float(rcond_min), _ptr(map_out), _stream(stream)))
+
+
+def fused_item_list(m1: int, m2: int, count: int) -> np.ndarray:
+    """The fused kernel's work list for `count` chunks of complex length m1 x m2, as an int
+    array [n_items, 3] of (kind, chunk, index); host only."""
+    n = ctypes.c_int()
+    _check("mm_fused_item_list", load().mm_fused_item_list(m1, m2, count, None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, 3), dtype=np.int32)
+    _check("mm_fused_item_list", load().mm_fused_item_list(
+        m1, m2, count, out.ctypes.data_as(_ip), n.value, ctypes.byref(n)))
+    return out
 
 
 def check_bounded_wait(n_polls: int, flag_set: bool, stream=None) -> bool:

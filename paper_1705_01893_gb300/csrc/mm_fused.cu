@@ -11,6 +11,8 @@
 // only ever waits for items that CTAs already running hold: no deadlock whatever number of
 // CTAs is resident.  Waits are bounded (about a second): on expiry the kernel sets the plan's
 // fault flag and carries on (the result is then wrong, and mm_plan_fault_flags reports it).
+#include <vector>
+
 #include "mm_colcommon.cuh"
 #include "mm_rowcommon.cuh"
 
@@ -220,6 +222,32 @@ __global__ void k_wait_check(int n_polls) {
 }
 
 }  // namespace mm
+
+extern "C" mm_status mm_fused_item_list(int m1, int m2, int count, int* out, int capacity,
+                                        int* n_items) {
+  using namespace mm;
+  if (!n_items || count < 1 || count > 0xffff || m1 < 2 || m2 < kColCB || (m2 % kColCB) != 0 ||
+      (m1 & (m1 - 1)) != 0) {
+    mm_set_error("mm_fused_item_list: bad argument");
+    return MM_ERR_ARG;
+  }
+  const int per = 2 * (m2 / kColCB) + m1 / 2 + 1;
+  const int64_t total = (int64_t)per * count;
+  *n_items = (int)total;
+  if (!out) return MM_OK;
+  if (capacity < total) {
+    mm_set_error("mm_fused_item_list: capacity %d < %lld items", capacity, (long long)total);
+    return MM_ERR_ARG;
+  }
+  std::vector<int2> v((size_t)total);
+  const int n = fused_build_items(m1, m2, count, v.data());
+  for (int i = 0; i < n; ++i) {
+    out[3 * i] = v[i].x >> 16;
+    out[3 * i + 1] = v[i].x & 0xffff;
+    out[3 * i + 2] = v[i].y;
+  }
+  return n == total ? MM_OK : MM_ERR_ARG;
+}
 
 extern "C" mm_status mm_check_bounded_wait(int n_polls, int flag_set, int* expired, void* stream) {
   using namespace mm;

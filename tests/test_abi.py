@@ -94,3 +94,34 @@ def test_bounded_wait_check_rejects_bad_limits(lib):
     assert lib.mm_check_bounded_wait(0, 0, ctypes.byref(e), None) == binding.MM_ERR_ARG
     assert lib.mm_check_bounded_wait((1 << 22) + 1, 0, ctypes.byref(e), None) == binding.MM_ERR_ARG
     assert lib.mm_check_bounded_wait(10, 0, None, None) == binding.MM_ERR_ARG
+
+
+@pytest.mark.parametrize("count", list(range(1, 13)) + [31])
+def test_fused_item_list_order(lib, count):
+    """The fused kernel's work list (host code, no GPU): each item exactly once, and every
+    row job after all column tiles of its chunk, every inverse tile after all row jobs of
+    its chunk -- the order that keeps the kernel free of deadlock."""
+    items = binding.fused_item_list(512, 4096, count)
+    nA, nB = 4096 // 16, 512 // 2 + 1
+    assert items.shape == (count * (2 * nA + nB), 3)
+    assert len({tuple(r) for r in items}) == len(items)
+    doneA = np.zeros(count, dtype=int)
+    doneB = np.zeros(count, dtype=int)
+    for kind, c, i in items:
+        assert 0 <= c < count
+        if kind == 0:
+            assert 0 <= i < nA
+            doneA[c] += 1
+        elif kind == 1:
+            assert 0 <= i < nB and doneA[c] == nA
+            doneB[c] += 1
+        else:
+            assert kind == 2 and 0 <= i < nA and doneB[c] == nB
+    assert (doneA == nA).all() and (doneB == nB).all()
+
+
+def test_fused_item_list_rejects_bad_shapes(lib):
+    n = ctypes.c_int()
+    assert lib.mm_fused_item_list(512, 4096, 0, None, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
+    assert lib.mm_fused_item_list(500, 4096, 1, None, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
+    assert lib.mm_fused_item_list(512, 4008, 1, None, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
