@@ -569,6 +569,28 @@ def run_gpu(args):
         md_cmp["map_sized"]["ms_m_d_per_lambda"] = t[("map_sized", 10)] - \
             10 * md_cmp["map_sized"]["ms_per_iter"]
 
+    # diagnostics beside the iteration: chi^2 of a map (mm_chi2, total) and chi^2 per Fourier
+    # mode (mm_chi2_modes, Sec. 3.1's diagnostic), each a forward pass of its own
+    diag = None
+    if not args.no_plain and name == WORKLOAD:
+        mm = m.clone()
+        reps = 10
+        plan.chi2(mm)
+        plan.chi2_modes(mm)
+        fence(dev)
+        diag = {}
+        for label, fn in (("chi2_total_ms", lambda: plan.chi2(mm)),
+                          ("chi2_per_mode_ms", lambda: plan.chi2_modes(mm))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            diag[label] = e0.elapsed_time(e1) / reps
+        diag["timing"] = ("events around 10 calls each; the chi^2 that the iteration reports "
+                          "with chi2_out comes from its own row jobs at no extra pass")
+
     # end to end through the public call, host buffers: map in (pinned), one iteration,
     # map and chi^2 out, synchronised every step
     m_host = torch.zeros(npix, nc, dtype=torch.float64).pin_memory()
@@ -642,6 +664,7 @@ def run_gpu(args):
         "fp64_plain_ms_per_step": plain_ms,
         "fft_vs_cufft": fft_cmp,
         "map_sized_form": md_cmp,
+        "chi2_diagnostics": diag,
         "speedup_vs_fp64_plain": None if plain_ms is None else plain_ms / ms_step,
         "stage_ms_per_launch": {k: round(v, 5) for k, v in sm["avg"].items()},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": sm["achieved"], "peak": hbm,

@@ -2086,8 +2086,9 @@ __global__ void k_chi2_modes(const ChunkDesc* __restrict__ desc, int n_chunks, i
       const float2 D = dtab[slot];
       dre = D.x; dim = D.y; nb = nbar[slot];
     }
-    const double er = dre - X.x, ei = dim - X.y;
-    const double v = (er * er + ei * ei) / ((nb + lambda * d.tau) * d.n);
+    // FP32 per bin (the narrow FP64 pipe made this kernel the cost of the call), FP64 sums
+    const float er = (float)dre - X.x, ei = (float)dim - X.y;
+    const double v = (double)__fdividef(er * er + ei * ei, (float)(nb + lambda * d.tau)) / d.n;
     reinterpret_cast<double*>(io)[i] = v;
     w += (k == 0 || 2 * k == d.n) ? v : 2.0 * v;
   }
@@ -2114,7 +2115,15 @@ extern "C" mm_status mm_chi2_modes(mm_plan p, const double* map, double lambda, 
   if (chi2_dev) MM_CUDA(cudaMemsetAsync(chi2_dev, 0, sizeof(double), s));
   mm_status st = load_map(p, map, s);
   if (st != MM_OK) return st;
-  // the spectrum of P m, natural order, into the caller's buffer (8 bytes per bin either way)
+  if (p->n_gen == 0) {
+    // compile-time lengths: the row jobs write each mode's chi^2 to its natural-order slot
+    // and add the total, in one forward pass
+    RowArgs a{kRowChi2Modes, lambda, chi2_dev, reinterpret_cast<float2*>(modes)};
+    FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s)));
+    return MM_OK;
+  }
+  // general lengths: the spectrum of P m, natural order, into the caller's buffer (8 bytes
+  // per bin either way), then one thread per bin
   RowArgs a{kRowNatural, 1.0, nullptr, reinterpret_cast<float2*>(modes)};
   FOR_BATCHES(L_(launch_col_forward(p, B, kSrcGather, nullptr, s)); L_(launch_row(p, B, a, s)));
   const ChunkDesc& last = p->h_desc[p->n_chunks - 1];

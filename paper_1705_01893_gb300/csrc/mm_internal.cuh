@@ -527,7 +527,10 @@ enum RowMode {
   kRowResidual = 8,   // forward, Y = (d~ - X) / (n (Nbar / lambda + tau)), chi^2, inverse
   // the messenger step that also keeps its forward spectrum X = (P m)~ in row layout at
   // RowArgs::natural + spec (the adjoint's recomputation; run-time instance only)
-  kRowMessengerKeep = 9
+  kRowMessengerKeep = 9,
+  // forward, chi^2(m, lambda) per Fourier mode, |d~_k - X_k|^2 / (n (Nbar_k + lambda tau)),
+  // as float64 at ((double*)RowArgs::natural)[nat + k] in natural order, and the total
+  kRowChi2Modes = 10
 };
 
 struct RowArgs {

@@ -93,7 +93,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
     lt = lam_inf ? 0.f : (float)(lambda * d.tau);
   }
   // N' = Nbar + cn for chi^2: tau (Eq. 3) or lambda tau (chi^2(m, lambda))
-  const float cn = mode == kRowChi2 ? (float)(lambda * d.tau) : tau;
+  const float cn = (mode == kRowChi2 || mode == kRowChi2Modes) ? (float)(lambda * d.tau) : tau;
   // output scale: irfft normalisation 1/n, and T^-1 = 1/tau for the messenger map step
   const float sc = mess ? inv_n / tau : inv_n;
   const float2* dt = q.dtab + d.spec;
@@ -112,6 +112,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   };
   const bool want_x2 = chi2 != nullptr &&
                        (mode == kRowMessenger || mode == kRowMessengerF || mode == kRowChi2 ||
+                        mode == kRowChi2Modes ||
                         mode == kRowPcgRhs);
   const bool spec_out = mode == kRowSpectrum || mode == kRowNatural;
   const bool load_d = !spec_out && mode != kRowPcgApply && mode != kRowMessengerF;
@@ -168,7 +169,14 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
         if (mode == kRowMessengerKeep) q.a.natural[d.spec] = make_float2(X0, XM);
         const float2 D = load_d ? dt[0] : make_float2(0.f, 0.f);
         const float n0 = nb[0], nM = __ldg(q.nyq + c);
-        if (want_x2) {
+        if (mode == kRowChi2Modes) {
+          const float e0 = D.x - X0, eM = D.y - XM;
+          const float v0 = __fdividef(e0 * e0, n0 + cn), vM = __fdividef(eM * eM, nM + cn);
+          x2 += v0 + vM;
+          double* o = reinterpret_cast<double*>(q.a.natural) + d.nat;
+          o[0] = (double)(v0 * inv_n);
+          o[M] = (double)(vM * inv_n);
+        } else if (want_x2) {
           const float e0 = D.x - X0, eM = D.y - XM;
           x2 += __fdividef(e0 * e0, n0 + cn) + __fdividef(eM * eM, nM + cn);
         }
@@ -202,7 +210,17 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
         q.a.natural[d.spec + sk] = Xk;
         if (!same) q.a.natural[d.spec + sp] = Xp;
       }
-      if (want_x2) {
+      if (mode == kRowChi2Modes) {
+        // each mode's term at its natural-order slot: k = rA + M1 p, partner M - k
+        const float2 ek = csub(Dk[u], Xk), ep = csub(Dp[u], Xp);
+        const float tk = __fdividef(ek.x * ek.x + ek.y * ek.y, nk[u] + cn);
+        const float tp = same ? 0.f : __fdividef(ep.x * ep.x + ep.y * ep.y, np[u] + cn);
+        x2 += 2.f * (tk + tp);
+        double* o = reinterpret_cast<double*>(q.a.natural) + d.nat;
+        const int k = rA + M1 * p;
+        o[k] = (double)(tk * inv_n);
+        if (!same) o[M - k] = (double)(tp * inv_n);
+      } else if (want_x2) {
         const float2 ek = csub(Dk[u], Xk), ep = csub(Dp[u], Xp);
         float t = __fdividef(ek.x * ek.x + ek.y * ek.y, nk[u] + cn);
         if (!same) t += __fdividef(ep.x * ep.x + ep.y * ep.y, np[u] + cn);
