@@ -105,7 +105,9 @@ mm_status mm_lambda_max(mm_plan p, double* out, void* stream);
  * chi2_out:  device float64 [n_iter] or NULL; chi2_out[i] = chi^2(m_i) (Eq. 3) of the map
  *            entering iteration i, summed over all Fourier modes (Sec. 3.1).
  * precision: MM_FP32_MIXED (FP32 timestreams and FFTs, FP64 pixel accumulation,
- *            3x3 solves and chi^2 sums). */
+ *            3x3 solves and chi^2 sums); other values return MM_ERR_UNSUPPORTED.  The
+ *            all-FP64 step is its own entry point, mm_messenger_plain_fp64, because it
+ *            needs the data d itself and a work buffer that this call does not take. */
 mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int precision,
                                double* map_inout, double* chi2_out, void* stream);
 
