@@ -504,6 +504,8 @@ def run_gpu(args):
     lam_g = np.array([float(sched[(args.warmup + k) % len(sched)]) for k in range(args.steps)])
     ms_local = graph_ms(plan, m.clone(), lam_g, dev, stream)
     clocks = sampler.stop()
+    # bounded waits of the fused launch that ran out during the runs above (0: none)
+    fault_flags = plan.fault_flags()
     value, ms_step = job_rate(ms_local, world, dev)
 
     # the plain FP64 single-launch-per-iteration step on the same GPU (comparison bar; one
@@ -660,6 +662,7 @@ def run_gpu(args):
                   "ifft_bin: the three separate kernels; fused_passes: the one launch of all "
                   "three that the graph runs)",
         "fused_batches": n_fused,
+        "fault_flags": fault_flags,
         "stage_loop_ms_per_step": stage_ms_step,
         "fp64_plain_ms_per_step": plain_ms,
         "fft_vs_cufft": fft_cmp,
