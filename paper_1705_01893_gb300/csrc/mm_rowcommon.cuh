@@ -119,7 +119,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
 
   // Pairs (k, M - k): p in row rA with partner qi in row rB (or in row rA itself when the
   // row pairs with itself).  PB pairs per thread have their d~ / Nbar loads in flight at once.
-  constexpr int PB = 4;
+  constexpr int PB = M2 >= 8192 ? 2 : 4;   // fewer in flight where the 1024-thread jobs spill
   for (int p0 = threadIdx.x; p0 < M2; p0 += PB * T) {
     float2 Dk[PB], Dp[PB];
     float nk[PB], np[PB];
