@@ -182,12 +182,15 @@ def test_heterogeneous_tau_same_solution():
 
 
 def test_unbiased_over_noise_seeds():
-    """<m_i> = m_true for every iterate (Sec. 2.1): mean over seeds within 5 sigma."""
+    """<m_i> = m_true for every iterate (Sec. 2.1): the mean over 256 noise draws is within
+    5 standard errors of m_true on every kept map component.  5 rather than 4: the maximum
+    is taken over all components (768 here), and at 4 a correct solver would still fail
+    about one draw set in twenty; 256 draws resolve a bias of sigma/16 per component."""
     base = tiny(seed=100)
     v = O.problem_from_synth(base).valid
     mt = base["m_true"] * v[:, None]        # no signal on cut pixels (their rows are zero)
     maps = []
-    for k in range(48):
+    for k in range(256):
         s = tiny(seed=100 + k)
         s["tod"] = (exact_signal(base, mt) + (s["tod"] - exact_signal(s))).astype(np.float32)
         prob = O.problem_from_synth(s)
