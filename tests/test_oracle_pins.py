@@ -203,12 +203,14 @@ def test_unbiased_over_noise_seeds():
     assert np.max(z) < 5.0
 
 
-def test_rfft_convention_round_trip():
-    """The oracle's spectrum convention: Parseval with multiplicity weights, and round trip."""
-    x = np.random.default_rng(0).standard_normal(1000)
+@pytest.mark.parametrize("n", [1000, 999, 1875, 2])
+def test_rfft_convention_round_trip(n):
+    """The oracle's spectrum convention: Parseval with multiplicity weights (no Nyquist bin
+    for odd n), and round trip."""
+    x = np.random.default_rng(n).standard_normal(n)
     X = np.fft.rfft(x)
-    assert abs(np.sum(O.rfft_weights(1000) * np.abs(X) ** 2) / 1000 - x @ x) < 1e-9 * (x @ x)
-    assert np.allclose(np.fft.irfft(X, 1000), x)
+    assert abs(np.sum(O.rfft_weights(n) * np.abs(X) ** 2) / n - x @ x) < 1e-9 * (x @ x)
+    assert np.allclose(np.fft.irfft(X, n), x)
 
 
 def test_schedule_shape():
