@@ -93,3 +93,67 @@ def test_fixed_lambda_reaches_the_lambda_solution():
     # and not the lambda = 1 solution
     c1 = C.chi2(prob, C.dense_solution(prob, 1.0), lam)
     assert (c1 - c_ref) / c_ref > 1e-4
+
+
+# --------------------------------------------------------------- planted mistakes
+def _step_variant(sign=1.0, lam_times=False):
+    """C.step retyped with one slip: the residual's sign, or lambda multiplying Nbar."""
+    def step(prob, m, lam):
+        acc = np.zeros((prob.npix, prob.ncomp))
+        x2 = C.chi2(prob, m)
+        for c, (a, b) in enumerate(prob.chunks()):
+            n = b - a
+            r = np.fft.rfft(sign * (prob.tod[a:b] - prob.P(m, a, b)))
+            nbar = prob.psd[c] - prob.tau[c]
+            if np.isinf(lam):
+                den = prob.tau[c]
+            else:
+                den = (nbar * lam if lam_times else nbar / lam) + prob.tau[c]
+            acc += prob.PT(np.fft.irfft(r / den, n), a, b)
+        return m + np.einsum("pij,pj->pi", prob.W, acc), x2
+    return step
+
+
+PINS = [test_no_second_component_is_the_single_beam_step,
+        test_gls_solution_is_a_fixed_point_and_noiseless_sky_too,
+        test_fixed_lambda_reaches_the_lambda_solution,
+        test_iterations_reach_the_gls_chi2]
+
+
+def test_planted_mistakes_break_a_pin(monkeypatch):
+    """Each plausible slip in the composite oracle (the T split, the residual's sign, lambda
+    on the wrong side of Nbar, the second beam missing from P^T) fails at least one pin."""
+    orig_plan = C.CompositeProblem._plan
+
+    def plan_full_t(self):             # T_A = T_B = tau instead of tau / 2
+        orig_plan(self)
+        self.D = 0.5 * self.D
+        self.W = np.zeros_like(self.D)
+        self.W[self.valid] = np.linalg.inv(self.D[self.valid])
+
+    def pt_first_only(self, t, a, b):  # P_A^T t only
+        out = np.zeros((self.npix, self.ncomp))
+        pix, w = self.comps[0]
+        p = pix[a:b]
+        good = (p >= 0) & self.valid[np.where(p >= 0, p, 0)]
+        np.add.at(out, p[good], w[a:b][good] * t[good][:, None])
+        return out
+
+    slips = {
+        "T split": lambda mp: mp.setattr(C.CompositeProblem, "_plan", plan_full_t),
+        "sign": lambda mp: mp.setattr(C, "step", _step_variant(sign=-1.0)),
+        "lambda": lambda mp: mp.setattr(C, "step", _step_variant(lam_times=True)),
+        "second beam": lambda mp: mp.setattr(C.CompositeProblem, "PT", pt_first_only),
+    }
+    for name, plant in slips.items():
+        with monkeypatch.context() as mp:
+            plant(mp)
+            caught = False
+            for pin in PINS:
+                try:
+                    with np.errstate(all="ignore"):
+                        pin()
+                except (AssertionError, np.linalg.LinAlgError):
+                    caught = True
+                    break
+            assert caught, f"no pin caught the planted mistake: {name}"
