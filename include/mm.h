@@ -54,7 +54,7 @@ enum {
   MM_ERR_ARG = -1,          /* bad argument (null pointer, size, range)            */
   MM_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed         */
   MM_ERR_NOMEM = -3,        /* workspace (or state) smaller than required          */
-  MM_ERR_TIMEOUT = -4,      /* reserved: a bounded device wait gave up             */
+  MM_ERR_TIMEOUT = -4,      /* a bounded device wait gave up (plain FP64 barrier)  */
   MM_ERR_STATE = -5,        /* call out of order (e.g. iterate before set_noise)   */
   MM_ERR_SINGULAR = -6,     /* every pixel was cut                                 */
   MM_ERR_UNSUPPORTED = -7   /* valid input this version does not handle            */
