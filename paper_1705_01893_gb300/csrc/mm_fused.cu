@@ -118,12 +118,10 @@ __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
         scatter4<NC>(q.c, tbase + e, *reinterpret_cast<const float4*>(smf + e), e4 & 7);
       }
     }
-    // release the intermediate rows written by an A tile or a B job before its count: the
-    // barrier orders every thread's stores before thread 0's fence (fences are cumulative),
-    // and the fence orders them before the count
+    // release the intermediate rows written by an A tile or a B job before its count
+    if (kind != kItemC) __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-      if (kind != kItemC) __threadfence();
       if (kind == kItemA) atomicAdd(doneA + ci, 1u);
       if (kind == kItemB) atomicAdd(doneB + ci, 1u);
       s_it = nxt;
