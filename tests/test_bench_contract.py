@@ -27,3 +27,24 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_algorithmic_bytes_of_the_headline_workload():
+    """The byte model behind `roofline` and `iteration_hbm` on the 512^2 IQU, 8 x 2^22 FP32
+    workload: A n(4+w) + 4n + 16 n_pix, B 14n, C 4n + n(4+w) + 24 n_pix, D 112 B per pixel,
+    the fused launch A + B + C; B_pass and B_strict per iteration (46 B/sample + 152 B/px
+    and 28 B/sample + 104 B/px)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    n, npix = 8 << 22, 512 * 512
+    s = {"offsets": np.arange(9, dtype=np.int64) << 22, "ncomp": 3, "npix": npix,
+         "cos": np.zeros(1, dtype=np.float32)}
+    stages, strict, bpass = bench.bytes_model(s)
+    assert stages["gather_fft"] == n * 12 + 4 * n + 16 * npix          # 541 MB
+    assert stages["filter"] == 14 * n                                 # 470 MB
+    assert stages["ifft_bin"] == 4 * n + 12 * n + 24 * npix           # 543 MB
+    assert stages["map"] == 112 * npix                                # 29 MB
+    assert stages["fused_passes"] == stages["gather_fft"] + stages["filter"] + stages["ifft_bin"]
+    assert bpass == 46 * n + 152 * npix                               # 1.58 GB
+    assert strict == 28 * n + 104 * npix                              # 0.97 GB
