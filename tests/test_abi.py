@@ -125,3 +125,25 @@ def test_fused_item_list_rejects_bad_shapes(lib):
     assert lib.mm_fused_item_list(512, 4096, 0, None, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
     assert lib.mm_fused_item_list(500, 4096, 1, None, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
     assert lib.mm_fused_item_list(512, 4008, 1, None, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
+
+
+def test_product_package_never_imports_the_oracle():
+    """The CUDA path and the oracle share no code: nothing in the package imports oracle/."""
+    pkg = os.path.join(ROOT, "paper_1705_01893_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle\b", text, flags=re.M), f
+    assert "oracle" not in open(os.path.join(ROOT, "include", "mm.h")).read().lower()
+
+
+def test_missing_library_raises_instead_of_falling_back(tmp_path):
+    """No CPU fallback: loading a library that is not there is an error."""
+    saved = binding._lib
+    binding._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            binding.load(str(tmp_path / "libmm.so"))
+    finally:
+        binding._lib = saved
