@@ -18,7 +18,7 @@ Everything is float64 NumPy, written for legibility, following the paper's order
 * the brute-force dense GLS solve (Eq. 2) used as the convergence target (Sec. 3.2 uses
   the same device on a 50x50 map).
 
-Readings where the paper is silent (each also listed in the design notes):
+Readings where the paper is silent:
 * noise is exactly circulant per chunk, independent between chunks; N_k is given on the
   rfft bins k = 0..n//2 with F unnormalised and F^-1 carrying 1/n;
 * the model PSD is N(f) = sigma^2 (1 + (fknee/f)^alpha), DC bin floored to bin 1;
@@ -28,8 +28,9 @@ Readings where the paper is silent (each also listed in the design notes):
   (eigmin/eigmax) of its 3x3 block of P^T T^-1 P is >= rcond_min.  Samples on cut pixels
   keep their data but get zero pointing rows;
 * the "diagonal preconditioner" of the comparison PCG is the 3x3 pixel-block Jacobi
-  matrix sum_c c0_c P_c^T P_c, c0_c = (1/n_c) sum_k 1/N_c(f_k), the diagonal of the
-  circulant N_c^-1 (exactly diag(A) for T-only maps);
+  matrix sum_c c0_c P_c^T P_c, c0_c = (1/n_c) sum_k 1/N_c(f_k) over all n_c frequencies,
+  the diagonal of the circulant N_c^-1: the pixel blocks of P^T diag(N^-1) P (for white
+  noise exactly the diagonal pixel blocks of A = P^T N^-1 P);
 * cooling schedule: levels lambda_j = lambda_max^((L-1-j)/(L-1)), j = 0..L-1, each run
   for a fixed number of iterations, lambda_max = max_c max_k Nbar_c(f_k)/tau_c, after one
   lambda = inf step.
@@ -297,7 +298,8 @@ def rhs_b(prob):
 
 
 def jacobi_blocks(prob):
-    """Inverse of the pixel-block preconditioner sum_c c0_c P_c^T P_c (cut pixels -> 0)."""
+    """Inverse of the pixel-block preconditioner sum_c c0_c P_c^T P_c (cut pixels -> 0),
+    c0_c = (N_c^-1)_jj = (1/n) sum over all n frequencies of 1/N_c(f_k) (rfft multiplicities)."""
     nc = prob.ncomp
     M = np.zeros((prob.npix, nc, nc))
     for c, (a, b) in enumerate(prob.chunks()):

@@ -91,3 +91,18 @@ def test_adjoint_planted_mistake_is_caught():
             g_next += prob.PT(np.fft.irfft(bv * V, n), a, b) / tau
         g = g_next
     assert abs(fd - (dth[c, j] - w_term)) > 1e-3 * abs(fd)
+
+
+@pytest.mark.parametrize("n", [1024, 999, 8])
+def test_psd_parts_is_the_model_psd(n):
+    """psd_parts (the adjoint's noise model with its derivatives) restates N(f); its N must
+    be the messenger oracle's psd_from_params to rounding, with tau = sigma^2 and
+    Nbar + tau = N, for even and odd lengths (DC floored to bin 1 in both)."""
+    for sigma, fknee, alpha in ((1.0, 0.5, 2.0), (1.7, 3.0, 1.3)):
+        N, nbar, tau, dnbar, dtau = A.psd_parts(n, 200.0, sigma, fknee, alpha)
+        ref = O.psd_from_params(n, 200.0, sigma, fknee, alpha)
+        assert np.allclose(N, ref, rtol=1e-14, atol=0)
+        # Nbar + tau = N (comparing Nbar with N - tau would measure the cancellation)
+        assert tau == sigma * sigma and np.allclose(nbar + tau, ref, rtol=1e-14, atol=0)
+        assert np.all(nbar > 0)
+        assert dnbar.shape == (3, n // 2 + 1) and dtau.shape == (3,)

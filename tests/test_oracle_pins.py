@@ -101,7 +101,65 @@ def pin_pcg(prob):
     assert np.all(np.diff(ch[:20]) <= 1e-9 * ch[0])
 
 
-ALL_PINS = ["fourier_chi2", "white_noise", "noiseless", "gls", "fixed_lambda", "pcg"]
+def explicit_pointing(prob, a, b):
+    """Pointing rows of samples a..b as a dense [n, npix * ncomp] matrix, written straight
+    from Eq. 1 (weights 1, cos 2psi, sin 2psi; excluded and cut pixels give zero rows)."""
+    nc = prob.ncomp
+    Pm = np.zeros((b - a, prob.npix * nc))
+    for s in range(a, b):
+        p = int(prob.pix[s])
+        if p < 0 or not prob.valid[p]:
+            continue
+        Pm[s - a, p * nc] = 1.0
+        if nc == 3:
+            Pm[s - a, p * nc + 1] = prob.cos[s]
+            Pm[s - a, p * nc + 2] = prob.sin[s]
+    return Pm
+
+
+def explicit_Ninv(psd_rfft, n):
+    """N^-1 of a stationary chunk as F^H diag(1 / N_k) F / n with the n x n DFT matrix F
+    and N_k on all n frequencies (N_k = N_{n-k})."""
+    k = np.arange(n)
+    F = np.exp(-2j * np.pi * np.outer(k, k) / n)
+    full = psd_rfft[np.minimum(k, n - k)]
+    return (F.conj().T @ (F / full[:, None])).real / n
+
+
+def pin_jacobi(prob):
+    """The comparison PCG's preconditioner (the paper's "diagonal preconditioner", read as
+    pixel blocks): jacobi_blocks holds, on every kept pixel, the inverse of that pixel's
+    ncomp x ncomp block of P^T diag(N^-1) P, where diag(N^-1) is the diagonal of the
+    explicit N^-1 = F^H diag(1/N_k) F / n of each chunk; cut and unobserved pixels hold 0.
+    With white noise N^-1 is itself diagonal, and the blocks are then exactly the diagonal
+    pixel blocks of A = P^T N^-1 P (checked on a white-noise copy of the problem)."""
+    nc = prob.ncomp
+    for white in (False, True):
+        if white:
+            psd = [np.full_like(p, 2.5) for p in prob.psd]
+            q = O.Problem(prob.pix, prob.cos, prob.sin, prob.tod, prob.offsets, prob.npix, nc,
+                          psd, prob.tau, prob.rcond_min)
+        else:
+            q = prob
+        Minv = O.jacobi_blocks(q)
+        D = np.zeros((q.npix * nc, q.npix * nc))
+        A = np.zeros_like(D)
+        for c, (a, b) in enumerate(q.chunks()):
+            Pc = explicit_pointing(q, a, b)
+            Ni = explicit_Ninv(q.psd[c], b - a)
+            D += Pc.T @ (np.diag(Ni)[:, None] * Pc)
+            A += Pc.T @ Ni @ Pc
+        for p in range(q.npix):
+            sl = slice(p * nc, (p + 1) * nc)
+            if not q.valid[p]:
+                assert np.all(Minv[p] == 0)
+                continue
+            assert np.allclose(Minv[p] @ D[sl, sl], np.eye(nc), rtol=0, atol=1e-10), p
+            if white:
+                assert np.allclose(Minv[p] @ A[sl, sl], np.eye(nc), rtol=0, atol=1e-10), p
+
+
+ALL_PINS = ["fourier_chi2", "white_noise", "noiseless", "gls", "fixed_lambda", "pcg", "jacobi"]
 
 
 def run_pin(name):
@@ -118,6 +176,8 @@ def run_pin(name):
         pin_fixed_lambda(O.problem_from_synth(s))
     elif name == "pcg":
         pin_pcg(O.problem_from_synth(s))
+    elif name == "jacobi":
+        pin_jacobi(O.problem_from_synth(tiny(width=4, n=256)))
 
 
 @pytest.mark.parametrize("name", ALL_PINS)
@@ -213,6 +273,17 @@ def test_rfft_convention_round_trip(n):
     assert np.allclose(np.fft.irfft(X, n), x)
 
 
+def test_noise_model_values():
+    """The model PSD at hand-evaluated points: n = 8 samples at fs = 8 Hz puts bin k at k Hz;
+    sigma = 2, f_knee = 1 Hz, alpha = 2 gives N(1) = 4 (1 + 1) = 8, N(2) = 4 (1 + 1/4) = 5,
+    N(3) = 4 (1 + 1/9), N(4) = 4 (1 + 1/16) = 4.25, and the DC bin takes bin 1's 8."""
+    N = O.psd_from_params(8, 8.0, 2.0, 1.0, 2.0)
+    assert np.allclose(N, [8.0, 8.0, 5.0, 4.0 + 4.0 / 9.0, 4.25], rtol=1e-15, atol=0)
+    # odd length: bins k = 0..3 of n = 7 at fs = 7 Hz, f_knee = 2 Hz, alpha = 1
+    N = O.psd_from_params(7, 7.0, 1.0, 2.0, 1.0)
+    assert np.allclose(N, [3.0, 3.0, 2.0, 1.0 + 2.0 / 3.0], rtol=1e-15, atol=0)
+
+
 def test_schedule_shape():
     lam = O.cooling_schedule(1e4, 10, 10)
     assert lam.size == 101 and np.isinf(lam[0])
@@ -253,6 +324,21 @@ def _plant(monkeypatch, which):
     elif which == "pcg_no_precond_update":
         orig = O.jacobi_blocks
         monkeypatch.setattr(O, "jacobi_blocks", lambda prob: 2.0 * orig(prob) + 1e-3)
+    elif which == "jacobi_no_multiplicity":
+        # c0 without the rfft multiplicities (the mean of 1/N over the rfft bins only)
+        def bad(prob):
+            nc = prob.ncomp
+            M = np.zeros((prob.npix, nc, nc))
+            for c, (a, b) in enumerate(prob.chunks()):
+                c0 = np.mean(1.0 / prob.psd[c])
+                pix = prob.pix[a:b]
+                good = pix >= 0
+                w = prob.weights(a, b)[good]
+                np.add.at(M, pix[good], c0 * w[:, :, None] * w[:, None, :])
+            Minv = np.zeros_like(M)
+            Minv[prob.valid] = np.linalg.inv(M[prob.valid])
+            return Minv
+        monkeypatch.setattr(O, "jacobi_blocks", bad)
     elif which == "transposed_block":
         orig = O.Problem.bin
 
@@ -263,7 +349,8 @@ def _plant(monkeypatch, which):
 
 
 @pytest.mark.parametrize("which", ["drop_lambda", "swap_qu", "filter_sign", "chi2_no_mult",
-                                   "nbar_is_n", "transposed_block"])
+                                   "nbar_is_n", "transposed_block", "pcg_no_precond_update",
+                                   "jacobi_no_multiplicity"])
 def test_planted_mistakes(monkeypatch, which):
     """Each planted slip in the oracle must break at least one pin."""
     _plant(monkeypatch, which)
