@@ -2,28 +2,33 @@
 
 One step = one cooled messenger iteration (Sec. 2.1) over the whole workload: pointing
 gather + column FFTs, row FFTs with the Fourier-diagonal filter and chi^2, inverse FFTs +
-FP64 binning, and the per-pixel 3x3 map solve.  Default workload: 512x512 IQU map, 8
-detectors x 2^22 samples at 200 Hz (33.5 M samples), FP32 cos/sin weights, per-detector
-1/f noise, lambda cycling through a 10 x 10 cooling schedule.  Inputs per step (pointing
-403 MB, data spectrum 134 MB, noise table 67 MB) exceed the 129 MB L2, so no flush is
-needed.  The default line also carries the uneven-chunk workload (64 chunks of 2-3-5-smooth
-lengths in [2^16, 2^20], 1024^2 IQU map) under "uneven_chunks".  ``--workload`` selects
-another headline workload: ``uneven64_1024`` or ``crosslinked2048_32det_2^24`` (2048^2 IQU,
-32 x 2^24 samples, FP16 weights; 200 cooled messenger iterations against 200 PCG
-iterations with chi^2 per iteration).
+FP64 binning, and the per-pixel 3x3 map solve.  Default workload: the large single-GPU run,
+a 2048x2048 IQU map (12.6 M unknowns), 32 detectors x 2^24 samples at 200 Hz (537 M FP32
+samples), FP16 cos 2psi / sin 2psi, cross-linked rasters at 0, 45, 90 and 135 degrees, 1/f
+noise with f_knee 0.5 Hz and alpha 2, lambda cycling through a 10 x 10 cooling schedule.
+Inputs per step (pointing 4.3 GB, data spectrum 2.1 GB) are far larger than the 129 MB L2,
+so no flush is needed.  The metric is TOD samples processed per second by the messenger
+iteration (sum of the chunk lengths x iterations / s); iterations/s is reported beside it.
+The line also carries 200 cooled messenger iterations against 200 PCG iterations with chi^2
+per iteration (time to chi^2 tolerance), the plain FP64 single-launch step on the same GPU,
+and secondary records of the other workloads (512^2 IQU 8 x 2^22, uneven chunks, composite
+pointing, 64^2 T-only, the adjoint).
 
-``--impl reference`` times the FP64 CPU oracle on the same workload instead (a bounded
-sample: one detector chunk per step, scaled by the number of chunks).
+``--impl reference`` times the FP64 CPU oracle on the same workload instead, on the host's
+cores: each step is one oracle messenger iteration over a bounded sample of the workload
+(whole chunks, one per worker process), and the value is samples of that sample per second.
 
 With ``--gpus N`` under torchrun each rank runs an independent replica on its own GPU
-(the solver is single-GPU); value = total iterations of all ranks / max rank time.
+(the solver is single-GPU); value = samples of all ranks' iterations / max rank time.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -35,10 +40,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "messenger iters/s"
-UNIT = "iter/s"
-WORKLOAD = "iqu512_8det_2^22"
-WORKLOADS = ("iqu512_8det_2^22", "uneven64_1024", "crosslinked2048_32det_2^24", "t64_1det_2^15")
+METRIC = "messenger TOD Gsamples/s"
+UNIT = "Gsamples/s"
+WORKLOAD = "crosslinked2048_32det_2^24"
+WORKLOADS = ("crosslinked2048_32det_2^24", "iqu512_8det_2^22", "uneven64_1024", "t64_1det_2^15",
+             "crosslinked2048_4det_2^24")
+# Samples one CTA's shared memory could transform on its own (8192 complex points, 64 KB).
+# Chunks longer than this pay one global exchange per FFT direction in the bytes model.
+N_ONCHIP = 1 << 14
 
 
 def load_workload(name):
@@ -51,6 +60,8 @@ def load_workload(name):
         return synth.config_crosslinked()
     if name == "t64_1det_2^15":
         return synth.config_temperature_64()
+    if name == "crosslinked2048_4det_2^24":   # one detector per raster angle: profiling size
+        return synth.config_crosslinked(n_det=4)
     raise ValueError(name)
 
 
@@ -65,7 +76,7 @@ def workload_config(name, s):
            "schedule": "10 levels x 10 iterations, cycled",
            "l2": ("inputs larger than L2 (>%d MB read per step), no flush" % (n * 12 // 2 ** 20)
                   if n * 12 > 129 * 2 ** 20 else
-                  "inputs fit in L2 (not flushed): a latency figure, iterations/s only"),
+                  "inputs fit in L2 (not flushed): a latency figure"),
            "parallelism": "replicas"}
     if len(set(lens.tolist())) == 1:
         cfg["samples_per_chunk"] = int(lens[0])
@@ -76,29 +87,44 @@ def workload_config(name, s):
 
 
 def bytes_model(s):
-    """Algorithmic HBM bytes of each kernel for one whole iteration (see the design notes):
-    Y = bytes of the four-step intermediate (4 per sample for even chunks, packed as complex
-    pairs; 8 for odd ones, complex transforms), w = weight bytes per sample."""
+    """Algorithmic HBM bytes of one whole iteration, per kernel, B_strict and B_pass.
+
+    Symbols: n samples, w weight bytes per sample (0 T-only, 8 FP32 cos/sin, 4 FP16), Y the
+    bytes of the data spectrum and of the four-step intermediate (complex64 per 2 samples,
+    4n, for even chunks; per sample, 8n, for odd chunks, which are complex transforms).
+    B_strict = 2 n (4 + w) + Y + n_pix B_map: the pointing read for P and again for P^T, the
+    data spectrum once, and the map-sized traffic B_map = 104 B per IQU pixel (float4 gather
+    source 16, FP64 accumulator write 24, FP64 inverse block 48, map write 16; T-only 4 + 8 +
+    8 + 4 = 24).  B_pass = B_strict + one global exchange per FFT direction (write + read of
+    the intermediate, 4Y) for every chunk longer than N_ONCHIP.  Per kernel: A (gather +
+    column FFT) n (4 + w) + Y + gather, B (row FFT + filter) 3Y, C (inverse column FFT +
+    binning) Y + n (4 + w) + accumulator, D (map step) inverse + map write; A + B + C + D =
+    B_pass.  `tables`: the bytes of the FP32 Nbar table the filter also reads (one float
+    per spectrum slot), which the model leaves out (the spectrum is a function of the
+    noise parameters)."""
     lens = np.diff(s["offsets"]).astype(np.int64)
     n = int(lens.sum())
     nc, npix = s["ncomp"], s["npix"]
     w = 0 if nc == 1 else (4 if s["cos"].dtype == np.float16 else 8)
     if s.get("pix_b") is not None:
         w = 2 * (4 + w) - 4          # two pointing entries per sample (App. B)
-    Y = int(np.sum(np.where(lens % 2 == 1, 8 * lens, 4 * lens)))
-    blk = 6 if nc == 3 else 1
-    mapb = 16 if nc == 3 else 4
+    ybytes = np.where(lens % 2 == 1, 8 * lens, 4 * lens)
+    Y = int(ybytes.sum())
+    exchange = int(4 * ybytes[lens > N_ONCHIP].sum())
+    gather, accb = (16, 24) if nc == 3 else (4, 8)
+    dmap = (48 + 16) if nc == 3 else (8 + 4)
     stages = {
-        "gather_fft": n * (4 + w) + Y + mapb * npix,
-        "filter": 2 * Y + Y + Y // 2,
-        "ifft_bin": Y + n * (4 + w) + 8 * nc * npix,
-        "map": npix * (16 * nc + 8 * blk + mapb),
+        "gather_fft": n * (4 + w) + Y + gather * npix,
+        "filter": 3 * Y,
+        "ifft_bin": Y + n * (4 + w) + accb * npix,
+        "map": dmap * npix,
     }
-    # one launch of the three passes together: their bytes (the intermediate still makes
-    # the round trips between the passes)
+    # one launch of the three passes together (the intermediate still makes its round trip)
     stages["fused_passes"] = stages["gather_fft"] + stages["filter"] + stages["ifft_bin"]
-    strict = 2 * n * (4 + w) + Y + npix * (104 if nc == 3 else 24)
-    return stages, strict, sum(v for k, v in stages.items() if k != "fused_passes")
+    strict = 2 * n * (4 + w) + Y + npix * (gather + accb + dmap)
+    bpass = strict + exchange
+    tables = int(np.where(lens % 2 == 1, 4 * lens, 2 * lens).sum())
+    return stages, strict, bpass, tables
 
 
 class ClockSampler:
@@ -176,42 +202,132 @@ def max_over_ranks(x, dev):
     return float(t.item())
 
 
-def job_rate(ms_per_step_local, world, dev):
-    """(whole-job iterations/s, ms per step): every rank runs its own replica, so the job
-    completes world iterations per step in the slowest rank's time."""
+def job_rate(ms_per_step_local, world, dev, units_per_step=1.0):
+    """(whole-job units/s, ms per step): every rank runs its own replica of `units_per_step`
+    units, so the job completes world x units_per_step units per step in the slowest rank's
+    time."""
     ms = max_over_ranks(ms_per_step_local, dev)
-    return world / (ms / 1e3), ms
+    return world * units_per_step / (ms / 1e3), ms
 
 
 # ----------------------------------------------------------------------- CPU oracle
-def time_oracle(s, steps, warmup, one_chunk=True):
-    """Time the FP64 oracle's messenger step on the host (chunk 0 only when one_chunk,
-    scaled by total samples / chunk-0 samples)."""
-    import oracle.messenger as O
-    sub = s
-    scale = 1.0
-    if one_chunk:
-        c = 0
-        a, b = int(s["offsets"][c]), int(s["offsets"][c + 1])
-        sub = dict(s)
-        sub["pix"], sub["tod"] = s["pix"][a:b], s["tod"][a:b]
-        sub["cos"] = None if s["cos"] is None else s["cos"][a:b]
-        sub["sin"] = None if s["sin"] is None else s["sin"][a:b]
-        sub["offsets"] = np.array([0, b - a], dtype=np.int64)
-        sub["params"] = s["params"][c:c + 1]
-        scale = float(len(s["offsets"]) - 1)
-    if one_chunk:
-        scale = float(s["offsets"][-1]) / float(len(sub["pix"]))
-    prob = O.problem_from_synth(sub)
-    lam = O.cooling_schedule(O.lambda_max(prob), 10, 10)
-    m = np.zeros((sub["npix"], sub["ncomp"]))
-    for i in range(warmup):
-        m, _ = O.messenger_step(prob, m, lam[i % len(lam)])
-    t0 = time.perf_counter()
-    for i in range(steps):
-        m, _ = O.messenger_step(prob, m, lam[(warmup + i) % len(lam)])
-    dt = (time.perf_counter() - t0) / steps * scale
-    return 1.0 / dt, dt
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _mem_available_gb():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                gb = int(line.split()[1]) / 2 ** 20
+                break
+        else:
+            return None
+    except OSError:
+        return None
+    try:   # a cgroup limit below the host's free memory
+        lim = open("/sys/fs/cgroup/memory.max").read().strip()
+        use = int(open("/sys/fs/cgroup/memory.current").read().strip())
+        if lim != "max":
+            gb = min(gb, (int(lim) - use) / 2 ** 30)
+    except (OSError, ValueError):
+        pass
+    return gb
+
+
+def chunk_sample(s, chunks):
+    """The sub-workload made of the given whole chunks (same map, same noise model)."""
+    parts = [(int(s["offsets"][c]), int(s["offsets"][c + 1])) for c in chunks]
+    sub = dict(s)
+    for k in ("pix", "tod", "cos", "sin"):
+        sub[k] = None if s[k] is None else np.concatenate([s[k][a:b] for a, b in parts])
+    sub["offsets"] = np.concatenate([[0], np.cumsum([b - a for a, b in parts])]).astype(np.int64)
+    sub["params"] = s["params"][list(chunks)]
+    return sub
+
+
+def _oracle_worker(sub, steps, warmup, barrier, queue):
+    """One host process: the FP64 oracle's messenger step on its own chunks, each step
+    started together with the other workers (barrier), wall time per step."""
+    try:
+        import oracle.messenger as O
+        prob = O.problem_from_synth(sub)
+        lam = O.cooling_schedule(O.lambda_max(prob), 10, 10)
+        m = np.zeros((sub["npix"], sub["ncomp"]))
+        times = []
+        for i in range(warmup + steps):
+            barrier.wait(timeout=3600)
+            t0 = time.perf_counter()
+            m, _ = O.messenger_step(prob, m, lam[i % len(lam)])
+            times.append(time.perf_counter() - t0)
+        queue.put(("ok", times[warmup:]))
+    except Exception as e:  # noqa: BLE001 -- reported to the parent
+        queue.put(("error", repr(e)))
+
+
+def oracle_rate(s, workers, steps, warmup):
+    """Time the FP64 oracle as it stands on `workers` host processes (started with spawn,
+    one thread each), worker k iterating on chunk k of the workload; every step starts
+    together on all workers.  Returns (samples/s, mean step wall in s, chunks, samples per
+    step).  Workers are capped by the chunk count and by host memory (about 4 GB per
+    chunk of 2^24 samples on a 4 M-pixel map)."""
+    import multiprocessing as mp
+    nch = len(s["offsets"]) - 1
+    lens = np.diff(s["offsets"])
+    per_gb = 0.5 + (150.0 * float(lens.max()) + 100.0 * s["npix"] * s["ncomp"]) / 1e9
+    mem = _mem_available_gb()
+    cap = nch if mem is None else max(1, int(0.5 * mem / per_gb))
+    workers = max(1, min(workers, nch, cap))
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(workers)
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_worker,
+                         args=(chunk_sample(s, [c]), steps, warmup, barrier, queue))
+             for c in range(workers)]
+    for p in procs:
+        p.start()
+    res = [queue.get(timeout=7200) for _ in procs]
+    for p in procs:
+        p.join(timeout=600)
+    bad = [r[1] for r in res if r[0] != "ok"]
+    if bad:
+        raise RuntimeError("oracle worker failed: %s" % bad[0])
+    walls = [max(r[1][i] for r in res) for i in range(steps)]
+    samples = int(lens[:workers].sum())
+    wall = sum(walls) / len(walls)
+    return samples / wall, wall, workers, samples
+
+
+def cpu_baseline_record(s, steps=1):
+    """The oracle on one core and on all host cores (one process per chunk), one iteration
+    each after none untimed, in Gsamples/s."""
+    one_v, one_wall, _, one_n = oracle_rate(s, 1, steps, 0)
+    allc = os.cpu_count() or 1
+    all_v, all_wall, w, all_n = oracle_rate(s, allc, steps, 0)
+    return {"value": all_v / 1e9, "unit": UNIT, "cores": w, "kind": "oracle",
+            "sample": "%d iteration(s) of the FP64 oracle's messenger step on %d whole chunk(s) "
+                      "(%d samples), one process and thread per chunk, on the full map; "
+                      "rate = samples / wall time of the slowest process" % (steps, w, all_n),
+            "cpu_model": cpu_model(), "cpu_count": allc,
+            "single_core": {"value": one_v / 1e9, "unit": UNIT, "cores": 1,
+                            "sample": "%d iteration(s) on chunk 0 (%d samples), 1 thread"
+                                      % (steps, one_n), "s_per_iteration": one_wall}}
 
 
 def run_reference(args):
@@ -219,17 +335,20 @@ def run_reference(args):
     if rank != 0:
         return
     s = load_workload(args.workload)
-    nch = len(s["offsets"]) - 1
-    v, dt = time_oracle(s, args.steps, args.warmup, one_chunk=True)
-    sample = "chunk 0 of %d (%d samples) per step, time x%d; numpy FP64, 1 thread" % (
-        nch, int(s["offsets"][1] - s["offsets"][0]), nch)
-    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args.workload, s),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+    v, wall, w, n_samp = oracle_rate(s, os.cpu_count() or 1, args.steps, args.warmup)
+    sample = ("per step one FP64 oracle messenger iteration on each of %d whole chunks (%d "
+              "samples), one process and thread per chunk, on the full map; rate = samples / "
+              "wall time of the slowest process; %s, %d logical CPUs"
+              % (w, n_samp, cpu_model(), os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v / 1e9, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.workload, s),
+            "cpu_baseline": {"value": v / 1e9, "unit": UNIT, "cores": w, "kind": "oracle",
                              "sample": sample},
-            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": v / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -290,10 +409,11 @@ def fused_loop(plan, sched, first, steps, dev, stream, chi):
                              for b in range(nb)]}
 
 
-def graph_ms(plan, m, lams, dev, stream):
-    """Device time per iteration of `lams` replayed as one captured CUDA graph each."""
+def graph_ms(plan, m, lam_warm, lams, dev, stream):
+    """Device time per iteration of `lams` replayed as one captured CUDA graph each, after
+    the warm-up iterations `lam_warm` (the first captures the graph)."""
     import torch
-    plan.messenger_graph(m, lams[:2])
+    plan.messenger_graph(m, lam_warm if len(lam_warm) else lams[:2])
     fence(dev)
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(stream)
@@ -311,28 +431,165 @@ def hbm_peak():
     return float(peaks.get("hbm_gbs", 6800.0)), ("measured" if "hbm_gbs" in peaks else "fallback")
 
 
-def summarise(s, nb, stage_ms, ms_iter, hbm):
-    """Per-kernel averages, the dominant kernel and the iteration's HBM fractions.  With a
-    fused launch timed (`fused_passes`), the dominant kernel is taken among the launches
-    the graph-replayed iteration runs (the fused one and the map step)."""
-    stages, strict, bpass = bytes_model(s)
+def source_digest():
+    """SHA-256 of the CUDA sources (csrc/*.cu, *.cuh) and the public header: DRAM byte counts
+    recorded in profiles/traffic.json are used only while the kernels they were taken on are
+    unchanged."""
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1705_01893_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(f.encode())
+            h.update(open(os.path.join(d, f), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "mm.h"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, kernel):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary, or
+    None when there is none or the sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(workload)
+    if not rec or rec.get("source_digest") != source_digest():
+        return None
+    return rec.get("bytes_per_launch", {}).get(kernel)
+
+
+def kernel_table(name, s, nb, stage_ms, hbm):
+    """Per-launch time, algorithmic bytes and HBM fraction of each kernel of the iteration;
+    the dominant one is the slowest launch of the graph-replayed iteration (the fused launch
+    and the map step when the batches run fused)."""
+    stages, _, _, _ = bytes_model(s)
     avg = {k: sum(v) / len(v) for k, v in stage_ms.items()}
-    # the FFT kernels run once per batch; batches split the samples
     per_launch = {k: (v / nb if k != "map" else v) for k, v in stages.items()}
-    runs = ["fused_passes", "map"] if "fused_passes" in avg else [k for k in avg]
+    runs = ["fused_passes", "map"] if "fused_passes" in avg else \
+        ["gather_fft", "filter", "ifft_bin", "map"]
+    table = {k: {"ms_per_launch": round(avg[k], 5), "bytes_per_launch": int(per_launch[k]),
+                 "achieved_gbs": per_launch[k] / (avg[k] * 1e-3) / 1e9,
+                 "frac": per_launch[k] / (avg[k] * 1e-3) / 1e9 / hbm} for k in avg}
     dom = max(runs, key=lambda k: avg[k])
-    return {
-        "avg": avg, "dom": dom, "per_launch": per_launch,
-        "achieved": per_launch[dom] / (avg[dom] * 1e-3) / 1e9,
-        "iteration_hbm": {"bytes_pass": bpass, "bytes_strict": strict,
-                          "frac_pass": bpass / (ms_iter * 1e-3) / 1e9 / hbm,
-                          "frac_strict": strict / (ms_iter * 1e-3) / 1e9 / hbm},
-    }
+    return table, dom
 
 
-def measure_secondary(name, args, dev, stream):
-    """Graph-replayed iteration time, per-kernel times and HBM fractions of another workload
-    (a compact record beside the headline line)."""
+def iteration_hbm(s, ms_iter, hbm, src):
+    _, strict, bpass, tables = bytes_model(s)
+    return {"bytes_pass": bpass, "bytes_strict": strict,
+            "frac_pass": bpass / (ms_iter * 1e-3) / 1e9 / hbm,
+            "frac_strict": strict / (ms_iter * 1e-3) / 1e9 / hbm,
+            "bytes_nbar_table": tables,
+            "frac_pass_with_table": (bpass + tables) / (ms_iter * 1e-3) / 1e9 / hbm,
+            "peak_gbs": hbm, "peak": src}
+
+
+def measure_kernels(plan, sched, dev, stream, chi, steps, warmup):
+    """Per-launch times of the iteration's kernels: the three pass kernels and the map step
+    launched stage by stage with events between them, then (when every batch runs fused)
+    the fused launch that the graph-replayed iteration runs."""
+    nb = plan.n_batches()
+    stage_loop(plan, sched, 0, warmup, dev, stream, chi)
+    st, total = stage_loop(plan, sched, warmup, steps, dev, stream, chi)
+    if plan.n_fused_batches() == nb:
+        fused_loop(plan, sched, 0, warmup, dev, stream, chi)
+        st.update(fused_loop(plan, sched, warmup, steps, dev, stream, chi))
+    return st, total / steps
+
+
+def plain_fp64_ms(plan, m, sched, dev, stream, n_it=3):
+    """The plain FP64 single-launch-per-iteration step on the same GPU (comparison bar)."""
+    import torch
+    mp = m.clone()
+    lam_p = np.array([float(sched[k % len(sched)]) for k in range(n_it)])
+    plan.messenger_plain_fp64(mp, lam_p[:1])
+    torch.cuda.synchronize(dev)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    plan.messenger_plain_fp64(mp, lam_p)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    return p0.elapsed_time(p1) / len(lam_p)
+
+
+def fft_vs_cufft(plan, lens, dev, stream, reps=10):
+    """cuFFT (through torch.fft, a library call timed only as a comparison) against this
+    library's rfft of the same chunks (column + row kernels, natural-order output)."""
+    import torch
+    tod_dev = plan.tod.view(len(lens), -1)
+    spec = torch.empty(tod_dev.shape[0] * (tod_dev.shape[1] // 2 + 1), 2, dtype=torch.float32,
+                       device=dev)
+    for _ in range(3):
+        torch.fft.rfft(tod_dev, dim=1)
+        plan.rfft(plan.tod, spec)
+    f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    f0.record(stream)
+    for _ in range(reps):
+        torch.fft.rfft(tod_dev, dim=1)
+    f1.record(stream)
+    for _ in range(reps):
+        plan.rfft(plan.tod, spec)
+    f2.record(stream)
+    torch.cuda.synchronize(dev)
+    out = {"cufft_rfft_ms": f0.elapsed_time(f1) / reps, "mm_rfft_ms": f1.elapsed_time(f2) / reps,
+           "what": "rfft of %d x %d float32 samples, complex64 out" % (len(lens), lens[0])}
+    del spec
+    torch.cuda.empty_cache()
+    return out
+
+
+def map_sized_cmp(plan, m, sched, dev, stream):
+    """The map-sized form m' = m_d(lambda) + F(lambda) m against the standard step, both
+    launched stage by stage from the host: 10 and 60 iterations at one lambda separate the
+    per-iteration cost from the one-off m_d pass of each distinct lambda."""
+    import torch
+    lam1 = float(sched[len(sched) // 2])
+    t = {}
+    for label, fn in (("standard", lambda mm, l: plan.messenger(mm, l)),
+                      ("map_sized", lambda mm, l: plan.messenger_md(mm, l))):
+        mm = m.clone()
+        fn(mm, [lam1] * 2)
+        for n_it in (10, 60):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(mm, [lam1] * n_it)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t[(label, n_it)] = e0.elapsed_time(e1)
+    out = {k: {"ms_per_iter": (t[(k, 60)] - t[(k, 10)]) / 50, "ms_10_iter": t[(k, 10)]}
+           for k in ("standard", "map_sized")}
+    out["map_sized"]["ms_m_d_per_lambda"] = t[("map_sized", 10)] - \
+        10 * out["map_sized"]["ms_per_iter"]
+    return out
+
+
+def chi2_diagnostics(plan, m, dev, stream, reps=10):
+    """chi^2 of a map (mm_chi2, total) and chi^2 per Fourier mode (mm_chi2_modes, Sec. 3.1's
+    diagnostic), each a forward pass of its own."""
+    import torch
+    mm = m.clone()
+    plan.chi2(mm)
+    plan.chi2_modes(mm)
+    torch.cuda.synchronize(dev)
+    diag = {}
+    for label, fn in (("chi2_total_ms", lambda: plan.chi2(mm)),
+                      ("chi2_per_mode_ms", lambda: plan.chi2_modes(mm))):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        diag[label] = e0.elapsed_time(e1) / reps
+    diag["timing"] = ("events around 10 calls each; the chi^2 that the iteration reports "
+                      "with chi2_out comes from its own row jobs at no extra pass")
+    return diag
+
+
+def measure_secondary(name, args, dev, stream, extras=False):
+    """Graph-replayed iteration time, per-kernel times, the dominant kernel's roofline and
+    the iteration's HBM fractions of another workload (a compact record beside the headline
+    line); with `extras`, also the plain FP64 step, cuFFT, the map-sized form and the chi^2
+    diagnostics on it."""
     import torch
     from paper_1705_01893_gb300 import binding
     s = load_workload(name)
@@ -343,20 +600,30 @@ def measure_secondary(name, args, dev, stream):
     chi = torch.zeros(len(sched), dtype=torch.float64, device=dev)
     plan.stage(binding.MM_STAGE_LOAD, map_inout=m)
     steps = 20
-    stage_loop(plan, sched, 0, 3, dev, stream, chi)
-    st, _ = stage_loop(plan, sched, 3, steps, dev, stream, chi)
+    st, _ = measure_kernels(plan, sched, dev, stream, chi, steps, 3)
     lam = np.array([float(sched[k % len(sched)]) for k in range(steps)])
-    ms = graph_ms(plan, m.clone(), lam, dev, stream)
+    ms = graph_ms(plan, m.clone(), lam[:3], lam, dev, stream)
     hbm, src = hbm_peak()
-    sm = summarise(s, plan.n_batches(), st, ms, hbm)
+    table, dom = kernel_table(name, s, plan.n_batches(), st, hbm)
     n = int(s["offsets"][-1])
+    lens = np.diff(s["offsets"])
     out = {"config": workload_config(name, s), "ms_per_iter": ms, "iters_per_s": 1e3 / ms,
            "schedule": dict(zip(("col_nb", "col_threads", "row_threads", "radix_order"), plan.tune)),
            "tod_gsamples_per_s": n / ms / 1e6, "batches": plan.n_batches(),
-           "stage_ms_per_launch": {k: round(v, 5) for k, v in sm["avg"].items()},
-           "dominant": {"kernel": sm["dom"], "achieved_gbs": sm["achieved"],
-                        "frac": sm["achieved"] / hbm, "bytes_per_launch": sm["per_launch"][sm["dom"]]},
-           "iteration_hbm": dict(sm["iteration_hbm"], peak_gbs=hbm, peak=src)}
+           "fused_batches": plan.n_fused_batches(), "kernels": table,
+           "roofline": {"bound": "hbm", "kernel": dom, "achieved": table[dom]["achieved_gbs"],
+                        "peak": hbm, "unit": "GB/s", "frac": table[dom]["frac"],
+                        "traffic": measured_traffic(name, dom),
+                        "bytes_per_launch": table[dom]["bytes_per_launch"], "peak_source": src},
+           "iteration_hbm": iteration_hbm(s, ms, hbm, src)}
+    if extras:
+        plain = plain_fp64_ms(plan, m, sched, dev, stream, 5)
+        out["fp64_plain_ms_per_step"] = plain
+        out["speedup_vs_fp64_plain"] = plain / ms
+        if len(set(lens.tolist())) == 1:
+            out["fft_vs_cufft"] = fft_vs_cufft(plan, lens, dev, stream)
+        out["map_sized_form"] = map_sized_cmp(plan, m, sched, dev, stream)
+        out["chi2_diagnostics"] = chi2_diagnostics(plan, m, dev, stream)
     del plan
     torch.cuda.empty_cache()
     return out
@@ -381,16 +648,12 @@ def measure_composite(dev, stream, steps=20):
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
     hbm, src = hbm_peak()
-    _, strict, bpass = bytes_model(s)
     n = int(s["offsets"][-1])
     out = {"config": dict(workload_config("differential512_9x2^21", s),
                           pointing="two beams per sample (+1 / -1), 3 px apart"),
            "ms_per_iter": ms, "iters_per_s": 1e3 / ms, "tod_gsamples_per_s": n / ms / 1e6,
            "schedule": dict(zip(("col_nb", "col_threads", "row_threads", "radix_order"), plan.tune)),
-           "iteration_hbm": {"bytes_pass": bpass, "bytes_strict": strict,
-                             "frac_pass": bpass / (ms * 1e-3) / 1e9 / hbm,
-                             "frac_strict": strict / (ms * 1e-3) / 1e9 / hbm,
-                             "peak_gbs": hbm, "peak": src},
+           "iteration_hbm": iteration_hbm(s, ms, hbm, src),
            "timing": "K iterations in one mm_messenger_iterate call, events around it"}
     del plan
     torch.cuda.empty_cache()
@@ -482,116 +745,34 @@ def run_gpu(args):
     plan.autotune()          # schedules of the general-length kernels (no-op otherwise)
     sched = binding.cooling_schedule(plan.lambda_max(), 10, 10)
     m = torch.zeros(npix, nc, dtype=torch.float64, device=dev)
-    chi = torch.zeros(max(args.steps, 1) + args.warmup, dtype=torch.float64, device=dev)
+    chi = torch.zeros(len(sched), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     nb = plan.n_batches()
-
     plan.stage(binding.MM_STAGE_LOAD, map_inout=m)
-    stage_loop(plan, sched, 0, args.warmup, dev, stream, chi)
 
     uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", local))
     sampler = ClockSampler(("GPU-" + uuid) if "-" in uuid and not uuid.startswith("GPU") else uuid)
     time.sleep(0.3)
-    stage_ms, total_ms = stage_loop(plan, sched, args.warmup, args.steps, dev, stream, chi)
-    _, stage_ms_step = job_rate(total_ms / args.steps, world, dev)
-    n_fused = plan.n_fused_batches()
-    fused = n_fused == nb
-    if fused:
-        fused_loop(plan, sched, 0, args.warmup, dev, stream, chi)
-        stage_ms.update(fused_loop(plan, sched, args.warmup, args.steps, dev, stream, chi))
-
-    # the same iterations replayed as one captured CUDA graph per iteration (the value)
-    lam_g = np.array([float(sched[(args.warmup + k) % len(sched)]) for k in range(args.steps)])
-    ms_local = graph_ms(plan, m.clone(), lam_g, dev, stream)
+    # W warm-up iterations, then the timed K, replayed as one captured CUDA graph each
+    lam_w = np.array([float(sched[k % len(sched)]) for k in range(args.warmup)])
+    lam_t = np.array([float(sched[(args.warmup + k) % len(sched)]) for k in range(args.steps)])
+    ms_local = graph_ms(plan, m.clone(), lam_w, lam_t, dev, stream)
+    value, ms_step = job_rate(ms_local, world, dev, units_per_step=n / 1e9)
+    # per-kernel times (stage API and the fused launch, events between launches)
+    stage_ms, stage_ms_step = measure_kernels(plan, sched, dev, stream, chi, args.steps,
+                                              args.warmup)
     clocks = sampler.stop()
     # bounded waits of the fused launch that ran out during the runs above (0: none)
     fault_flags = plan.fault_flags()
-    value, ms_step = job_rate(ms_local, world, dev)
+    hbm, peak_src = hbm_peak()
+    table, dom = kernel_table(name, s, nb, stage_ms, hbm)
+    n_fused = plan.n_fused_batches()
 
-    # the plain FP64 single-launch-per-iteration step on the same GPU (comparison bar; one
-    # power-of-two chunk length only)
-    plain_ms = None
-    if not args.no_plain and plan.n_batches() >= 1 and len(set(lens.tolist())) == 1 \
-            and name == WORKLOAD:
-        mp = m.clone()
-        lam_p = np.array([float(sched[k % len(sched)]) for k in range(5)])
-        plan.messenger_plain_fp64(mp, lam_p[:1])
-        torch.cuda.synchronize(dev)
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        plan.messenger_plain_fp64(mp, lam_p)
-        p1.record(stream)
-        torch.cuda.synchronize(dev)
-        plain_ms = p0.elapsed_time(p1) / len(lam_p)
-
-    # cuFFT (through torch.fft, a library call timed only as a comparison) against this
-    # library's rfft of the same chunks (column + row kernels, natural-order output)
-    fft_cmp = None
-    if not args.no_plain and len(set(lens.tolist())) == 1:
-        tod_dev = plan.tod.view(len(lens), -1)
-        spec = torch.empty(tod_dev.shape[0] * (tod_dev.shape[1] // 2 + 1), 2, dtype=torch.float32,
-                           device=dev)
-        for _ in range(3):
-            torch.fft.rfft(tod_dev, dim=1)
-            plan.rfft(plan.tod, spec)
-        f0, f1, f2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        reps = 10
-        f0.record(stream)
-        for _ in range(reps):
-            torch.fft.rfft(tod_dev, dim=1)
-        f1.record(stream)
-        for _ in range(reps):
-            plan.rfft(plan.tod, spec)
-        f2.record(stream)
-        torch.cuda.synchronize(dev)
-        fft_cmp = {"cufft_rfft_ms": f0.elapsed_time(f1) / reps, "mm_rfft_ms": f1.elapsed_time(f2) / reps,
-                   "what": "rfft of %d x %d float32 samples, complex64 out" % (len(lens), lens[0])}
-        del spec
-
-    # the map-sized form m' = m_d(lambda) + F(lambda) m against the standard step, both
-    # launched stage by stage from the host: 10 and 60 iterations at one lambda separate the
-    # per-iteration cost from the one-off m_d pass of each distinct lambda
-    md_cmp = None
-    if not args.no_plain and name == WORKLOAD:
-        lam1 = float(sched[len(sched) // 2])
-        t = {}
-        for label, fn in (("standard", lambda mm, l: plan.messenger(mm, l)),
-                          ("map_sized", lambda mm, l: plan.messenger_md(mm, l))):
-            mm = m.clone()
-            fn(mm, [lam1] * 2)
-            for n_it in (10, 60):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                fn(mm, [lam1] * n_it)
-                e1.record(stream)
-                torch.cuda.synchronize(dev)
-                t[(label, n_it)] = e0.elapsed_time(e1)
-        md_cmp = {k: {"ms_per_iter": (t[(k, 60)] - t[(k, 10)]) / 50,
-                      "ms_10_iter": t[(k, 10)]} for k in ("standard", "map_sized")}
-        md_cmp["map_sized"]["ms_m_d_per_lambda"] = t[("map_sized", 10)] - \
-            10 * md_cmp["map_sized"]["ms_per_iter"]
-
-    # diagnostics beside the iteration: chi^2 of a map (mm_chi2, total) and chi^2 per Fourier
-    # mode (mm_chi2_modes, Sec. 3.1's diagnostic), each a forward pass of its own
-    diag = None
-    if not args.no_plain and name == WORKLOAD:
-        mm = m.clone()
-        reps = 10
-        plan.chi2(mm)
-        plan.chi2_modes(mm)
-        fence(dev)
-        diag = {}
-        for label, fn in (("chi2_total_ms", lambda: plan.chi2(mm)),
-                          ("chi2_per_mode_ms", lambda: plan.chi2_modes(mm))):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                fn()
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            diag[label] = e0.elapsed_time(e1) / reps
-        diag["timing"] = ("events around 10 calls each; the chi^2 that the iteration reports "
-                          "with chi2_out comes from its own row jobs at no extra pass")
+    plain_ms = fft_cmp = None
+    if not args.no_plain:
+        plain_ms = plain_fp64_ms(plan, m, sched, dev, stream, 3)
+        if len(set(lens.tolist())) == 1:
+            fft_cmp = fft_vs_cufft(plan, lens, dev, stream)
 
     # end to end through the public call, host buffers: map in (pinned), one iteration,
     # map and chi^2 out, synchronised every step
@@ -618,9 +799,12 @@ def run_gpu(args):
         torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     fence(dev)
-    e2e_rate, _ = job_rate(e2e_s * 1e3, world, dev)
+    e2e_rate, _ = job_rate(e2e_s * 1e3, world, dev, units_per_step=n / 1e9)
     e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": 8 * npix * nc,
-           "d2h_bytes_per_step": 8 * npix * nc + 8}
+           "d2h_bytes_per_step": 8 * npix * nc + 8,
+           "timing": "wall clock per step: pinned-host map -> device, mm_messenger_iterate "
+                     "(one iteration), map and chi^2 -> pinned host, synchronise"}
+    del m_host, m_back, m_dev
 
     tol = None
     if not args.no_tolerance:
@@ -630,67 +814,56 @@ def run_gpu(args):
         else:
             tol = time_to_tolerance(plan, s, dev, stream, args)
 
-    secondary = composite = small = adjoint = None
+    secondary = {}
     if name == WORKLOAD and not args.no_secondary:
         del plan
         torch.cuda.empty_cache()
-        secondary = measure_secondary("uneven64_1024", args, dev, stream)
-        composite = measure_composite(dev, stream)
-        small = measure_secondary("t64_1det_2^15", args, dev, stream)
-        adjoint = measure_adjoint(dev, stream)
+        secondary["iqu512_8det_2^22"] = measure_secondary("iqu512_8det_2^22", args, dev, stream,
+                                                          extras=not args.no_plain)
+        secondary["uneven64_1024"] = measure_secondary("uneven64_1024", args, dev, stream)
+        secondary["composite_pointing"] = measure_composite(dev, stream)
+        secondary["t64_1det_2^15"] = measure_secondary("t64_1det_2^15", args, dev, stream)
+        secondary["adjoint"] = measure_adjoint(dev, stream)
 
     if rank != 0:
         return
-    hbm, peak_src = hbm_peak()
-    sm = summarise(s, nb, stage_ms, ms_step, hbm)
-    dom = sm["dom"]
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof) and name == WORKLOAD:
-        traffic = json.load(open(prof)).get(dom)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(name, s),
-        "tod_gsamples_per_s": n * value / 1e9,
-        "iteration_hbm": dict(sm["iteration_hbm"], peak_gbs=hbm, peak=peak_src),
-        "batches": nb,
-        "timing": "value/ms_per_step: K iterations replayed as one CUDA graph each (events on "
-                  "the launching stream); roofline/stage_ms_per_launch: K iterations launched "
-                  "stage by stage with events between the kernels (gather_fft, filter, "
-                  "ifft_bin: the three separate kernels; fused_passes: the one launch of all "
-                  "three that the graph runs)",
-        "fused_batches": n_fused,
+        "iters_per_s": world * 1e3 / ms_step,
+        "iteration_hbm": iteration_hbm(s, ms_step, hbm, peak_src),
+        "batches": nb, "fused_batches": n_fused,
+        "timing": "value/ms_per_step: W warm-up then K iterations replayed as one captured CUDA "
+                  "graph each, events on the launching stream, barrier + synchronize on both "
+                  "sides, max over ranks; kernels/roofline: K iterations launched stage by "
+                  "stage with events between the kernels (gather_fft, filter, ifft_bin: the "
+                  "three pass kernels; fused_passes: the one launch of all three, when the "
+                  "batches run fused); algorithmic bytes per launch from the bytes model "
+                  "(36 B/sample + 104 B/pixel per iteration for FP16 weights)",
         "fault_flags": fault_flags,
         "stage_loop_ms_per_step": stage_ms_step,
-        "fp64_plain_ms_per_step": plain_ms,
-        "fft_vs_cufft": fft_cmp,
-        "map_sized_form": md_cmp,
-        "chi2_diagnostics": diag,
-        "speedup_vs_fp64_plain": None if plain_ms is None else plain_ms / ms_step,
-        "stage_ms_per_launch": {k: round(v, 5) for k, v in sm["avg"].items()},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": sm["achieved"], "peak": hbm,
-                     "unit": "GB/s", "frac": sm["achieved"] / hbm, "traffic": traffic,
-                     "bytes_per_launch": sm["per_launch"][dom], "peak_source": peak_src},
+        "kernels": table,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": table[dom]["achieved_gbs"],
+                     "peak": hbm, "unit": "GB/s", "frac": table[dom]["frac"],
+                     "traffic": measured_traffic(name, dom),
+                     "bytes_per_launch": table[dom]["bytes_per_launch"],
+                     "peak_source": peak_src},
         "e2e": e2e,
-        # per timed region: per iteration one launch per batch (fused) or three, and the map
-        "gpu_launches": args.steps * ((1 if fused else 3) * nb + 1),
+        # per timed iteration: one launch per batch (fused) or three, and the map step
+        "gpu_launches": args.steps * ((1 if n_fused == nb else 3) * nb + 1),
+        "fp64_plain_ms_per_step": plain_ms,
+        "speedup_vs_fp64_plain": None if plain_ms is None else plain_ms / ms_step,
+        "fft_vs_cufft": fft_cmp,
         "time_to_chi2_tol": tol,
-        "uneven_chunks": secondary,
-        "composite_pointing": composite,
-        "temperature_64": small,
-        "adjoint": adjoint,
+        "secondary": secondary,
         "clocks": clocks,
+        "clocks_window": "nvidia-smi every 200 ms over the warm-up, the timed iterations and "
+                         "the per-kernel loops",
     }
     if world == 1 and not args.no_cpu_baseline:
-        one = name != WORKLOAD
-        v, dt = time_oracle(s, 1, 0, one_chunk=one)
-        line["cpu_baseline"] = {
-            "value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": ("1 full iteration of the workload" if not one else
-                       "1 iteration of chunk 0, scaled by total / chunk-0 samples") +
-                      ", numpy FP64, 1 thread"}
+        line["cpu_baseline"] = cpu_baseline_record(s, 1)
     print(json.dumps(line), flush=True)
 
 
@@ -781,7 +954,7 @@ def main():
                     help="lambda = 1 iterations after the cooling schedule (and PCG length)")
     ap.add_argument("--workload", default=WORKLOAD, choices=WORKLOADS)
     ap.add_argument("--no-secondary", action="store_true",
-                    help="skip the uneven-chunk record in the default line")
+                    help="skip the records of the other workloads in the default line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

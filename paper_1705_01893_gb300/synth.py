@@ -23,6 +23,9 @@ w ~ N(0, 1), whose covariance is exactly F^-1 diag(N_k) F.
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 SEED_BASE = 1705_0000
@@ -30,6 +33,18 @@ SEED_BASE = 1705_0000
 
 def _rng(seed: int, stream: int) -> np.random.Generator:
     return np.random.default_rng([int(seed), int(stream)])
+
+
+def _pmap(fn, items):
+    """[fn(x) for x in items] on a thread pool (NumPy's FFTs, random draws and elementwise
+    kernels release the GIL); every chunk has its own random stream, so the result does not
+    depend on the number of threads."""
+    items = list(items)
+    workers = min(len(items), os.cpu_count() or 1, 16)
+    if workers <= 1:
+        return [fn(x) for x in items]
+    with ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(fn, items))
 
 
 def grf_map(nx: int, ny: int, seed: int, stream: int, rms: float = 1.0) -> np.ndarray:
@@ -161,7 +176,7 @@ def make_problem(width: int, ncomp: int, pix_chunks, fs: float, sigmas, fknees, 
         sin = np.empty(offsets[-1], dtype=weight_dtype)
     tod = np.empty(offsets[-1], dtype=np.float32)
     params = np.zeros((nchunk, 4))
-    for c in range(nchunk):
+    def fill(c):
         a, b = offsets[c], offsets[c + 1]
         n = b - a
         cc = ss = None
@@ -177,6 +192,8 @@ def make_problem(width: int, ncomp: int, pix_chunks, fs: float, sigmas, fknees, 
             sig = sig + draw_noise(n, noise_psd(n, fs, sigmas[c], fknees[c], alphas[c]), seed, 100 + c)
         tod[a:b] = sig
         params[c] = (sigmas[c], fknees[c], alphas[c], fs)
+
+    _pmap(fill, range(nchunk))
     return dict(width=width, npix=width * width, ncomp=ncomp, pix=pix, cos=cos, sin=sin,
                 tod=tod, offsets=offsets, params=params, m_true=m_true)
 
@@ -198,7 +215,8 @@ def config_iqu(width: int, n_det: int, n_per_det: int, seed: int, fs: float = 20
     alphas = rng.uniform(*alpha_range, size=n_det)
     if phase_step is None:
         phase_step = max(1, width // n_det)
-    chunks = [raster_alternating(width, spp, n_per_det, d * phase_step) for d in range(n_det)]
+    chunks = _pmap(lambda d: raster_alternating(width, spp, n_per_det, d * phase_step),
+                   range(n_det))
     angles = [180.0 * d / n_det for d in range(n_det)]
     return make_problem(width, 3, chunks, fs, [1.0] * n_det, fknees, alphas, angles, 0.5,
                         seed, weight_dtype=weight_dtype, noiseless=noiseless)
@@ -229,8 +247,8 @@ def config_uneven(width: int = 1024, n_chunks: int = 64, lo: int = 1 << 16, hi: 
     raster = rng.uniform(0.0, np.pi, size=n_chunks)
     angles = rng.uniform(0.0, 180.0, size=n_chunks)
     phases = rng.integers(0, 1 << 20, size=n_chunks)
-    chunks = [raster_angled(width, spp, int(lens[c]), raster[c], int(phases[c]))
-              for c in range(n_chunks)]
+    chunks = _pmap(lambda c: raster_angled(width, spp, int(lens[c]), raster[c], int(phases[c])),
+                   range(n_chunks))
     return make_problem(width, 3, chunks, fs, sigmas, fknees, alphas, angles, 0.5, seed)
 
 
@@ -241,8 +259,8 @@ def config_crosslinked(width: int = 2048, n_det: int = 32, n_per_det: int = 1 <<
     degrees (detector d at 45 (d mod 4) degrees), detector angles d * 180 / n_det plus a
     0.5 Hz half-wave plate, 1/f noise f_knee 0.5 Hz, alpha 2, sigma 1, FP16 weights."""
     step = max(1, width // max(1, n_det // 4))
-    chunks = [raster_angled(width, spp, n_per_det, np.deg2rad(45.0 * (d % 4)), (d // 4) * step)
-              for d in range(n_det)]
+    chunks = _pmap(lambda d: raster_angled(width, spp, n_per_det, np.deg2rad(45.0 * (d % 4)),
+                                           (d // 4) * step), range(n_det))
     angles = [180.0 * d / n_det for d in range(n_det)]
     return make_problem(width, 3, chunks, fs, [1.0] * n_det, [0.5] * n_det, [2.0] * n_det,
                         angles, 0.5, seed, weight_dtype=weight_dtype)
