@@ -54,7 +54,8 @@ enum {
   MM_ERR_ARG = -1,          /* bad argument (null pointer, size, range)            */
   MM_ERR_CUDA = -2,         /* a CUDA runtime call or kernel launch failed         */
   MM_ERR_NOMEM = -3,        /* workspace (or state) smaller than required          */
-  MM_ERR_TIMEOUT = -4,      /* a bounded device wait gave up (plain FP64 barrier)  */
+  MM_ERR_TIMEOUT = -4,      /* a bounded device wait gave up (plain FP64 barrier;  */
+                            /* fused launch under check-on-return, see below)      */
   MM_ERR_STATE = -5,        /* call out of order (e.g. iterate before set_noise)   */
   MM_ERR_SINGULAR = -6,     /* every pixel was cut                                 */
   MM_ERR_UNSUPPORTED = -7   /* valid input this version does not handle            */
@@ -115,8 +116,22 @@ mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int
  * wait of the fused iteration kernel (one launch for the column, row and inverse column
  * passes of a batch, whose work items wait for their chunk's earlier passes) ran out after
  * about a second; the results of that iteration are then wrong.  Synchronises `stream`.
- * No counterpart in the paper: a check of this library's own scheduling. */
+ * The solver calls (mm_messenger_iterate, mm_messenger_graph, mm_pcg_iterate,
+ * mm_messenger_iterate_md, mm_messenger_adaptive) are asynchronous and, under the default
+ * wait policy, do not see such an expiry: a caller that keeps the default must read these
+ * flags after synchronising to know that its results are valid (or choose check-on-return,
+ * below).  No counterpart in the paper: a check of this library's own scheduling. */
 mm_status mm_plan_fault_flags(mm_plan p, int* flags, void* stream);
+
+/* Wait policy of the fused iteration kernel's bounded waits.  n_polls (1 .. 2^22, default
+ * 2^22, about a second): how often a waiting work item polls its chunk's counter (about
+ * 256 ns apart) before it gives up, sets the plan's fault flag and carries on (its results
+ * are then wrong; nothing traps or hangs).  check_on_return (0 default, 1): with 1, the
+ * solver calls listed above synchronise their stream before returning and return
+ * MM_ERR_TIMEOUT (flag cleared) when a wait of their own launches ran out; with 0 they stay
+ * asynchronous.  A change of n_polls drops the plan's captured graphs (they are captured
+ * again on next use).  Host only.  No counterpart in the paper. */
+mm_status mm_plan_set_wait_policy(mm_plan p, int n_polls, int check_on_return);
 
 /* The work list of the fused iteration kernel for a batch of `count` chunks whose complex
  * length is m1 x m2 (m1 a power of two, m2 a multiple of 16): per item (kind, chunk, index)
@@ -367,8 +382,10 @@ mm_status mm_plan_maps(mm_plan p, int32_t* hits, uint8_t* valid, double* weight,
  * device inputs; map_out is device float64 [n_pix][ncomp].  No workspace: the FP64
  * accumulators sit in one fixed device array of 2^18 pixels x 9 doubles (18.9 MB) that
  * every GPU loading the library keeps until the process exits; n_pix > 262144 returns
- * MM_ERR_ARG.  The first call on a device looks up that array's address on the current
- * device, so make the first call before any stream capture.  Each call clears the part of
+ * MM_ERR_ARG, and so does rcond_min outside [0, 1] (or NaN).  A call outside stream capture
+ * looks up that array's address on the current device; a call during capture reuses the
+ * last address found on that device, so make the first call on a device before any stream
+ * capture (otherwise MM_ERR_CUDA).  Each call clears the part of
  * the array it uses; all calls on a device share the one array, so calls whose kernels
  * overlap on the GPU (e.g. on two streams) race.  Asynchronous on `stream`. */
 mm_status mm_binned_map_noalloc(const int32_t* pix, const void* cos2psi, const void* sin2psi,

@@ -53,6 +53,7 @@ SIGNATURES = {
     "mm_messenger_adjoint_ckpt": (ctypes.c_int, [_vp, _dp, ctypes.c_int, _vp, _vp, _vp, _vp,
                                                  ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "mm_plan_fault_flags": (ctypes.c_int, [_vp, _ip, _vp]),
+    "mm_plan_set_wait_policy": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "mm_check_bounded_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip, _vp]),
     "mm_fused_item_list": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip,
                                           ctypes.c_int, _ip]),
@@ -254,6 +255,12 @@ class Plan:
                                                                  _stream(stream)))
         return f.value
 
+    def set_wait_policy(self, n_polls: int = 1 << 22, check_on_return: bool = False):
+        """Poll limit of the fused launch's bounded waits and whether the solver calls
+        synchronise and raise MMError(MM_ERR_TIMEOUT) when one of them ran out."""
+        _check("mm_plan_set_wait_policy", load().mm_plan_set_wait_policy(
+            self._h, int(n_polls), int(bool(check_on_return))))
+
     def n_fused_batches(self) -> int:
         n = ctypes.c_int()
         _check("mm_plan_fused_batches", load().mm_plan_fused_batches(self._h, ctypes.byref(n)))
@@ -438,11 +445,39 @@ def plan_from_synth(s: dict, device="cuda:0", rcond_min: float = 1e-3, tau=None,
 def binned_map_noalloc(pix, cos2psi, sin2psi, tod, n_pix: int, ncomp: int, map_out,
                        rcond_min: float = 1e-3, stream=None):
     """(P^T P)^-1 P^T d per pixel with no device allocation by the library (its scratch is a
-    fixed device array of 2^18 pixels); for callers that must not allocate."""
+    fixed device array of 2^18 pixels); for callers that must not allocate.  The tensors are
+    checked here (types, sizes, contiguity, one CUDA device) before any pointer is passed,
+    because the kernels trust the sizes they are given."""
     import torch
-    wd = MM_W_F16 if (cos2psi is not None and cos2psi.dtype == torch.float16) else MM_W_F32
+    n = int(pix.numel())
+    ts = [t for t in (pix, cos2psi, sin2psi, tod, map_out) if t is not None]
+    if not all(isinstance(t, torch.Tensor) for t in ts):
+        raise TypeError("binned_map_noalloc: every array must be a torch tensor")
+    if pix.dtype != torch.int32:
+        raise TypeError("binned_map_noalloc: pix must be int32")
+    if tod.dtype != torch.float32 or tod.numel() != n:
+        raise ValueError("binned_map_noalloc: tod must be float32 with pix.numel() elements")
+    if ncomp not in (1, 3):
+        raise ValueError("binned_map_noalloc: ncomp must be 1 or 3")
+    if map_out.dtype != torch.float64 or map_out.numel() < int(n_pix) * int(ncomp):
+        raise ValueError("binned_map_noalloc: map_out must be float64 with >= n_pix * ncomp "
+                         "elements")
+    if (ncomp == 3) != (cos2psi is not None and sin2psi is not None):
+        raise ValueError("binned_map_noalloc: cos2psi and sin2psi are given iff ncomp == 3")
+    wd = MM_W_F32
+    if ncomp == 3:
+        if cos2psi.dtype != sin2psi.dtype or cos2psi.dtype not in (torch.float32, torch.float16):
+            raise TypeError("binned_map_noalloc: cos2psi and sin2psi must both be float32 or "
+                            "both float16")
+        if cos2psi.numel() != n or sin2psi.numel() != n:
+            raise ValueError("binned_map_noalloc: cos2psi and sin2psi need pix.numel() elements")
+        wd = MM_W_F16 if cos2psi.dtype == torch.float16 else MM_W_F32
+    if any(not t.is_cuda for t in ts) or len({t.device for t in ts}) != 1:
+        raise ValueError("binned_map_noalloc: every tensor must be on one CUDA device")
+    if any(not t.is_contiguous() for t in ts):
+        raise ValueError("binned_map_noalloc: every tensor must be contiguous")
     _check("mm_binned_map_noalloc", load().mm_binned_map_noalloc(
-        _ptr(pix), _ptr(cos2psi), _ptr(sin2psi), wd, _ptr(tod), int(pix.numel()), int(n_pix),
+        _ptr(pix), _ptr(cos2psi), _ptr(sin2psi), wd, _ptr(tod), n, int(n_pix),
         int(ncomp), float(rcond_min), _ptr(map_out), _stream(stream)))
 
 

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse_adjoint(C
     const ChunkDesc d = q.desc[c];
     const int cb = t % tpc;
     smem_fft<M1, CB, ColLayout<CB>, T, +1>(sm, q.g.tw_col,
-                                           SrcY{q.ybuf + (int64_t)ci * d.M, cb * CB, M2});
+                                           SrcY<>{q.ybuf + (int64_t)ci * d.M, cb * CB, M2});
     const int64_t tbase = d.off + (int64_t)cb * NS;
     const float itau = (float)(1.0 / d.tau);
     float dot = 0.f;
@@ -389,6 +389,7 @@ static cudaError_t col_adjoint_m1(const mm_plan_s* p, const Batch& b, const AdjC
   q.ybuf = p->ybuf;
   q.acc = p->acc;
   q.acc_stride = acc_stride_of(p->n_pix, p->ncomp);
+  static_assert(col_cb(M1) == kColCB, "the adjoint takes chunks of at most 2^22 samples");
   const int ntiles = (g.M2 / kColCB) * b.count;
   const size_t smem = sizeof(float2) * M1 * kColCB;
   int grid = 0;
@@ -415,7 +416,6 @@ static cudaError_t col_adjoint(const mm_plan_s* p, const Batch& b, const AdjColE
     case 128: return col_adjoint_m1<128, THETA>(p, b, x, st);
     case 256: return col_adjoint_m1<256, THETA>(p, b, x, st);
     case 512: return col_adjoint_m1<512, THETA>(p, b, x, st);
-    case 1024: return col_adjoint_m1<1024, THETA>(p, b, x, st);
   }
   return cudaErrorInvalidValue;
 }

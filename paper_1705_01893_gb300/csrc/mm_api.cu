@@ -89,7 +89,9 @@ cudaError_t mm::resident_ctas(const void* kernel, int threads, size_t smem, int*
 
 // ------------------------------------------------------------------------ FFT shapes
 // M = 2^p complex points per chunk (n = 2M real samples): columns M1, rows M2 = M / M1.
-// Rows stay <= 8192 (two rows in shared memory), columns <= 1024.
+// Columns up to 512 points, then rows stay at 4096 (a row pair in 64 KB of shared memory,
+// two CTAs per SM) and the columns grow to 1024 and 2048 points (tiles of 8 and 4 columns,
+// also 64 KB).
 static bool fft_shape(int64_t n, int* M, int* M1, int* M2) {
   if (n < 512 || (n & 1)) return false;
   const int64_t m = n / 2;
@@ -97,9 +99,10 @@ static bool fft_shape(int64_t n, int* M, int* M1, int* M2) {
   int p = 0;
   while ((int64_t(1) << p) < m) ++p;
   if (p < 8 || p > 23) return false;
+  constexpr int kRowLog = 12;
   int lo = p / 2;
   if (lo > 9) lo = 9;
-  if (p - lo > 13) lo = p - 13;
+  if (p - lo > kRowLog) lo = p - kRowLog;
   *M = (int)m;
   *M1 = 1 << lo;
   *M2 = (int)(m >> lo);
@@ -1116,6 +1119,8 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
   p->fused_items = reinterpret_cast<int2*>(ws + L.fitems);
   p->fused_ctr = reinterpret_cast<unsigned*>(ws + L.fctr);
   p->fault = reinterpret_cast<int*>(ws + L.fault);
+  p->wait_polls = 1 << 22;
+  p->check_on_return = 0;
   p->h_fused_first = nullptr;
   p->h_fused_n = nullptr;
   p->scal = reinterpret_cast<double*>(ws + L.scal);
@@ -1466,6 +1471,8 @@ static mm_status load_map(mm_plan p, const double* map, cudaStream_t s) {
   return MM_OK;
 }
 
+static mm_status check_waits(mm_plan p, cudaStream_t s, const char* who);
+
 extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int n_iter, int precision,
                                           double* map_inout, double* chi2_out, void* stream) {
   MmRange nvtx_range_("mm_messenger_iterate");
@@ -1512,7 +1519,7 @@ extern "C" mm_status mm_messenger_iterate(mm_plan p, const double* lambdas, int 
     else k_bin_apply<1><<<blocks_for(p->n_pix, 256), 256, 0, s>>>(p->n_pix, p->acc, p->W, p->map4, mo);
     LAUNCHED("k_bin_apply");
   }
-  return MM_OK;
+  return check_waits(p, s, "mm_messenger_iterate");
 }
 
 mm_status mm::messenger_step_keep(mm_plan_s* p, double lambda, double* map_inout, float2* keep,
@@ -1672,7 +1679,7 @@ extern "C" mm_status mm_messenger_iterate_md(mm_plan p, const double* lambdas, i
       k_bin_md<1><<<nbp, 256, 0, s>>>(p->n_pix, p->acc, p->W, mdl, p->map4, mo, p->bvec, p->scal + kScalCdd, cn);
     LAUNCHED("k_bin_md");
   }
-  return MM_OK;
+  return check_waits(p, s, "mm_messenger_iterate_md");
 }
 
 extern "C" mm_status mm_plan_fault_flags(mm_plan p, int* flags, void* stream) {
@@ -1683,6 +1690,34 @@ extern "C" mm_status mm_plan_fault_flags(mm_plan p, int* flags, void* stream) {
   MM_CUDA(cudaStreamSynchronize(s));
   MM_CUDA(cudaMemsetAsync(p->fault, 0, sizeof(int), s));
   *flags = f;
+  return MM_OK;
+}
+
+// With the plan's check-on-return policy: synchronise `s` and report a bounded wait that
+// ran out in the launches queued so far (MM_ERR_TIMEOUT; the flag is cleared).
+static mm_status check_waits(mm_plan p, cudaStream_t s, const char* who) {
+  if (!p->check_on_return) return MM_OK;
+  int f = 0;
+  MM_CUDA(cudaMemcpyAsync(&f, p->fault, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MM_CUDA(cudaStreamSynchronize(s));
+  if (f) {
+    MM_CUDA(cudaMemsetAsync(p->fault, 0, sizeof(int), s));
+    mm_set_error("%s: a bounded wait of the fused launch ran out (its results are wrong)", who);
+    return MM_ERR_TIMEOUT;
+  }
+  return MM_OK;
+}
+
+extern "C" mm_status mm_plan_set_wait_policy(mm_plan p, int n_polls, int check_on_return) {
+  MM_ARG(p != nullptr, "plan is NULL");
+  MM_ARG(n_polls >= 1 && n_polls <= (1 << 22), "n_polls must be in [1, 2^22]");
+  MM_ARG(check_on_return == 0 || check_on_return == 1, "check_on_return must be 0 or 1");
+  if (n_polls != p->wait_polls) {   // captured graphs hold the old limit: capture again
+    if (p->graph_exec) { cudaGraphExecDestroy(p->graph_exec); p->graph_exec = nullptr; }
+    if (p->adapt_exec) { cudaGraphExecDestroy(p->adapt_exec); p->adapt_exec = nullptr; }
+  }
+  p->wait_polls = n_polls;
+  p->check_on_return = check_on_return;
   return MM_OK;
 }
 
@@ -1942,7 +1977,7 @@ extern "C" mm_status mm_messenger_adaptive(mm_plan p, const double* levels, int 
                           cudaMemcpyDeviceToDevice, s));
   MM_CUDA(cudaMemcpyAsync(n_done, reinterpret_cast<char*>(p->adapt_st) + offsetof(AdaptState, n_done),
                           sizeof(int), cudaMemcpyDeviceToDevice, s));
-  return MM_OK;
+  return check_waits(p, s, "mm_messenger_adaptive");
 }
 
 extern "C" mm_status mm_messenger_graph(mm_plan p, const double* lambdas, int n_iter,
@@ -1971,7 +2006,7 @@ extern "C" mm_status mm_messenger_graph(mm_plan p, const double* lambdas, int n_
   for (int it = 0; it < n_iter; ++it) MM_CUDA(cudaGraphLaunch(p->graph_exec, s));
   MM_CUDA(cudaMemcpyAsync(map_inout, p->map64, sizeof(double) * p->ncomp * p->n_pix,
                           cudaMemcpyDeviceToDevice, s));
-  return MM_OK;
+  return check_waits(p, s, "mm_messenger_graph");
 }
 
 extern "C" mm_status mm_pcg_state_bytes(mm_plan p, size_t* bytes) {
@@ -2042,7 +2077,7 @@ extern "C" mm_status mm_pcg_iterate(mm_plan p, int n_iter, double* map_inout, vo
     // rz_cur <- rz_next for the next iteration
     MM_CUDA(cudaMemcpyAsync(sc + kPcgRz0, sc + kPcgRz1, sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  return MM_OK;
+  return check_waits(p, s, "mm_pcg_iterate");
 }
 
 extern "C" mm_status mm_chi2(mm_plan p, const double* map, double lambda, double* chi2_dev, void* stream) {

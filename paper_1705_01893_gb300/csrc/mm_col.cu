@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_forward(ColParams
     const ChunkDesc d = q.desc[q.chunks[ci]];
     const int cb = t % tpc;
     const int j2_0 = cb * CB;
-    const DstY dst{q.ybuf + (int64_t)ci * d.M, &q.g, j2_0, M2};
+    const DstY<true> dst{q.ybuf + (int64_t)ci * d.M, &q.g, j2_0, M2};
     if constexpr (SRC == kSrcTod)
       smem_fft<M1, CB, ColLayout<CB>, T, -1>(sm, q.g.tw_col,
                                              SrcTod{q.tod, d.off + 2ll * j2_0, M2}, dst);
@@ -41,21 +41,27 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse(ColParams
   const int ntiles = q.count * tpc;
   constexpr int RUN = 2 * CB;
   constexpr int NS = M1 * RUN;
-  static_assert(RUN == 32 && (NS / 4) % T == 0 && T % 32 == 0,
-                "rows of 8 lanes and a warp-uniform scatter loop");
+  constexpr int ROWL = RUN / 4;   // lanes per row of the tile (4 samples per lane)
+  static_assert((RUN == 32 || RUN == 16 || RUN == 8) && (NS / 4) % T == 0 && T % 32 == 0,
+                "rows of 8, 4 or 2 lanes and a warp-uniform scatter loop");
+  using Lay = ColLayout<CB>;
   const float* smf = reinterpret_cast<const float*>(sm);
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int ci = t / tpc;
     const ChunkDesc d = q.desc[q.chunks[ci]];
     const int cb = t % tpc;
     smem_fft<M1, CB, ColLayout<CB>, T, +1>(sm, q.g.tw_col,
-                                           SrcY{q.ybuf + (int64_t)ci * d.M, cb * CB, M2});
+                                           SrcY<true>{q.ybuf + (int64_t)ci * d.M, cb * CB, M2});
     // tile-ordered pointing: the tile's samples are contiguous, in the same order as t
     const int64_t tbase = d.off + (int64_t)cb * NS;
 #pragma unroll 4
     for (int e4 = threadIdx.x; e4 < NS / 4; e4 += T) {
       const int e = 4 * e4;
-      scatter4<NC>(q, tbase + e, *reinterpret_cast<const float4*>(smf + e), e4 & 7);
+      // sample e = 2 (i CB + b) + h sits at float 2 Lay::at(b, i) + h; a lane's 4 samples
+      // lie in one row i
+      const int i = e / RUN;
+      const int so = e + (Lay::kPad ? 2 * (i >> 4) * Lay::kPad : 0);
+      scatter4<NC, ROWL>(q, tbase + e, *reinterpret_cast<const float4*>(smf + so), e4 & (ROWL - 1));
     }
     __syncthreads();
   }
@@ -65,7 +71,8 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_col_inverse(ColParams
 
 
 // Copy the caller's pointing into tile order: sample 2 (j1 M2 + j2) + h of a chunk goes to
-// cb (2 CB M1) + j1 (2 CB) + 2 (j2 - cb CB) + h with cb = j2 / CB.  Coalesced writes.
+// cb (2 CB M1) + j1 (2 CB) + 2 (j2 - cb CB) + h with cb = j2 / CB (CB = col_cb(M1), the
+// column kernels' tile width).  Coalesced writes.
 template <int CB>
 __global__ void k_tile_pointing(const int32_t* __restrict__ pix, const void* cosw, const void* sinw,
                                 int wbytes, int64_t off, int M1, int M2, int32_t* __restrict__ tpix,
@@ -95,8 +102,15 @@ cudaError_t launch_tile_pointing(const mm_plan_s* p, cudaStream_t st) {
     const ChunkDesc& d = p->h_desc[c];
     if (p->groups[d.grp].general) continue;   // the general path reads the caller's order
     const int64_t n = d.n;
-    k_tile_pointing<kColCB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-        p->pix, p->cosw, p->sinw, wb, d.off, d.M1, d.M2, p->tpix, p->tcos, p->tsin);
+    if (col_cb(d.M1) == 4)
+      k_tile_pointing<4><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+          p->pix, p->cosw, p->sinw, wb, d.off, d.M1, d.M2, p->tpix, p->tcos, p->tsin);
+    else if (col_cb(d.M1) == 8)
+      k_tile_pointing<8><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+          p->pix, p->cosw, p->sinw, wb, d.off, d.M1, d.M2, p->tpix, p->tcos, p->tsin);
+    else
+      k_tile_pointing<kColCB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+          p->pix, p->cosw, p->sinw, wb, d.off, d.M1, d.M2, p->tpix, p->tcos, p->tsin);
   }
   return cudaGetLastError();
 }
@@ -129,21 +143,22 @@ template <int M1>
 static cudaError_t col_forward_m1(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                   const void* map4, float2* ybuf, cudaStream_t st) {
   constexpr int kColT = col_threads(M1);
+  constexpr int CB = col_cb(M1);
   const ColParams q = make_params(p, b, tod, map4, ybuf);
-  const int ntiles = (q.g.M2 / kColCB) * b.count;
-  const size_t smem = sizeof(float2) * M1 * kColCB;
+  const int ntiles = (q.g.M2 / CB) * b.count;
+  const size_t smem = sizeof(float2) * ColLayout<CB>::size(M1);
   cudaError_t e;
   int grid = 0;
   if (src == kSrcTod) {
-    auto k = k_col_forward<M1, kColCB, kColT, 1, kSrcTod>;
+    auto k = k_col_forward<M1, CB, kColT, 1, kSrcTod>;
     if ((e = persistent_grid(k, kColT, smem, ntiles, &grid)) != cudaSuccess) return e;
     k<<<grid, kColT, smem, st>>>(q);
   } else if (p->ncomp == 3) {
-    auto k = k_col_forward<M1, kColCB, kColT, 3, kSrcGather>;
+    auto k = k_col_forward<M1, CB, kColT, 3, kSrcGather>;
     if ((e = persistent_grid(k, kColT, smem, ntiles, &grid)) != cudaSuccess) return e;
     k<<<grid, kColT, smem, st>>>(q);
   } else {
-    auto k = k_col_forward<M1, kColCB, kColT, 1, kSrcGather>;
+    auto k = k_col_forward<M1, CB, kColT, 1, kSrcGather>;
     if ((e = persistent_grid(k, kColT, smem, ntiles, &grid)) != cudaSuccess) return e;
     k<<<grid, kColT, smem, st>>>(q);
   }
@@ -153,17 +168,18 @@ static cudaError_t col_forward_m1(const mm_plan_s* p, const Batch& b, int src, c
 template <int M1>
 static cudaError_t col_inverse_m1(const mm_plan_s* p, const Batch& b, cudaStream_t st) {
   constexpr int kColT = col_threads(M1);
+  constexpr int CB = col_cb(M1);
   const ColParams q = make_params(p, b, nullptr);
-  const int ntiles = (q.g.M2 / kColCB) * b.count;
-  const size_t smem = sizeof(float2) * M1 * kColCB;
+  const int ntiles = (q.g.M2 / CB) * b.count;
+  const size_t smem = sizeof(float2) * ColLayout<CB>::size(M1);
   cudaError_t e;
   int grid = 0;
   if (p->ncomp == 3) {
-    auto k = k_col_inverse<M1, kColCB, kColT, 3>;
+    auto k = k_col_inverse<M1, CB, kColT, 3>;
     if ((e = persistent_grid(k, kColT, smem, ntiles, &grid)) != cudaSuccess) return e;
     k<<<grid, kColT, smem, st>>>(q);
   } else {
-    auto k = k_col_inverse<M1, kColCB, kColT, 1>;
+    auto k = k_col_inverse<M1, CB, kColT, 1>;
     if ((e = persistent_grid(k, kColT, smem, ntiles, &grid)) != cudaSuccess) return e;
     k<<<grid, kColT, smem, st>>>(q);
   }
@@ -190,6 +206,7 @@ cudaError_t launch_col_forward_ex(const mm_plan_s* p, const Batch& b, int src, c
     case 256: return col_forward_m1<256>(p, b, src, tod, map4, ybuf, st);
     case 512: return col_forward_m1<512>(p, b, src, tod, map4, ybuf, st);
     case 1024: return col_forward_m1<1024>(p, b, src, tod, map4, ybuf, st);
+    case 2048: return col_forward_m1<2048>(p, b, src, tod, map4, ybuf, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -205,6 +222,7 @@ cudaError_t launch_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t 
     case 256: return col_inverse_m1<256>(p, b, st);
     case 512: return col_inverse_m1<512>(p, b, st);
     case 1024: return col_inverse_m1<1024>(p, b, st);
+    case 2048: return col_inverse_m1<2048>(p, b, st);
   }
   return cudaErrorInvalidValue;
 }

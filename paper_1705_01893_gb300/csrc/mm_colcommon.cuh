@@ -69,24 +69,27 @@ __device__ __forceinline__ float4 gather4(const ColParams& q, int64_t s) {
 // binning launch, which is bound by L2 reduction requests).
 template <int NC>
 __device__ __forceinline__ void emit_run(double* acc, int64_t stride, int p, float a0, float a1,
-                                         float a2) {
+                                         float a2, uint64_t pol) {
   if (p < 0) return;
   double* a = acc + p;
-  atomicAdd(a, f32_to_f64(a0));
+  red_add_f64(a, f32_to_f64(a0), pol);
   if constexpr (NC == 3) {
-    atomicAdd(a + stride, f32_to_f64(a1));
-    atomicAdd(a + 2 * stride, f32_to_f64(a2));
+    red_add_f64(a + stride, f32_to_f64(a1), pol);
+    red_add_f64(a + 2 * stride, f32_to_f64(a2), pol);
   }
 }
 
-// P^T t for samples s..s+3 (t4 = t_s..t_s+3), one lane of a row of 8 lanes (32 samples).
+// P^T t for samples s..s+3 (t4 = t_s..t_s+3), one lane of a row of ROWL lanes (4 ROWL
+// consecutive samples; ROWL = 8, 4 or 2, a power of two dividing the warp).
 // Reduce by pixel: runs inside the lane are summed in registers; runs that cross lanes are
 // closed by a linear-recurrence scan over the lanes of the row (S_u = X_u + G_u S_{u+1},
 // X_u = the lane's leading run when it continues the previous lane's trailing run, G_u = the
 // lane is one such run and the next lane continues it).  Each run's first sample's lane
 // issues one FP64 add per component.
-template <int NC>
+template <int NC, int ROWL = 8>
 __device__ __forceinline__ void scatter4(const ColParams& q, int64_t s, float4 t4, int qpos) {
+  static_assert(ROWL == 2 || ROWL == 4 || ROWL == 8, "rows of 2, 4 or 8 lanes");
+  const uint64_t pol = l2_policy_evict_last();
   const int4 p4 = __ldcs(reinterpret_cast<const int4*>(q.pix + s));
   const int p[4] = {p4.x, p4.y, p4.z, p4.w};
   const float tv[4] = {t4.x, t4.y, t4.z, t4.w};
@@ -123,9 +126,9 @@ __device__ __forceinline__ void scatter4(const ColParams& q, int64_t s, float4 t
   float S[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) S[k] = cont ? lead[k] : 0.f;
-  bool Gs = cont && single && qpos != 7;
+  bool Gs = cont && single && qpos != ROWL - 1;
 #pragma unroll
-  for (int d = 1; d < 8; d <<= 1) {
+  for (int d = 1; d < ROWL; d <<= 1) {
     float Sd[3];
 #pragma unroll
     for (int k = 0; k < NC; ++k) Sd[k] = __shfl_down_sync(0xffffffffu, S[k], d);
@@ -140,17 +143,17 @@ __device__ __forceinline__ void scatter4(const ColParams& q, int64_t s, float4 t
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     const float cd = __shfl_down_sync(0xffffffffu, S[k], 1);
-    carry[k] = qpos != 7 ? cd : 0.f;
+    carry[k] = qpos != ROWL - 1 ? cd : 0.f;
   }
   if (!(single && cont))
-    emit_run<NC>(q.acc, q.acc_stride, p[3], trail[0] + carry[0], trail[1] + carry[1], trail[2] + carry[2]);
-  if (!cont && !single) emit_run<NC>(q.acc, q.acc_stride, p[0], lead[0], lead[1], lead[2]);
+    emit_run<NC>(q.acc, q.acc_stride, p[3], trail[0] + carry[0], trail[1] + carry[1], trail[2] + carry[2], pol);
+  if (!cont && !single) emit_run<NC>(q.acc, q.acc_stride, p[0], lead[0], lead[1], lead[2], pol);
   if (b1 && l > 1) {   // middle run [1, e)
     const bool two = b2;
     emit_run<NC>(q.acc, q.acc_stride, p[1], two ? v[0][1] : v[0][1] + v[0][2], two ? v[1][1] : v[1][1] + v[1][2],
-                 two ? v[2][1] : v[2][1] + v[2][2]);
+                 two ? v[2][1] : v[2][1] + v[2][2], pol);
   }
-  if (b2 && l > 2) emit_run<NC>(q.acc, q.acc_stride, p[2], v[0][2], v[1][2], v[2][2]);
+  if (b2 && l > 2) emit_run<NC>(q.acc, q.acc_stride, p[2], v[0][2], v[1][2], v[2][2], pol);
 }
 
 // First-pass sources and last-pass sink of the column DFTs.  Element (b, i) of a tile is
@@ -187,23 +190,33 @@ struct SrcTod {      // z = (d_s, d_s+1)
   }
 };
 
-struct DstY {        // y[k1][j2] = Z * w_M^(k1 j2): the four-step twiddle on the way out
+// y[k1][j2] = Z * w_M^(k1 j2): the four-step twiddle on the way out.  kStream: the
+// intermediate is written with evict-first priority (separate pass kernels, whose next
+// reader comes a whole batch later), leaving L2 to the map and the accumulators.
+template <bool kStream = false>
+struct DstY {
   float2* y;
   const Group* g;
   int j2_0;
   int M2;
   __device__ __forceinline__ void operator()(int b, int k1, float2 v) const {
     const int j2 = j2_0 + b;
-    y[(int64_t)k1 * M2 + j2] = cmul(v, tw_big(*g, k1 * j2));
+    const float2 o = cmul(v, tw_big(*g, k1 * j2));
+    if constexpr (kStream) __stcs(y + (int64_t)k1 * M2 + j2, o);
+    else y[(int64_t)k1 * M2 + j2] = o;
   }
 };
 
-struct SrcY {        // filtered spectrum rows for the inverse column DFTs
+// Filtered spectrum rows for the inverse column DFTs.  kStream: the last read of the
+// intermediate (separate pass kernel), evict-first; otherwise L2 only, because in the fused
+// iteration kernel other CTAs wrote these rows in this launch.
+template <bool kStream = false>
+struct SrcY {
   const float2* y;
   int j2_0;
   int M2;
   __device__ __forceinline__ float2 operator()(int b, int k1) const {
-    // L2 only: in the fused iteration kernel other CTAs wrote these rows in this launch
+    if constexpr (kStream) return __ldcs(y + (int64_t)k1 * M2 + j2_0 + b);
     return __ldcg(y + (int64_t)k1 * M2 + j2_0 + b);
   }
 };

@@ -26,6 +26,7 @@ struct FusedParams {
   unsigned* ctr;          // [0] queue, [1] CTAs done, [2, 2 + count) A tiles done per chunk,
                           // [2 + count, 2 + 2 count) B jobs done per chunk; zero between launches
   int* fault;
+  int n_polls;            // poll limit of each wait (the plan's wait policy)
 };
 
 enum { kItemA = 0, kItemB = 1, kItemC = 2 };
@@ -54,7 +55,8 @@ __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
   // chunks this CTA has already seen complete (A tiles, B jobs): no second acquire poll
   constexpr int kMaskWords = 64;
   __shared__ unsigned s_mask[2][kMaskWords];
-  static_assert(M1 * CB <= 2 * M2, "column tiles share the row jobs' buffer");
+  // the launch sizes the dynamic buffer for the larger of a row-pair job (2 M2 words) and a
+  // column tile (ColLayout<CB>::size(M1) words)
   // The row twiddles stay in global memory (L1 / L2): staging them in shared memory, as the
   // row kernel does, would take the shared-memory reservation of every item from 64 to
   // 100 KB, and the column items lose the L1 their map gathers hit (measured: a separate
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
         const int m = kind == kItemB ? 0 : 1;
         const bool cached = ci < 32 * kMaskWords && ((s_mask[m][ci >> 5] >> (ci & 31)) & 1u);
         if (!cached) {
-          wait_count((m == 0 ? doneA : doneB) + ci, m == 0 ? nA : nB, q.fault);
+          wait_count((m == 0 ? doneA : doneB) + ci, m == 0 ? nA : nB, q.fault, q.n_polls);
           if (ci < 32 * kMaskWords) s_mask[m][ci >> 5] |= 1u << (ci & 31);
         }
       }
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
     __syncthreads();
     const ChunkDesc d = q.c.desc[q.c.chunks[ci]];
     if (kind == kItemA) {
-      const DstY dst{q.c.ybuf + (int64_t)ci * d.M, &q.c.g, idx * CB, M2};
+      const DstY<> dst{q.c.ybuf + (int64_t)ci * d.M, &q.c.g, idx * CB, M2};
       smem_fft<M1, CB, ColLayout<CB>, T, -1>(
           sm, q.c.g.tw_col, SrcGather<NC, CB>{&q.c, d.off + (int64_t)idx * (2 * CB * M1)}, dst);
     } else if (kind == kItemB) {
@@ -107,15 +109,18 @@ __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
       }
       kernel_body_job<M2, T, MODE>(q.r, sm, tws, red, ci, idx);
     } else {
-      constexpr int NS = M1 * 2 * CB;
+      constexpr int RUN = 2 * CB, NS = M1 * RUN, ROWL = RUN / 4;
+      using Lay = ColLayout<CB>;
       const float* smf = reinterpret_cast<const float*>(sm);
-      smem_fft<M1, CB, ColLayout<CB>, T, +1>(sm, q.c.g.tw_col,
-                                             SrcY{q.c.ybuf + (int64_t)ci * d.M, idx * CB, M2});
+      smem_fft<M1, CB, Lay, T, +1>(sm, q.c.g.tw_col,
+                                   SrcY<>{q.c.ybuf + (int64_t)ci * d.M, idx * CB, M2});
       const int64_t tbase = d.off + (int64_t)idx * NS;
 #pragma unroll 2
       for (int e4 = threadIdx.x; e4 < NS / 4; e4 += T) {
         const int e = 4 * e4;
-        scatter4<NC>(q.c, tbase + e, *reinterpret_cast<const float4*>(smf + e), e4 & 7);
+        const int so = e + (Lay::kPad ? 2 * ((e / RUN) >> 4) * Lay::kPad : 0);
+        scatter4<NC, ROWL>(q.c, tbase + e, *reinterpret_cast<const float4*>(smf + so),
+                           e4 & (ROWL - 1));
       }
     }
     // release the intermediate rows written by an A tile or a B job before its count
@@ -141,10 +146,11 @@ __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
   }
 }
 
-// The fused path covers the shape instantiated here: chunks of 2^22 samples (M = 2^21 =
-// 512 x 4096), the column and row passes both at 512 threads.
+// The fused path covers the shapes instantiated here, whose column tiles and row-pair jobs
+// both take 512 threads and about 64 KB: rows of 4096 points with columns of 512 (chunks of
+// 2^22 samples, 16-column tiles), 1024 (2^23, 8 columns) and 2048 points (2^24, 4 columns).
 static bool fused_shape(int M1, int M2, bool general) {
-  return !general && M1 == 512 && M2 == 4096;
+  return !general && M2 == 4096 && (M1 == 512 || M1 == 1024 || M1 == 2048);
 }
 
 bool fused_eligible(const mm_plan_s* p, const Batch& b) {
@@ -154,7 +160,7 @@ bool fused_eligible(const mm_plan_s* p, const Batch& b) {
 }
 
 int fused_items_per_chunk(int M1, int M2, bool general) {
-  return fused_shape(M1, M2, general) ? 2 * (M2 / kColCB) + M1 / 2 + 1 : 0;
+  return fused_shape(M1, M2, general) ? 2 * (M2 / col_cb(M1)) + M1 / 2 + 1 : 0;
 }
 
 // Item list of a batch of `count` chunks: step s has the A tiles of chunk s, the B jobs of
@@ -166,7 +172,7 @@ int fused_items_per_chunk(int M1, int M2, bool general) {
 // three launches (A + B + C = 465 us) is their tails and the gaps between them.
 int fused_build_items(int M1, int M2, int count, int2* out) {
   constexpr int kLagAB = 2, kLagBC = 3;
-  const int nA = M2 / kColCB, nB = M1 / 2 + 1, nC = nA;
+  const int nA = M2 / col_cb(M1), nB = M1 / 2 + 1, nC = nA;
   int n = 0;
   for (int s = 0; s < count + kLagAB + kLagBC; ++s) {
     const int ca = s, cb = s - kLagAB, cc = s - kLagAB - kLagBC;
@@ -182,6 +188,15 @@ int fused_build_items(int M1, int M2, int count, int2* out) {
   return n;
 }
 
+template <int M1, int NC>
+static void (*fused_kernel(int mode))(FusedParams) {
+  constexpr int CB = col_cb(M1);
+  if (mode == kRowMessenger) return k_fused<M1, 4096, CB, 512, NC, kRowMessenger>;
+  if (mode == kRowMessengerF) return k_fused<M1, 4096, CB, 512, NC, kRowMessengerF>;
+  if (mode == kRowPcgApply) return k_fused<M1, 4096, CB, 512, NC, kRowPcgApply>;
+  return nullptr;
+}
+
 // a.mode: kRowMessenger, kRowMessengerF or kRowPcgApply.
 cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st) {
   const int bi = (int)(&b - p->h_batches);
@@ -193,18 +208,27 @@ cudaError_t launch_fused(const mm_plan_s* p, const Batch& b, const RowArgs& a, c
   q.n_items = p->h_fused_n[bi];
   q.ctr = p->fused_ctr;
   q.fault = p->fault;
-  const size_t smem = sizeof(float2) * 2 * g.M2;
+  q.n_polls = p->wait_polls;
+  // the row jobs' two rows and the (padded) column tile share one buffer
+  size_t words = 2 * (size_t)g.M2;
   void (*k)(FusedParams) = nullptr;
-  if (p->ncomp == 3) {
-    if (a.mode == kRowMessenger) k = k_fused<512, 4096, kColCB, 512, 3, kRowMessenger>;
-    if (a.mode == kRowMessengerF) k = k_fused<512, 4096, kColCB, 512, 3, kRowMessengerF>;
-    if (a.mode == kRowPcgApply) k = k_fused<512, 4096, kColCB, 512, 3, kRowPcgApply>;
-  } else {
-    if (a.mode == kRowMessenger) k = k_fused<512, 4096, kColCB, 512, 1, kRowMessenger>;
-    if (a.mode == kRowMessengerF) k = k_fused<512, 4096, kColCB, 512, 1, kRowMessengerF>;
-    if (a.mode == kRowPcgApply) k = k_fused<512, 4096, kColCB, 512, 1, kRowPcgApply>;
+  const bool iqu = p->ncomp == 3;
+  switch (g.M1) {
+    case 512:
+      k = iqu ? fused_kernel<512, 3>(a.mode) : fused_kernel<512, 1>(a.mode);
+      words = words > (size_t)ColLayout<col_cb(512)>::size(512) ? words : ColLayout<col_cb(512)>::size(512);
+      break;
+    case 1024:
+      k = iqu ? fused_kernel<1024, 3>(a.mode) : fused_kernel<1024, 1>(a.mode);
+      words = words > (size_t)ColLayout<col_cb(1024)>::size(1024) ? words : ColLayout<col_cb(1024)>::size(1024);
+      break;
+    case 2048:
+      k = iqu ? fused_kernel<2048, 3>(a.mode) : fused_kernel<2048, 1>(a.mode);
+      words = words > (size_t)ColLayout<col_cb(2048)>::size(2048) ? words : ColLayout<col_cb(2048)>::size(2048);
+      break;
   }
-  if (k == nullptr) return cudaErrorInvalidValue;
+  if (k == nullptr || g.M2 != 4096) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * words;
   int grid = 0;
   cudaError_t e = persistent_grid(k, 512, smem, q.n_items, &grid);
   if (e != cudaSuccess) return e;
@@ -226,12 +250,12 @@ __global__ void k_wait_check(int n_polls) {
 extern "C" mm_status mm_fused_item_list(int m1, int m2, int count, int* out, int capacity,
                                         int* n_items) {
   using namespace mm;
-  if (!n_items || count < 1 || count > 0xffff || m1 < 2 || m2 < kColCB || (m2 % kColCB) != 0 ||
-      (m1 & (m1 - 1)) != 0) {
+  if (!n_items || count < 1 || count > 0xffff || m1 < 2 || m1 > 8192 || (m1 & (m1 - 1)) != 0 ||
+      m2 < col_cb(m1) || (m2 % col_cb(m1)) != 0) {
     mm_set_error("mm_fused_item_list: bad argument");
     return MM_ERR_ARG;
   }
-  const int per = 2 * (m2 / kColCB) + m1 / 2 + 1;
+  const int per = 2 * (m2 / col_cb(m1)) + m1 / 2 + 1;
   const int64_t total = (int64_t)per * count;
   *n_items = (int)total;
   if (!out) return MM_OK;

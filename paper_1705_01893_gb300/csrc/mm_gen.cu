@@ -410,7 +410,7 @@ __device__ __forceinline__ void gen_scatter(const GenParams& q, const ChunkDesc&
         const int so = __shfl_down_sync(0xffffffffu, seg, o);
         if (lane + o < 32 && so == seg) { v0 += a0; v1 += a1; v2 += a2; }
       }
-      if (head) emit_run<NC>(q.acc, q.acc_stride, p, v0, v1, v2);
+      if (head) emit_run<NC>(q.acc, q.acc_stride, p, v0, v1, v2, l2_policy_evict_last());
     }
   }
 }

@@ -171,6 +171,8 @@ struct mm_plan_s {
   int* h_fused_n;      // host [n_batches]: items of the batch's list, 0 = not fused
   unsigned* fused_ctr; // device [2 + 2 n_chunks], zero between launches
   int* fault;          // device flag: a bounded wait of a kernel expired
+  int wait_polls;      // poll limit of the fused launch's waits (default 2^22, about a second)
+  int check_on_return; // 1: the solver calls synchronise and report an expired wait
   double* scal;     // [64] scalars (see kScal*)
   double* params;   // [n_chunks][4] noise parameters (device copy)
   float2* tw_pool;
@@ -353,9 +355,17 @@ __device__ __forceinline__ void dftR(float2* v) {
 // ----------------------------------------------------------------- shared-memory layouts
 // Column layout: NB transforms interleaved, element (b, i) at s[i * NB + b]; with NB >= 16
 // consecutive b are consecutive 8-byte words, so every access of a pass is conflict-free.
+// Narrower tiles (NB = 8, 4) get one spare block of NB words after every 16 rows: the first
+// radix-16 pass stores the rows of a warp's butterflies 16 rows apart, which would
+// otherwise fall on the same banks; the spare block shifts each by 2 NB banks.
 template <int NB>
 struct ColLayout {
-  __device__ __forceinline__ static int at(int b, int i) { return i * NB + b; }
+  static constexpr int kPad = NB < 16 ? NB : 0;
+  __device__ __forceinline__ static int at(int b, int i) {
+    return i * NB + b + (kPad ? (i >> 4) * kPad : 0);
+  }
+  // float2 words of a tile of NB transforms of length L
+  __host__ __device__ static constexpr int size(int L) { return L * NB + (kPad ? (L >> 4) * kPad : 0); }
   static constexpr bool kBFast = true;
 };
 // Row layout: transform b occupies [b*L, (b+1)*L), XOR-swizzled in 16-word groups so the
@@ -474,6 +484,21 @@ __device__ __forceinline__ void smem_fft(float2* s, const float2* __restrict__ t
   fft_passes_io<L, NB, Lay, T, DIR, 1>(s, tw, src, dst);
 }
 
+// L2 eviction priority of the FP64 pixel accumulators: their reductions carry an
+// evict-last policy, so that the accumulators of a large map (100 MB at 4 M IQU pixels)
+// keep their lines in L2 against the streams of pointing and intermediate that pass
+// through it once per pass (read with evict-first loads).
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// *a += v (relaxed, device scope, performed in L2) with an L2 cache policy.
+__device__ __forceinline__ void red_add_f64(double* a, double v, uint64_t pol) {
+  asm volatile("red.relaxed.gpu.global.add.L2::cache_hint.f64 [%0], %1, %2;"
+               ::"l"(a), "d"(v), "l"(pol) : "memory");
+}
+
 // Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (p and bytes multiples of 16).
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -572,10 +597,15 @@ cudaError_t launch_gen_col_inverse(const mm_plan_s* p, const Batch& b, cudaStrea
 // Forward column pass gathering from `map4` into `ybuf` (either NULL = the plan's own).
 cudaError_t launch_col_forward_ex(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                   const void* map4, float2* ybuf, cudaStream_t st);
-// Threads of the column kernels for column length M1 (16 complex values per thread per pass).
+// Columns per tile of the column kernels: 16 (runs of 32 samples) up to 512-point columns,
+// then 8192 / M1 (8 for 1024, 4 for 2048 points), so that a tile stays at 64 KB and 512
+// threads: two CTAs per SM overlap one's loads with the other's DFT passes.
 constexpr int kColCB = 16;
+__host__ __device__ constexpr int col_cb(int M1) { return M1 <= 512 ? kColCB : 8192 / M1; }
+// Threads of the column kernels for column length M1 (16 complex values per thread per pass).
 __host__ __device__ constexpr int col_threads(int M1) {
-  return M1 * kColCB / 16 < 64 ? 64 : (M1 * kColCB / 16 > 1024 ? 1024 : M1 * kColCB / 16);
+  return M1 * col_cb(M1) / 16 < 64 ? 64
+         : (M1 * col_cb(M1) / 16 > 1024 ? 1024 : M1 * col_cb(M1) / 16);
 }
 
 }  // namespace mm

@@ -20,18 +20,26 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kMaxDevices] = {nullptr};
 
-// The device address of the scratch on the current device (looked up once per device).
-cudaError_t noalloc_scratch(double** out) {
+// The device address of the scratch on the current device.  Outside stream capture it is
+// looked up on every call (a host-side query once the module is loaded), so a context that
+// was reset and re-created, which may load the module at another address, is followed;
+// during capture the address of the last lookup on this device is used, which is why the
+// first call on a device must come before any capture.
+cudaError_t noalloc_scratch(cudaStream_t s, double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return e;
   std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_noalloc_ptr[dev] = static_cast<double*>(p);
+  } else if (!g_noalloc_ptr[dev]) {
+    return cudaErrorStreamCaptureUnsupported;
   }
   *out = g_noalloc_ptr[dev];
   return cudaSuccess;
@@ -143,18 +151,23 @@ extern "C" mm_status mm_binned_map_noalloc(const int32_t* pix, const void* cos2p
     mm_set_error("mm_binned_map_noalloc: bad weight_dtype %d", weight_dtype);
     return MM_ERR_ARG;
   }
+  if (!(rcond_min >= 0.0 && rcond_min <= 1.0)) {   // also rejects NaN
+    mm_set_error("mm_binned_map_noalloc: rcond_min must be in [0, 1]");
+    return MM_ERR_ARG;
+  }
   if (n_pix < 1 || n_pix > kNoallocMaxPix) {
     mm_set_error("mm_binned_map_noalloc: n_pix = %lld outside [1, %lld], the size of its "
                  "fixed scratch", (long long)n_pix, (long long)kNoallocMaxPix);
     return MM_ERR_ARG;
   }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   double* scratch = nullptr;
-  cudaError_t e = noalloc_scratch(&scratch);
+  cudaError_t e = noalloc_scratch(s, &scratch);
   if (e != cudaSuccess) {
-    mm_set_error("mm_binned_map_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    mm_set_error("mm_binned_map_noalloc: scratch address lookup failed: %s (the first call on "
+                 "a device must come before any stream capture)", cudaGetErrorString(e));
     return MM_ERR_CUDA;
   }
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t len = n_pix * kNoallocPerPix;   // the previous call's contents are cleared
   k_noalloc_clear<<<(unsigned)((len + 255) / 256 < 4096 ? (len + 255) / 256 : 4096), 256, 0, s>>>(
       scratch, len);

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(T, (T <= 512 ? 2 : 1)) k_row(RowParams q) {
         prefetch_l2(q.nbar + dn.spec + (int64_t)rb * M2, 4 * M2);
       }
     }
-    kernel_body_job<M2, T, MODE>(q, sm, tws, red, ci, job % jobs_pc);
+    kernel_body_job<M2, T, MODE, true>(q, sm, tws, red, ci, job % jobs_pc);
     __syncthreads();
     job = s_next;
     __syncthreads();

@@ -33,15 +33,20 @@ struct RowParams {
 
 // First pass of the forward row DFTs reads rows rA (b = 0) and rB (b = 1) straight from the
 // intermediate; the last inverse pass writes them back with the conjugate four-step twiddle.
+// kStream (separate row kernel): the rows are read and written back with evict-first
+// priority, their next use being a whole batch away; otherwise (fused iteration kernel)
+// they are read from L2 only, because other CTAs wrote them in this launch.
+template <bool kStream = false>
 struct SrcRows {
   const float2* y;
   int offA, offB;
   __device__ __forceinline__ float2 operator()(int b, int i) const {
-    // L2 only: in the fused iteration kernel other CTAs wrote these rows in this launch
+    if constexpr (kStream) return __ldcs(y + (b ? offB : offA) + i);
     return __ldcg(y + (b ? offB : offA) + i);
   }
 };
 
+template <bool kStream = false>
 struct DstRows {
   float2* y;
   const Group* g;
@@ -50,11 +55,13 @@ struct DstRows {
   __device__ __forceinline__ void operator()(int b, int i, float2 v) const {
     if (b && self) return;
     const int r = b ? rB : rA;
-    y[(int64_t)r * g->M2 + i] = cmulc(v, tw_big(*g, r * i));
+    const float2 o = cmulc(v, tw_big(*g, r * i));
+    if constexpr (kStream) __stcs(y + (int64_t)r * g->M2 + i, o);
+    else y[(int64_t)r * g->M2 + i] = o;
   }
 };
 
-template <int M2, int T, int MODE>
+template <int M2, int T, int MODE, bool kStream = false>
 __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, const float2* tws,
                                                 float* red, int ci, int rA_) {
   using Lay = RowLayout<M2>;
@@ -72,7 +79,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   const bool inv = mess || mode == kRowPcgApply || mode == kRowPcgRhs;
 
   if (fwd) {
-    const SrcRows src{y, rA * M2, rB * M2};
+    const SrcRows<kStream> src{y, rA * M2, rB * M2};
     smem_fft<M2, 2, Lay, T, -1>(sm, tws, src);
   }
 
@@ -254,7 +261,7 @@ __device__ __forceinline__ void kernel_body_job(const RowParams& q, float2* sm, 
   }
   if (!inv) return;
   __syncthreads();
-  smem_fft<M2, 2, Lay, T, +1>(sm, tws, SmemIO{}, DstRows{y, &q.g, rA, rB, self});
+  smem_fft<M2, 2, Lay, T, +1>(sm, tws, SmemIO{}, DstRows<kStream>{y, &q.g, rA, rB, self});
 }
 
 // The row kernel's parameters for batch b and row mode a.

@@ -96,13 +96,15 @@ def test_bounded_wait_check_rejects_bad_limits(lib):
     assert lib.mm_check_bounded_wait(10, 0, None, None) == binding.MM_ERR_ARG
 
 
-@pytest.mark.parametrize("count", list(range(1, 13)) + [31])
-def test_fused_item_list_order(lib, count):
-    """The fused kernel's work list (host code, no GPU): each item exactly once, and every
-    row job after all column tiles of its chunk, every inverse tile after all row jobs of
-    its chunk -- the order that keeps the kernel free of deadlock."""
-    items = binding.fused_item_list(512, 4096, count)
-    nA, nB = 4096 // 16, 512 // 2 + 1
+@pytest.mark.parametrize("m1,cb", [(512, 16), (1024, 8), (2048, 4)])
+@pytest.mark.parametrize("count", list(range(1, 13)) + [16, 31])
+def test_fused_item_list_order(lib, count, m1, cb):
+    """The fused kernel's work list (host code, no GPU) for the three fused shapes (columns
+    of 512, 1024 and 2048 points in tiles of 16, 8 and 4 columns, rows of 4096): each item
+    exactly once, and every row job after all column tiles of its chunk, every inverse tile
+    after all row jobs of its chunk -- the order that keeps the kernel free of deadlock."""
+    items = binding.fused_item_list(m1, 4096, count)
+    nA, nB = 4096 // cb, m1 // 2 + 1
     assert items.shape == (count * (2 * nA + nB), 3)
     assert len({tuple(r) for r in items}) == len(items)
     doneA = np.zeros(count, dtype=int)
@@ -147,3 +149,48 @@ def test_missing_library_raises_instead_of_falling_back(tmp_path):
             binding.load(str(tmp_path / "libmm.so"))
     finally:
         binding._lib = saved
+
+
+def test_noalloc_binding_checks_arguments_before_any_call():
+    """binned_map_noalloc checks types and sizes on the host before it passes a pointer (the
+    kernels trust the sizes they are given); wrong arguments raise without a launch."""
+    torch = pytest.importorskip("torch")
+    n, npix = 64, 16
+    pix = torch.zeros(n, dtype=torch.int32)
+    tod = torch.zeros(n, dtype=torch.float32)
+    c32, s32 = torch.zeros(n), torch.zeros(n)
+    out = torch.zeros(npix, 3, dtype=torch.float64)
+    with pytest.raises(ValueError):      # map_out too small for n_pix x ncomp
+        binding.binned_map_noalloc(pix, c32, s32, tod, npix, 3, out[:npix - 1])
+    with pytest.raises(TypeError):       # pixel indices not int32
+        binding.binned_map_noalloc(pix.long(), c32, s32, tod, npix, 3, out)
+    with pytest.raises(ValueError):      # tod shorter than pix
+        binding.binned_map_noalloc(pix, c32, s32, tod[:-1], npix, 3, out)
+    with pytest.raises(TypeError):       # weights of two precisions
+        binding.binned_map_noalloc(pix, c32, s32.half(), tod, npix, 3, out)
+    with pytest.raises(ValueError):      # weights shorter than pix
+        binding.binned_map_noalloc(pix, c32[:-1], s32[:-1], tod, npix, 3, out)
+    with pytest.raises(ValueError):      # weights given for a T-only map
+        binding.binned_map_noalloc(pix, c32, s32, tod, npix, 1, out)
+    with pytest.raises(TypeError):       # weights neither float32 nor float16
+        binding.binned_map_noalloc(pix, c32.double(), s32.double(), tod, npix, 3, out)
+    with pytest.raises(ValueError):      # map_out not float64
+        binding.binned_map_noalloc(pix, c32, s32, tod, npix, 3, out.float())
+    with pytest.raises(ValueError):      # correct arguments, but host tensors
+        binding.binned_map_noalloc(pix, c32, s32, tod, npix, 3, out)
+
+
+def test_noalloc_rejects_bad_rcond_on_the_host(lib):
+    """rcond_min outside [0, 1] or NaN is an argument error, as for mm_plan_pointing (checked
+    before any device work: the pointers below are never dereferenced)."""
+    dummy = ctypes.c_void_p(16)
+    for bad in (float("nan"), -0.5, 1.5):
+        st = lib.mm_binned_map_noalloc(dummy, None, None, 0, dummy, 0, 16, 1, bad, dummy, None)
+        assert st == binding.MM_ERR_ARG
+        assert b"rcond_min" in lib.mm_last_error()
+
+
+def test_wait_policy_host_checks(lib):
+    """The wait policy is checked on the host: a NULL plan or a limit outside [1, 2^22] is an
+    argument error."""
+    assert lib.mm_plan_set_wait_policy(None, 1, 0) == binding.MM_ERR_ARG

@@ -66,6 +66,37 @@ def test_fused_matches_separate_kernels(n_det):
         stage_iterate(plan, m_c, [lam])
 
 
+@pytest.mark.parametrize("log_n,n_det", [(23, 2), (24, 1), (24, 3)])
+def test_fused_long_chunks_match_separate_kernels(log_n, n_det):
+    """Chunks of 2^23 and 2^24 samples (columns of 1024 and 2048 points in tiles of 8 and 4
+    columns, rows of 4096) with FP16 weights: the fused launch against the three separate
+    kernels, maps to 1e-9 and no fault flag, then the PCG operator's fused launch against
+    the oracle's PCG.  PCG's step lengths amplify the FP32 operator error (about 3e-7 rms
+    for a 2^23-point transform): its second iterate is compared at the 1e-4 tolerance of
+    the long runs (measured 2.0e-5 for the 2^24-sample chunk)."""
+    s = synth.config_iqu(64, n_det, 1 << log_n, 70 + log_n + n_det, weight_dtype=np.float16)
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_batches() == 1 and plan.n_fused_batches() == 1
+    lams = [math.inf, 1e4, 30.0, 1.0]
+    m_f = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    plan.messenger(m_f, lams)
+    m_s = torch.zeros_like(m_f)
+    stage_iterate(plan, m_s, lams)
+    m_g = torch.zeros_like(m_f)
+    plan.messenger_graph(m_g, lams)
+    torch.cuda.synchronize()
+    assert plan.fault_flags() == 0
+    assert rel(m_f.cpu().numpy(), m_s.cpu().numpy()) <= 1e-9
+    assert rel(m_g.cpu().numpy(), m_s.cpu().numpy()) <= 1e-9
+    if n_det == 1:
+        prob = O.problem_from_synth(s)
+        x = torch.zeros_like(m_f)
+        plan.pcg(x, 2)
+        torch.cuda.synchronize()
+        x_ref, _ = O.pcg(prob, 2)
+        assert rel(x.cpu().numpy(), x_ref) <= 1e-4
+
+
 def test_fused_graph_and_repeated_launches():
     """The graph-replayed iteration (counters reset by each launch's last CTA) gives the
     iterate of the host-launched one, twice in a row."""
@@ -198,3 +229,37 @@ def test_bounded_wait_runs_out_and_reports():
     assert binding.check_bounded_wait(2000, flag_set=True) is False
     x = torch.ones(1024, device=DEV)
     assert float((x * 2).sum()) == 2048.0
+
+
+def test_solver_calls_report_an_expired_wait():
+    """With a one-poll limit and check-on-return, the fused launch's first row jobs (taken
+    at the start of the launch, beside the chunk's 256 column tiles, each of which takes
+    microseconds) poll their chunk's counter once, give up and set the fault flag; the
+    solver calls then synchronise and return MM_ERR_TIMEOUT.  A wait that gives up is a
+    loop that ends, not a fault: with the default policy back, the same plan gives the
+    correct iteration again."""
+    s = synth.config_iqu(64, 1, N22, 61)
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_fused_batches() == 1
+    lams = [math.inf, 30.0]
+    ref = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    plan.messenger(ref, lams)
+    torch.cuda.synchronize()
+    assert plan.fault_flags() == 0
+    plan.set_wait_policy(1, True)
+    m = torch.zeros_like(ref)
+    calls = [lambda: plan.messenger(m, lams), lambda: plan.messenger_graph(m, lams),
+             lambda: plan.pcg(m, 2)]
+    for call in calls:
+        with pytest.raises(binding.MMError) as e:
+            call()
+        assert e.value.code == binding.MM_ERR_TIMEOUT
+        assert "bounded wait" in str(e.value)
+    plan.set_wait_policy()
+    m2 = torch.zeros_like(ref)
+    plan.messenger(m2, lams)
+    plan.messenger_graph(m, lams)
+    torch.cuda.synchronize()
+    assert plan.fault_flags() == 0
+    assert rel(m2.cpu().numpy(), ref.cpu().numpy()) <= 1e-9
+    assert rel(m.cpu().numpy(), ref.cpu().numpy()) <= 1e-9

@@ -91,9 +91,9 @@ def test_apply_pointing_and_transpose(n_per, ndet, width):
 
 
 @pytest.mark.parametrize("n", [512, 1024, 1 << 12, 1 << 13, 1 << 15, 1 << 17, 1 << 19, 1 << 20,
-                               1 << 21, 1 << 22])
+                               1 << 21, 1 << 22, 1 << 23, 1 << 24])
 def test_rfft_against_numpy(n):
-    """Every supported FFT shape (columns 16..512, rows 16..8192) with several chunks."""
+    """Every supported FFT shape (columns 16..2048, rows 16..4096) with several chunks."""
     nch = 2 if n <= (1 << 20) else 1
     pix = [np.zeros(n, dtype=np.int32) for _ in range(nch)]
     s = synth.make_problem(4, 1, pix, 100.0, [1.0] * nch, [1.0] * nch, [2.0] * nch, [0.0] * nch,
@@ -164,6 +164,23 @@ def test_messenger_single_steps(cfg):
     m0 = np.random.default_rng(4).standard_normal((s["npix"], 3)) * prob.valid[:, None]
     for lam in (math.inf, lm, 3.0, 1.0):
         _, m, chi, m_ref, chi_ref = run_both(s, [lam], tau=tau, m0=m0)
+        assert rel(m, m_ref) <= 1e-5, (lam, rel(m, m_ref))
+        assert abs(chi[0] - chi_ref[0]) <= 1e-5 * chi_ref[0]
+
+
+@pytest.mark.parametrize("wdtype", [np.float16, np.float32])
+def test_long_chunks_one_step(wdtype):
+    """Chunks of 2^23 and 2^24 samples (1024- and 2048-point columns, tiles of 8 and 4
+    columns) on a 32x32 IQU map: one messenger step at lambda = inf, lambda_max and 3 from
+    a random map, element by element against the oracle."""
+    chunks = [synth.raster_alternating(32, 4, 1 << 23, 0), synth.raster_alternating(32, 4, 1 << 24, 5)]
+    s = synth.make_problem(32, 3, chunks, 200.0, [1.0, 1.3], [0.5, 1.5], [2.0, 1.5], [0.0, 60.0],
+                           0.5, 17050099, weight_dtype=wdtype)
+    prob = O.problem_from_synth(s)
+    lm = O.lambda_max(prob)
+    m0 = np.random.default_rng(8).standard_normal((s["npix"], 3)) * prob.valid[:, None]
+    for lam in (math.inf, lm, 3.0):
+        _, m, chi, m_ref, chi_ref = run_both(s, [lam], m0=m0)
         assert rel(m, m_ref) <= 1e-5, (lam, rel(m, m_ref))
         assert abs(chi[0] - chi_ref[0]) <= 1e-5 * chi_ref[0]
 
