@@ -27,7 +27,8 @@
  *  - Chunk lengths: any n_c in [4, 2^24] whose prime factors are 2, 3 and 5, with
  *    m = n_c/2 (even n_c) or n_c (odd n_c) splitting as m = M1 M2, M1 <= 512, M2 <= 4096.
  *    n_c = 2m with m a power of two in [2^8, 2^23] and a chunk offset divisible by 4 runs
- *    the compile-time kernels (and, for m = 2^21 with single pointing, the fused launch);
+ *    the compile-time kernels (and, for m = 2^21, 2^22 or 2^23 with single pointing, the
+ *    fused launch);
  *    the other lengths run the general mixed-radix kernels.  Other lengths return
  *    MM_ERR_UNSUPPORTED.  Entry points that support only the compile-time lengths say so.
  *  - One plan, one call at a time: calls on the same plan share its workspace (buffers,
@@ -134,7 +135,8 @@ mm_status mm_plan_fault_flags(mm_plan p, int* flags, void* stream);
 mm_status mm_plan_set_wait_policy(mm_plan p, int n_polls, int check_on_return);
 
 /* The work list of the fused iteration kernel for a batch of `count` chunks whose complex
- * length is m1 x m2 (m1 a power of two, m2 a multiple of 16): per item (kind, chunk, index)
+ * length is m1 x m2 (m1 a power of two up to 8192, m2 a multiple of the column tile width:
+ * 16 up to m1 = 512, else 8192 / m1): per item (kind, chunk, index)
  * with kind 0 = column tile, 1 = row-pair job, 2 = inverse column tile, written to out
  * (int [3 * capacity]; NULL to query the count).  Host only, no GPU.  The list puts every
  * item's prerequisites (all column tiles of its chunk for a row job, all row jobs for an
@@ -151,8 +153,8 @@ mm_status mm_fused_item_list(int m1, int m2, int count, int* out, int capacity, 
 mm_status mm_check_bounded_wait(int n_polls, int flag_set, int* expired, void* stream);
 
 /* How many of the plan's batches mm_messenger_iterate and mm_messenger_graph run as one
- * fused launch (column, row and inverse column passes together; chunks of 2^22 samples,
- * single pointing); the others run the three kernels one after the other. */
+ * fused launch (column, row and inverse column passes together; chunks of 2^22, 2^23 or
+ * 2^24 samples, single pointing); the others run the three kernels one after the other. */
 mm_status mm_plan_fused_batches(mm_plan p, int* n_fused);
 
 /* Chunks run in batches that share one four-step FFT intermediate buffer of at most 1 GB by

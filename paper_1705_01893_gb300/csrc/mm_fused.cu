@@ -164,18 +164,23 @@ int fused_items_per_chunk(int M1, int M2, bool general) {
 }
 
 // Item list of a batch of `count` chunks: step s has the A tiles of chunk s, the B jobs of
-// chunk s - kLagAB and the C tiles of chunk s - kLagAB - kLagBC, taken round-robin.  Every
+// chunk s - lagAB and the C tiles of chunk s - lagAB - lagBC, taken round-robin.  Every
 // item's prerequisites (all A tiles of its chunk for a B job, all B jobs for a C tile) come
 // earlier in the list.  Measured on 8 x 2^22 samples (us per launch): lags 1/1 546, 1/2 490,
 // 2/1 518, 2/2 449, 2/3 447, 3/3 447, 4/4 447, 8/8 (all A, then all B, then all C) 449:
 // short lags leave items waiting; beyond that the order hardly matters, and the gain over
-// three launches (A + B + C = 465 us) is their tails and the gaps between them.
+// three launches (A + B + C = 465 us) is their tails and the gaps between them.  For the
+// longer chunks (2048- and 1024-point columns) the phases run one after the other (lags of
+// `count`): on 32 x 2^24 samples in batches of 16 chunks, 4.57 ms per launch against 4.65
+// with lags 2/3, and 4.75 with the column tiles taken column block by column block across
+// the chunks (which spreads each moment's accumulator and map accesses over all chunks).
 int fused_build_items(int M1, int M2, int count, int2* out) {
-  constexpr int kLagAB = 2, kLagBC = 3;
+  const bool phases = M1 > 512;
+  const int lagAB = phases ? count : 2, lagBC = phases ? count : 3;
   const int nA = M2 / col_cb(M1), nB = M1 / 2 + 1, nC = nA;
   int n = 0;
-  for (int s = 0; s < count + kLagAB + kLagBC; ++s) {
-    const int ca = s, cb = s - kLagAB, cc = s - kLagAB - kLagBC;
+  for (int s = 0; s < count + lagAB + lagBC; ++s) {
+    const int ca = s, cb = s - lagAB, cc = s - lagAB - lagBC;
     const bool ha = ca < count, hb = cb >= 0 && cb < count, hc = cc >= 0 && cc < count;
     const int m = (ha ? nA : 0) > (hb ? nB : 0) ? (ha ? nA : 0) : (hb ? nB : 0);
     const int mm = m > (hc ? nC : 0) ? m : (hc ? nC : 0);
