@@ -1005,6 +1005,8 @@ static cudaError_t gen_upload(mm_plan_s* p, cudaStream_t s) {
   if ((e = cudaMemcpyAsync(p->gen_rec, rec.data(), sizeof(GenChunk) * ng, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(p->gen_ctab, ct.data(), sizeof(int2) * ct.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(p->gen_rtab, rt.data(), sizeof(int4) * rt.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+  // the column kernels read the pointing in tile order for this schedule's tile width
+  if ((e = launch_gen_tile_pointing(p, s)) != cudaSuccess) return e;
   return cudaStreamSynchronize(s);
 }
 

@@ -123,10 +123,13 @@ __global__ void __launch_bounds__(T, 2) k_fused(FusedParams q) {
                            e4 & (ROWL - 1));
       }
     }
-    // release the intermediate rows written by an A tile or a B job before its count
-    if (kind != kItemC) __threadfence();
+    // release the intermediate rows written by an A tile or a B job before its count: the
+    // barrier orders every thread's stores before thread 0's fence, which (being cumulative)
+    // orders them before the count at GPU scope (measured against a fence in every thread:
+    // 4.57 -> 4.54 ms per 16 x 2^24-sample batch, 429 -> 425 us per 8 x 2^22)
     __syncthreads();
     if (threadIdx.x == 0) {
+      if (kind != kItemC) __threadfence();
       if (kind == kItemA) atomicAdd(doneA + ci, 1u);
       if (kind == kItemB) atomicAdd(doneB + ci, 1u);
       s_it = nxt;

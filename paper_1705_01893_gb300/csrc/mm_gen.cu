@@ -31,6 +31,11 @@ struct GenParams {
   const int32_t* __restrict__ pix;      // caller's pointing, natural order
   const void* cosw;
   const void* sinw;
+  // the same pointing in column-tile order (k_gen_tile_pointing): the samples of the tile
+  // at first column j2_0 and width w are contiguous, row j1 after row j1 - 1
+  const int32_t* __restrict__ tpix;
+  const void* tcos;
+  const void* tsin;
   int half_w;
   const void* map4;
   const float* tod;
@@ -251,6 +256,7 @@ __device__ __forceinline__ void gen_gather_tile(const GenParams& q, const ChunkD
   constexpr int U = 4;
   const int n = d.M1 * NB;
   const int nh = d.cplx ? 1 : 2;
+  const int64_t tb = d.off + (int64_t)d.M1 * j2_0 * nh;   // the tile's first sample
   for (int e0 = threadIdx.x; e0 < n; e0 += U * T) {
     int pi[U][2];
     float cw[U][2], sw[U][2];
@@ -263,16 +269,15 @@ __device__ __forceinline__ void gen_gather_tile(const GenParams& q, const ChunkD
         pi[u][h] = -1;
         cw[u][h] = sw[u][h] = 0.f;
         if (e < n && c < width && h < nh) {
-          const int64_t j = (int64_t)j1 * d.M2 + j2_0 + c;
-          const int64_t s = d.cplx ? d.off + j : d.off + 2 * j + h;
-          pi[u][h] = __ldg(q.pix + s);
+          const int64_t s = tb + ((int64_t)j1 * width + c) * nh + h;
+          pi[u][h] = __ldg(q.tpix + s);
           if constexpr (NC == 3) {
             if (q.half_w) {
-              cw[u][h] = __half2float(static_cast<const __half*>(q.cosw)[s]);
-              sw[u][h] = __half2float(static_cast<const __half*>(q.sinw)[s]);
+              cw[u][h] = __half2float(static_cast<const __half*>(q.tcos)[s]);
+              sw[u][h] = __half2float(static_cast<const __half*>(q.tsin)[s]);
             } else {
-              cw[u][h] = __ldg(static_cast<const float*>(q.cosw) + s);
-              sw[u][h] = __ldg(static_cast<const float*>(q.sinw) + s);
+              cw[u][h] = __ldg(static_cast<const float*>(q.tcos) + s);
+              sw[u][h] = __ldg(static_cast<const float*>(q.tsin) + s);
             }
           }
         }
@@ -353,10 +358,11 @@ template <int NC>
 __device__ __forceinline__ void gen_scatter(const GenParams& q, const ChunkDesc& d, int j2_0,
                                             int width, const float* smf, int NB, int lnb, int T,
                                             const int32_t* __restrict__ pix, const void* cosw,
-                                            const void* sinw, float gain) {
+                                            const void* sinw, float gain, bool tiled) {
   const int rw = d.cplx ? NB : 2 * NB;          // samples per tile row
   const int lrw = d.cplx ? lnb : lnb + 1;
   const int valid_u = d.cplx ? width : 2 * width;
+  const int64_t tb = d.off + (int64_t)d.M1 * j2_0 * (d.cplx ? 1 : 2);   // tile order
   const int total = d.M1 * rw;
   const int lane = threadIdx.x & 31;
   // two rounds of 32 samples per warp: both rounds' pointing loads are issued before the
@@ -373,8 +379,9 @@ __device__ __forceinline__ void gen_scatter(const GenParams& q, const ChunkDesc&
       if (e < total) {
         const int j1 = e >> lrw, u = e & (rw - 1);
         if (u < valid_u) {
-          const int64_t s = d.off + (d.cplx ? (int64_t)j1 * d.M2 + j2_0 + u
-                                            : 2 * ((int64_t)j1 * d.M2 + j2_0) + u);
+          const int64_t s = tiled ? tb + (int64_t)j1 * valid_u + u
+                                  : d.off + (d.cplx ? (int64_t)j1 * d.M2 + j2_0 + u
+                                                    : 2 * ((int64_t)j1 * d.M2 + j2_0) + u);
           pv[k] = __ldg(pix + s);
           tv[k] = gain * (d.cplx ? smf[2 * e] : smf[e]);
           if constexpr (NC == 3) {
@@ -437,10 +444,10 @@ __global__ void __launch_bounds__(512) k_gen_col_inverse(GenParams q) {
     const float2* r = gen_dft_cols<+1>(a, b, M1, G.nr1, G.rad1, G.tw_col, NB, lnb, T);
     const float* rf = reinterpret_cast<const float*>(r);
     if (!q.composite) {
-      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.pix, q.cosw, q.sinw, 1.f);
-    } else {   // P^T t = g_a P_a^T t + g_b P_b^T t (App. B)
-      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.pix, q.cosw, q.sinw, q.ga);
-      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.pix2, q.cos2, q.sin2, q.gb);
+      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.tpix, q.tcos, q.tsin, 1.f, true);
+    } else {   // P^T t = g_a P_a^T t + g_b P_b^T t (App. B), natural-order pointing
+      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.pix, q.cosw, q.sinw, q.ga, false);
+      gen_scatter<NC>(q, d, j2_0, width, rf, NB, lnb, T, q.pix2, q.cos2, q.sin2, q.gb, false);
     }
     __syncthreads();
   }
@@ -653,6 +660,48 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
   }
 }
 
+// Copy one general chunk's pointing into column-tile order for tiles of nb columns: sample
+// (j1, j2, h) (even n: s = 2 (j1 M2 + j2) + h; odd n: s = j1 M2 + j2, h = 0) goes to
+// tile t = j2 / nb (first column j2_0 = t nb, width w = min(nb, M2 - j2_0)) at
+// M1 j2_0 nh + (j1 w + j2 - j2_0) nh + h, nh = 2 (even) or 1 (odd): a bijection of the
+// chunk's samples.
+__global__ void k_gen_tile_pointing(const int32_t* __restrict__ pix, const void* cosw,
+                                    const void* sinw, int wbytes, int64_t off, int n, int M1,
+                                    int M2, int cplx, int nb, int32_t* __restrict__ tpix,
+                                    void* tcos, void* tsin) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nh = cplx ? 1 : 2;
+  const int64_t j = cplx ? i : i >> 1;
+  const int h = cplx ? 0 : (int)(i & 1);
+  const int j1 = (int)(j / M2), j2 = (int)(j % M2);
+  const int j2_0 = j2 - j2 % nb;
+  const int w = min(nb, M2 - j2_0);
+  const int64_t o = off + ((int64_t)M1 * j2_0 + (int64_t)j1 * w + (j2 - j2_0)) * nh + h;
+  tpix[o] = pix[off + i];
+  if (cosw) {
+    if (wbytes == 2) {
+      static_cast<__half*>(tcos)[o] = static_cast<const __half*>(cosw)[off + i];
+      static_cast<__half*>(tsin)[o] = static_cast<const __half*>(sinw)[off + i];
+    } else {
+      static_cast<float*>(tcos)[o] = static_cast<const float*>(cosw)[off + i];
+      static_cast<float*>(tsin)[o] = static_cast<const float*>(sinw)[off + i];
+    }
+  }
+}
+
+cudaError_t launch_gen_tile_pointing(const mm_plan_s* p, cudaStream_t st) {
+  if (p->composite) return cudaSuccess;   // composite plans read the natural order
+  const int wb = p->wdtype == MM_W_F16 ? 2 : 4;
+  for (int i = 0; i < p->n_gen; ++i) {
+    const ChunkDesc& d = p->h_desc[p->h_gen_chunks[i]];
+    k_gen_tile_pointing<<<(unsigned)((d.n + 255) / 256), 256, 0, st>>>(
+        p->pix, p->cosw, p->sinw, wb, d.off, d.n, d.M1, d.M2, d.cplx, p->gen_tune.col_nb,
+        p->tpix, p->tcos, p->tsin);
+  }
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------ launchers
 static GenParams gen_params(const mm_plan_s* p, const Batch& b, const int2* items,
                             const int64_t* h_prefix) {
@@ -665,6 +714,9 @@ static GenParams gen_params(const mm_plan_s* p, const Batch& b, const int2* item
   q.pix = p->pix;
   q.cosw = p->cosw;
   q.sinw = p->sinw;
+  q.tpix = p->tpix;
+  q.tcos = p->tcos;
+  q.tsin = p->tsin;
   q.half_w = p->wdtype == MM_W_F16;
   q.map4 = p->map4;
   q.ybuf = p->ybuf;

@@ -594,6 +594,9 @@ cudaError_t launch_gen_col_forward(const mm_plan_s* p, const Batch& b, int src, 
                                    cudaStream_t st);
 cudaError_t launch_gen_row(const mm_plan_s* p, const Batch& b, const RowArgs& a, cudaStream_t st);
 cudaError_t launch_gen_col_inverse(const mm_plan_s* p, const Batch& b, cudaStream_t st);
+// Copy the general chunks' pointing into column-tile order for the schedule's tile width
+// (run whenever that width is set).
+cudaError_t launch_gen_tile_pointing(const mm_plan_s* p, cudaStream_t st);
 // Forward column pass gathering from `map4` into `ybuf` (either NULL = the plan's own).
 cudaError_t launch_col_forward_ex(const mm_plan_s* p, const Batch& b, int src, const float* tod,
                                   const void* map4, float2* ybuf, cudaStream_t st);
