@@ -157,9 +157,10 @@ mm_status mm_check_bounded_wait(int n_polls, int flag_set, int* expired, void* s
  * 2^24 samples, single pointing); the others run the three kernels one after the other. */
 mm_status mm_plan_fused_batches(mm_plan p, int* n_fused);
 
-/* Chunks run in batches that share one four-step FFT intermediate buffer of at most 1 GB by
+/* Chunks run in batches that share one four-step FFT intermediate buffer of at most 2 GB by
  * default (environment variable MM_YBUF_MB, read when the plan is made; a budget of about a
- * quarter of L2 keeps each batch's intermediate resident in L2 between passes).
+ * quarter of L2 keeps each batch's intermediate resident in L2 between passes, at the cost
+ * of more launches).
  * *n_batches receives their number; batches run one after another on the caller's stream. */
 mm_status mm_plan_batches(mm_plan p, int* n_batches);
 

@@ -88,6 +88,12 @@ cudaError_t mm::resident_ctas(const void* kernel, int threads, size_t smem, int*
 }
 
 // ------------------------------------------------------------------------ FFT shapes
+// Slots a chunk of complex length M takes in the spectrum-sized buffers (d~, Nbar, the
+// adjoint's kept spectra): M rounded up to a multiple of 4, so that every chunk's block
+// starts on 16 bytes of the FP32 table and 32 bytes of the complex ones (bulk prefetches
+// of its rows need 16-byte alignment, whatever lengths come before it in the plan).
+static inline int64_t spec_slots(int64_t M) { return (M + 3) & ~int64_t(3); }
+
 // M = 2^p complex points per chunk (n = 2M real samples): columns M1, rows M2 = M / M1.
 // Columns up to 512 points, then rows stay at 4096 (a row pair in 64 KB of shared memory,
 // two CTAs per SM) and the columns grow to 1024 and 2048 points (tiles of 8 and 4 columns,
@@ -191,13 +197,15 @@ struct Layout {
 
 static size_t up(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Bytes of four-step intermediate one batch may use (MM_YBUF_MB overrides; default 1 GB).
+// Bytes of four-step intermediate one batch may use (MM_YBUF_MB overrides; default 2 GB).
 // Small budgets (a quarter of L2) keep a batch's intermediate L2-resident between passes,
-// but the extra launches cost more than the saved HBM traffic on the 8 x 2^22 workload.
+// but the extra launches cost more than the saved HBM traffic on the 8 x 2^22 workload;
+// 2 GB puts the 32 chunks of 2^24 samples of the 2048^2 workload in one batch (one fused
+// launch per iteration: 9.15 -> 9.08 ms against two batches of 16).
 static size_t ybuf_budget() {
   const char* e = getenv("MM_YBUF_MB");
-  const long mb = e ? atol(e) : 1024;
-  return (size_t)(mb > 0 ? mb : 1024) << 20;
+  const long mb = e ? atol(e) : 2048;
+  return (size_t)(mb > 0 ? mb : 2048) << 20;
 }
 
 static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, int ncomp,
@@ -241,7 +249,7 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
     }
     L->gcount[g]++;
     L->chunk_group[c] = g;
-    L->spec_total += M;
+    L->spec_total += spec_slots(M);
     if (general) L->gen_list.push_back(c);
   }
   L->n_total = off[n_chunks];
@@ -1165,7 +1173,7 @@ static mm_status plan_create(mm_plan* out, int n_chunks, const int64_t* offsets,
     d.grp = g;
     d.cplx = L.gcplx[g];
     d.tau = 1.0;
-    spec += d.M;
+    spec += spec_slots(d.M);
     nat += d.n / 2 + 1;
     p->h_chunk_group[c] = g;
   }

@@ -497,10 +497,37 @@ __global__ void __launch_bounds__(1024) k_gen_row(GenParams q) {
     float2* b = gsm + q.tile;
     bool pz = false;
     float2* z = a;
+    if (threadIdx.x == 0 && job + gridDim.x < q.n_items) {
+      // the next job's rows (and its d~ / Nbar rows) into L2 while this one runs
+      const int4 nj = __ldg(q.jobs + q.base + job + gridDim.x);
+      const GenChunk& Gn = q.rec[nj.x];
+      const int nM1 = Gn.d.M1, nM2 = Gn.d.M2;
+      const int ncount = nj.z == 0 ? 1 : nj.z;
+      const float2* yn = q.ybuf + (Gn.yoff - q.base_y);
+      for (int s = 0; s < (nj.z == 0 ? 1 : 2 * ncount); ++s) {
+        const int r = nj.z == 0 ? nj.y : ((s & 1) ? nM1 - nj.y - (s >> 1) : nj.y + (s >> 1));
+        // rows of general chunks need not start on 16 bytes: prefetch their aligned interior
+        if (fwd) prefetch_l2_inner(yn + (int64_t)r * nM2, 8 * (size_t)nM2);
+        if (load_d) prefetch_l2_inner(q.dtab + Gn.d.spec + (int64_t)r * nM2, 8 * (size_t)nM2);
+        prefetch_l2_inner(q.nbar + Gn.d.spec + (int64_t)r * nM2, 4 * (size_t)nM2);
+      }
+    }
     if (fwd) {
-      for (int e = threadIdx.x; e < nseq * M2; e += T) {
-        const int sq = fm2.div(e), p = e - sq * M2;
-        a[e] = y[(int64_t)row_of(sq) * M2 + p];
+      // four elements' loads in flight per thread before their stores
+      const int ne = nseq * M2;
+      for (int e0 = threadIdx.x; e0 < ne; e0 += 4 * T) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * T;
+          if (e < ne) {
+            const int sq = fm2.div(e), p = e - sq * M2;
+            v[u] = y[(int64_t)row_of(sq) * M2 + p];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (e0 + u * T < ne) a[e0 + u * T] = v[u];
       }
       __syncthreads();
       z = gen_dft_rows<-1>(a, b, pz, M2, G.nr2, G.rad2, G.tw_row, nseq, T);

@@ -66,8 +66,8 @@ __host__ __device__ inline int gen_row_pairs(int M1, int M2) {
 }
 
 // A batch: `count` consecutive chunks of one group whose four-step intermediates share the
-// ybuf slot.  Batches are sized so the slot (default 32 MB) stays resident in L2 between
-// the column and row passes; they run one after another on the caller's stream.
+// ybuf slot (its size is the plan's intermediate budget, 2 GB by default); batches run one
+// after another on the caller's stream.
 struct Batch {
   int group;          // -1: a batch of the general path (chunks of any general length)
   int first;          // index into the group's chunk list (general: into the general list)
@@ -502,6 +502,15 @@ __device__ __forceinline__ void red_add_f64(double* a, double v, uint64_t pol) {
 // Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (p and bytes multiples of 16).
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Bulk prefetch of the 16-byte-aligned interior of [p, p + bytes) (start rounded up, end
+// rounded down, so that nothing outside the range is touched), for ranges that need not be
+// aligned (rows of general-length chunks).
+__device__ __forceinline__ void prefetch_l2_inner(const void* p, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p), e = a + bytes;
+  const uintptr_t a16 = (a + 15) & ~uintptr_t(15), e16 = e & ~uintptr_t(15);
+  if (e16 > a16) prefetch_l2(reinterpret_cast<const void*>(a16), (unsigned)(e16 - a16));
 }
 
 // Resident CTAs of `kernel` on the whole GPU (opting it in to `smem` bytes of dynamic

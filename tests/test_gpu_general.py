@@ -78,6 +78,30 @@ def test_rfft_mixed_plan_and_unaligned_offsets():
     rfft_check(t_only([4096, 1536, 2048], first=3))
 
 
+def test_power_of_two_chunk_after_odd_spectrum_block():
+    """A power-of-two chunk (compile-time kernels: its offset 4500 is a multiple of 4) after
+    two chunks of 2250 samples, whose complex lengths 1125 sum to 2250 slots, then odd-length
+    and power-of-two chunks on the general path: every chunk's block in the spectrum-sized
+    buffers starts on a multiple of 4 slots, so the row jobs' bulk prefetches of d~ / Nbar
+    rows stay 16-byte aligned.  rfft and one messenger step at lambda = 10 against the
+    oracle."""
+    lens = [2250, 2250, 1 << 16, 3375, 1 << 14]
+    chunks = [synth.raster_alternating(16, 2, n, k) for k, n in enumerate(lens)]
+    k = len(lens)
+    s = synth.make_problem(16, 3, chunks, 100.0, [1.0, 1.2, 0.9, 1.1, 1.0][:k],
+                           [1.0, 0.5, 2.0, 0.3, 0.7][:k], [2.0, 1.5, 1.0, 2.5, 2.0][:k],
+                           [0.0, 30.0, 60.0, 90.0, 120.0][:k], 0.5, 21)
+    rfft_check(s)
+    prob = O.problem_from_synth(s)
+    plan = binding.plan_from_synth(s, DEV)
+    m0 = np.random.default_rng(2).standard_normal((s["npix"], 3)) * prob.valid[:, None]
+    m_ref, _ = O.messenger_step(prob, m0, 10.0)
+    m = to_dev(m0)
+    plan.messenger(m, [10.0])
+    torch.cuda.synchronize()
+    assert rel(m.cpu().numpy(), m_ref) <= 1e-5
+
+
 @pytest.fixture(scope="module")
 def uneven():
     s = synth.config_uneven(32, 5, 2000, 12000, seed=17050112)
