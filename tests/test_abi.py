@@ -194,3 +194,21 @@ def test_wait_policy_host_checks(lib):
     """The wait policy is checked on the host: a NULL plan or a limit outside [1, 2^22] is an
     argument error."""
     assert lib.mm_plan_set_wait_policy(None, 1, 0) == binding.MM_ERR_ARG
+
+
+def test_degenerate_plans_rejected_on_host(lib):
+    """No chunk, a negative chunk count, offsets that decrease (an empty or negative chunk)
+    and a NULL offsets array are argument errors, answered before any device work."""
+    n = ctypes.c_size_t()
+
+    def ws(off, nc):
+        o = np.array(off, dtype=np.int64)
+        return lib.mm_plan_workspace_size(nc, o.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                          10, 1, 0, ctypes.byref(n))
+    assert ws([0], 0) == binding.MM_ERR_ARG and b"n_chunks" in lib.mm_last_error()
+    assert ws([0, 4096], -1) == binding.MM_ERR_ARG
+    assert ws([0, 4096, 2048], 2) == binding.MM_ERR_ARG and b"empty" in lib.mm_last_error()
+    assert ws([0, 4096, 4096], 2) == binding.MM_ERR_ARG
+    assert lib.mm_plan_workspace_size(1, None, 10, 1, 0, ctypes.byref(n)) == binding.MM_ERR_ARG
+    # a plan may start at a non-zero offset (samples before it belong to no chunk)
+    assert ws([5, 5 + 4096], 1) == binding.MM_OK
