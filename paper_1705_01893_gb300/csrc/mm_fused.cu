@@ -173,13 +173,16 @@ int fused_items_per_chunk(int M1, int M2, bool general) {
 // 2/1 518, 2/2 449, 2/3 447, 3/3 447, 4/4 447, 8/8 (all A, then all B, then all C) 449:
 // short lags leave items waiting; beyond that the order hardly matters, and the gain over
 // three launches (A + B + C = 465 us) is their tails and the gaps between them.  For the
-// longer chunks (2048- and 1024-point columns) the phases run one after the other (lags of
-// `count`): on 32 x 2^24 samples in batches of 16 chunks, 4.57 ms per launch against 4.65
-// with lags 2/3, and 4.75 with the column tiles taken column block by column block across
-// the chunks (which spreads each moment's accumulator and map accesses over all chunks).
+// longer chunks (1024- and 2048-point columns) the column tiles of all chunks run first
+// (lagAB = count), then the row jobs and inverse tiles interleaved with lag 3: on 32 x 2^24
+// samples in one batch, 8.89 ms per launch against 8.98 with the three phases one after
+// the other, 8.93 with the column and row passes interleaved and the inverse tiles last,
+// and (per 16-chunk batch) 4.65 against 4.57 with lags 2/3 throughout: the column and
+// inverse tiles' map and accumulator accesses do better apart.  Taking the column tiles
+// column block by column block across the chunks was slower still (4.75 per 16 chunks).
 int fused_build_items(int M1, int M2, int count, int2* out) {
-  const bool phases = M1 > 512;
-  const int lagAB = phases ? count : 2, lagBC = phases ? count : 3;
+  const bool long_chunks = M1 > 512;
+  const int lagAB = long_chunks ? count : 2, lagBC = 3;
   const int nA = M2 / col_cb(M1), nB = M1 / 2 + 1, nC = nA;
   int n = 0;
   for (int s = 0; s < count + lagAB + lagBC; ++s) {
