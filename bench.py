@@ -302,7 +302,22 @@ def oracle_rate(s, workers, steps, warmup):
              for c in range(workers)]
     for p in procs:
         p.start()
-    res = [queue.get(timeout=7200) for _ in procs]
+    # collect one result per worker; a worker that dies without reporting (killed, out of
+    # memory) ends the wait instead of leaving the others at their barrier
+    import queue as queue_mod
+    res = []
+    deadline = time.time() + 7200
+    while len(res) < len(procs):
+        try:
+            res.append(queue.get(timeout=5))
+        except queue_mod.Empty:
+            dead = [p.exitcode for p in procs if p.exitcode not in (None, 0)]
+            if dead or time.time() > deadline:
+                for p in procs:
+                    if p.is_alive():
+                        p.terminate()
+                raise RuntimeError("oracle worker exited with code %s before reporting"
+                                   % (dead[0] if dead else "timeout"))
     for p in procs:
         p.join(timeout=600)
     bad = [r[1] for r in res if r[0] != "ok"]
