@@ -28,7 +28,8 @@
  *    m = n_c/2 (even n_c) or n_c (odd n_c) splitting as m = M1 M2, M1 <= 512, M2 <= 4096.
  *    n_c = 2m with m a power of two in [2^8, 2^23] and a chunk offset divisible by 4 runs
  *    the compile-time kernels (and, for m = 2^21, 2^22 or 2^23 with single pointing, the
- *    fused launch);
+ *    fused launch), except where the plan also has general-path chunks and the chunks of
+ *    that length hold at most 2^20 samples in all: those join the general batch;
  *    the other lengths run the general mixed-radix kernels.  Other lengths return
  *    MM_ERR_UNSUPPORTED.  Entry points that support only the compile-time lengths say so.
  *  - One plan, one call at a time: calls on the same plan share its workspace (buffers,

@@ -220,13 +220,36 @@ static mm_status make_layout(int n_chunks, const int64_t* off, int64_t n_pix, in
   L->gen_list.clear();
   L->gen_batches.clear();
   L->spec_total = 0;
+  // Power-of-two chunks on 16-byte boundaries take the compile-time kernels (vector loads),
+  // one batch per length.  When the plan has a general batch anyway, a length whose chunks
+  // hold at most 2^20 samples in all joins it instead: its own batch would add three
+  // launches of a few small waves (about 25 us per iteration for one chunk of 2^17 samples
+  // beside 24.6 M general samples: 0.851 -> 0.827 ms), more than the general kernels' lower
+  // rate costs on that many samples.
+  bool any_general = force_general;
+  std::vector<std::pair<int64_t, int64_t>> pow2_total;   // (length, samples of that length)
+  for (int c = 0; c < n_chunks; ++c) {
+    const int64_t n = off[c + 1] - off[c];
+    int M_, M1_, M2_;
+    if (n < 1) continue;   // reported below
+    if (!(fft_shape(n, &M_, &M1_, &M2_) && off[c] % 4 == 0)) { any_general = true; continue; }
+    bool found = false;
+    for (auto& e : pow2_total)
+      if (e.first == n) { e.second += n; found = true; }
+    if (!found) pow2_total.push_back({n, n});
+  }
+  auto joins_general = [&](int64_t n) {
+    if (!any_general) return false;
+    for (const auto& e : pow2_total)
+      if (e.first == n) return e.second <= (int64_t(1) << 20);
+    return false;
+  };
   for (int c = 0; c < n_chunks; ++c) {
     const int64_t n = off[c + 1] - off[c];
     MM_ARG(n >= 1, "chunk %d is empty or offsets decrease", c);
     int M, M1, M2, cplx = 0;
-    // power-of-two chunks on 16-byte boundaries take the compile-time kernels (vector loads)
     bool general = false;
-    if (force_general || !(fft_shape(n, &M, &M1, &M2) && off[c] % 4 == 0)) {
+    if (force_general || joins_general(n) || !(fft_shape(n, &M, &M1, &M2) && off[c] % 4 == 0)) {
       if (!gen_shape(n, &M, &M1, &M2, &cplx)) {
         mm_set_error("chunk %d: length %lld unsupported (need prime factors 2, 3, 5 only and "
                      "n <= 2^24; n/2 up to 2^21 for lengths that are not powers of two)",

@@ -72,20 +72,46 @@ def test_rfft_general_lengths(n):
 
 
 def test_rfft_mixed_plan_and_unaligned_offsets():
-    """Power-of-two and general chunks in one plan; a power-of-two chunk that does not start
-    on a 16-byte boundary takes the general path; a plan that starts at an odd offset."""
-    rfft_check(t_only([4096, 3375, 4096, 1024, 6250]))
+    """Power-of-two and general chunks in one plan (the 2^21-sample chunk keeps the
+    compile-time kernels); power-of-two chunks that do not start on a 16-byte boundary take
+    the general path; a plan that starts at an odd offset."""
+    rfft_check(t_only([1 << 21, 3375, 4096, 1024, 6250]))
     rfft_check(t_only([4096, 1536, 2048], first=3))
 
 
+def test_small_power_of_two_chunks_join_the_general_batch():
+    """In a plan with general chunks, a power-of-two length whose chunks hold at most 2^20
+    samples in all runs in the general batch (one batch in all); a longer one keeps a
+    compile-time batch of its own.  Without general chunks nothing changes.  One messenger
+    step of the joined plan against the oracle."""
+    # power-of-two chunks first, so that they start on 16-byte boundaries
+    assert binding.plan_from_synth(t_only([1 << 14, 1 << 14, 1 << 16, 3375]), DEV).n_batches() == 1
+    assert binding.plan_from_synth(t_only([1 << 16] * 17 + [3375]), DEV).n_batches() == 2
+    assert binding.plan_from_synth(t_only([1 << 21, 3375]), DEV).n_batches() == 2
+    assert binding.plan_from_synth(t_only([1 << 14, 1 << 16]), DEV).n_batches() == 2
+    lens = [1 << 14, 1 << 16, 3375, 6250]
+    chunks = [synth.raster_alternating(16, 2, n, k) for k, n in enumerate(lens)]
+    s = synth.make_problem(16, 3, chunks, 100.0, [1.0, 1.2, 0.9, 1.1], [1.0, 0.5, 2.0, 0.3],
+                           [2.0, 1.5, 1.0, 2.5], [0.0, 45.0, 90.0, 135.0], 0.5, 23)
+    prob = O.problem_from_synth(s)
+    plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_batches() == 1
+    m0 = np.random.default_rng(5).standard_normal((s["npix"], 3)) * prob.valid[:, None]
+    m_ref, _ = O.messenger_step(prob, m0, 10.0)
+    m = to_dev(m0)
+    plan.messenger(m, [10.0])
+    torch.cuda.synchronize()
+    assert rel(m.cpu().numpy(), m_ref) <= 1e-5
+
+
 def test_power_of_two_chunk_after_odd_spectrum_block():
-    """A power-of-two chunk (compile-time kernels: its offset 4500 is a multiple of 4) after
-    two chunks of 2250 samples, whose complex lengths 1125 sum to 2250 slots, then odd-length
-    and power-of-two chunks on the general path: every chunk's block in the spectrum-sized
-    buffers starts on a multiple of 4 slots, so the row jobs' bulk prefetches of d~ / Nbar
-    rows stay 16-byte aligned.  rfft and one messenger step at lambda = 10 against the
-    oracle."""
-    lens = [2250, 2250, 1 << 16, 3375, 1 << 14]
+    """A power-of-two chunk (compile-time kernels: its offset 4500 is a multiple of 4, and
+    its 2^21 samples are too many to join the general batch) after two chunks of 2250
+    samples, whose complex lengths 1125 sum to 2250 slots, then odd-length and power-of-two
+    chunks on the general path: every chunk's block in the spectrum-sized buffers starts on
+    a multiple of 4 slots, so the row jobs' bulk prefetches of d~ / Nbar rows stay 16-byte
+    aligned.  rfft and one messenger step at lambda = 10 against the oracle."""
+    lens = [2250, 2250, 1 << 21, 3375, 1 << 14]
     chunks = [synth.raster_alternating(16, 2, n, k) for k, n in enumerate(lens)]
     k = len(lens)
     s = synth.make_problem(16, 3, chunks, 100.0, [1.0, 1.2, 0.9, 1.1, 1.0][:k],
@@ -94,6 +120,7 @@ def test_power_of_two_chunk_after_odd_spectrum_block():
     rfft_check(s)
     prob = O.problem_from_synth(s)
     plan = binding.plan_from_synth(s, DEV)
+    assert plan.n_batches() == 2          # the 2^21-sample chunk has a batch of its own
     m0 = np.random.default_rng(2).standard_normal((s["npix"], 3)) * prob.valid[:, None]
     m_ref, _ = O.messenger_step(prob, m0, 10.0)
     m = to_dev(m0)
