@@ -50,6 +50,39 @@ def test_differentiation_workload_101_cooled_iterations():
     assert np.max(np.abs(c - chi_ref) / chi_ref) <= 1e-5, np.max(np.abs(c - chi_ref) / chi_ref)
 
 
+def test_differentiation_workload_pcg_and_map_sized_form():
+    """256^2 IQU, 4 x 2^20 samples: the comparison solver (PCG with the 3x3 block-Jacobi
+    preconditioner, 30 iterations from m = 0) against the FP64 PCG oracle, and 20 cooled
+    iterations of the map-sized form m' = m_d(lambda) + F(lambda) m (Sec. 2.1) against the
+    oracle's messenger iterates.  PCG: iterate <= 1e-4 relative L2 and chi^2 of every
+    iterate <= 1e-5 (the tolerances of the small-size PCG test; measured 2.8e-5 and 1.1e-7);
+    map-sized form: final map <= 1e-4 relative rms, chi^2 per iteration <= 1e-5 (measured
+    3.6e-7 and 7.0e-7)."""
+    s = synth.config_iqu_256()
+    prob = O.problem_from_synth(s)
+    plan = binding.plan_from_synth(s, DEV)
+    x_ref, chi_ref = O.pcg(prob, 30)
+    x = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    chi = torch.zeros(30, dtype=torch.float64, device=DEV)
+    plan.pcg(x, 30, restart=True, chi2_out=chi)
+    torch.cuda.synchronize()
+    e_x = rel(x.cpu().numpy(), x_ref)
+    e_c = float(np.max(np.abs(chi.cpu().numpy() - chi_ref) / chi_ref))
+    assert e_x <= 1e-4, e_x
+    assert e_c <= 1e-5, e_c
+    lam = O.cooling_schedule(O.lambda_max(prob), 5, 4)
+    m_ref, c_ref = O.run_messenger(prob, lam)
+    m = torch.zeros(s["npix"], 3, dtype=torch.float64, device=DEV)
+    cm = torch.zeros(len(lam), dtype=torch.float64, device=DEV)
+    plan.messenger_md(m, lam, cm)
+    torch.cuda.synchronize()
+    got = m.cpu().numpy()
+    rms = np.sqrt(np.mean((got - m_ref) ** 2)) / np.sqrt(np.mean(m_ref ** 2))
+    assert rms <= 1e-4, rms
+    e_m = float(np.max(np.abs(cm.cpu().numpy() - c_ref) / c_ref))
+    assert e_m <= 1e-5, e_m
+
+
 def test_differentiation_workload_adjoint_k50():
     """The gradient of L = 1/2 |m_K - m_true|^2 through K = 50 cooled iterations (5 levels x
     10), checkpoints every 10, against the FP64 adjoint oracle on the same data: dL/dd and
